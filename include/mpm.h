@@ -1,0 +1,209 @@
+/*
+ * mpm.h -- exact multiple pattern matching on GB300 (MAG / SMAG).
+ *
+ * C ABI of the library built from paper_1405_5483_gb300/csrc.  It implements
+ * the text scan of Susik, Grabowski and Fredriksson, "Multiple pattern
+ * matching revisited": alphabet reduction, non-overlapping q-grams of all q
+ * shifts of every pattern superimposed into one Shift-Or mask table, the
+ * average-optimal Shift-Or scan that reads only every k-th text q-gram,
+ * candidate compaction, exact verification and a deterministic order.
+ *
+ * Problem (Section 1): text T[0..n), patterns P_0..P_{r-1}, all of length m,
+ * bytes as symbols; report every (i, p) with T[i..i+m) == P_p.
+ *
+ * Conventions shared by every entry point
+ *   - Return value: MPM_OK (0) or a positive MPM_E* code; the same code is
+ *     kept per thread for mpm_last_error().  Functions returning a pointer
+ *     return NULL on error.
+ *   - Device pointers are CUDA global memory of the current device.  Work is
+ *     enqueued on the handle's stream (mpm_set_stream), default stream 0.
+ *   - Occurrence lists are sorted by position, then pattern id; pattern ids
+ *     are 0-based row indices of P; identical patterns are each reported.
+ *   - Positions and q-gram indices are 32-bit: n < 2^32.
+ *   - Nothing here falls back to the CPU: without a usable GPU the calls
+ *     that launch kernels return MPM_ECUDA.
+ */
+#ifndef MPM_H
+#define MPM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ------------------------------------------------------------ error codes */
+#define MPM_OK         0
+#define MPM_EINVAL     1  /* bad argument or infeasible explicit parameter   */
+#define MPM_ENOMEM     2  /* host or device allocation failed                */
+#define MPM_ECUDA      3  /* a CUDA call failed (no device, launch error ...) */
+#define MPM_ECAPACITY  4  /* output capacity too small; *z = required count  */
+#define MPM_ETIMEOUT   5  /* a bounded device wait gave up; results invalid  */
+#define MPM_ENOTSUP    6  /* combination not supported by this build         */
+
+/* ----------------------------------------------------- parameter choices */
+#define MPM_MAP_AUTO     0
+#define MPM_MAP_RANK     1  /* frequency-rank bins (Section 3.3)                 */
+#define MPM_MAP_GREEDY   2  /* equal-weight bins, greedy (Section 3.3)           */
+#define MPM_MAP_LOWBITS  3  /* low-order bits after a right shift (Section 3.3)  */
+
+#define MPM_TABLE_AUTO   0
+#define MPM_TABLE_SMEM   1  /* mask table copied to shared memory per block  */
+#define MPM_TABLE_GLOBAL 2  /* mask table read from global memory (L2)       */
+
+/*
+ * Filter parameters (Sections 3.2, 3.3).  Zero in q, sigma_r, k, map_kind,
+ * table_place or chunk means "choose automatically"; map_shift < 0 means
+ * "choose automatically" (0 is a valid shift).
+ *   q        q-gram length, 1..16, with q*log2(sigma_r) <= 30 and
+ *            L' = floor((m - q + 1) / q) >= 1.
+ *   sigma_r  reduced alphabet size sigma', a power of two in 2..256.
+ *   k        AOSO sampling step: every k-th text q-gram is read; 1..32 and
+ *            k <= min(L', 64).
+ *   map_kind MPM_MAP_*.
+ *   map_shift right shift applied to a byte before its low log2(sigma_r)
+ *            bits are kept (MPM_MAP_LOWBITS only), 0..7.
+ *   table_place MPM_TABLE_*.
+ *   smag     0: MAG, q-gram codes computed on the fly inside the scan;
+ *            1: SMAG, the whole text is encoded first (Section 3.2).
+ *   chunk    text bytes one scan thread handles before it moves on, or 0.
+ */
+typedef struct {
+    int q;
+    int sigma_r;
+    int k;
+    int map_kind;
+    int map_shift;
+    int table_place;
+    int smag;
+    int chunk;
+} mpm_params;
+
+/* Sizes that follow from resolved parameters and m (Sections 3.1, 3.2). */
+typedef struct {
+    int L;             /* common q-gram length of the q shifted patterns, L'  */
+    int mprime;        /* AOSO subpattern length m' = floor(min(L',64)/k)     */
+    int positions;     /* filter positions m'' = k * m' (<= 64)               */
+    int entry_bytes;   /* bytes per mask-table entry: 1, 2, 4 or 8            */
+    uint64_t entries;  /* sigma_r^q                                           */
+    uint64_t table_bytes;
+    double est_candidate_rate; /* estimated candidate records per sampled q-gram,
+                                  from the pattern-set symbol frequencies       */
+} mpm_table_info;
+
+/* Counters of the last mpm_search / mpm_scan on a handle. */
+typedef struct {
+    uint64_t n;            /* text bytes                                      */
+    uint64_t sampled;      /* sampled q-grams read by the scan                */
+    uint64_t candidates;   /* candidate records (sampled q-grams that fired)  */
+    uint64_t z;            /* occurrences found                               */
+    uint32_t launches;     /* kernels launched by the call                    */
+    uint32_t retries;      /* re-runs after growing an internal buffer        */
+} mpm_stats;
+
+typedef struct mpm_handle mpm_handle;
+
+/* ------------------------------------------------------------ core calls */
+
+/*
+ * Builds the filter for r patterns of length m (row-major, r*m bytes of host
+ * memory at P; copied, the caller keeps ownership).  sigma is the declared
+ * alphabet size (1..256; used to choose parameters and to validate
+ * sigma_r <= max(2, sigma) when sigma_r is given).  params may be NULL (all
+ * automatic).  Host work (Sections 2, 3.2, 3.3): pattern histogram, mapping
+ * mu, the q shifts of every pattern cut into non-overlapping q-grams, their
+ * superimposition into the mask table, and a hash of the patterns for
+ * verification; then one upload to the device, which the handle owns.
+ * Returns NULL on error (mpm_last_error(): MPM_EINVAL, MPM_ENOMEM, MPM_ECUDA).
+ */
+mpm_handle *mpm_build(const uint8_t *P, size_t r, size_t m, int sigma,
+                      const mpm_params *params);
+
+/*
+ * Finds all occurrences in T[0..n).  T may be device or host memory (host
+ * text is copied to a device buffer the handle owns).  out_pos / out_pid
+ * receive the sorted occurrence list and may be device or host memory; *z is
+ * in: their capacity (entries), out: the number of occurrences.  When that
+ * number exceeds the capacity the call returns MPM_ECAPACITY, sets *z to the
+ * required count and the outputs hold nothing valid.  Blocks the calling
+ * host thread until the occurrence count is known (one 16-byte read-back);
+ * device outputs are complete when the handle's stream is.  Steps (Sections
+ * 3.1, 3.2): one fused encode+scan kernel (or SMAG encode then scan), one
+ * verification kernel, one sort.  Concurrent calls on the same handle race.
+ */
+int mpm_search(mpm_handle *h, const uint8_t *T, size_t n, uint32_t *out_pos,
+               uint32_t *out_pid, size_t *z);
+
+/* Releases the handle and all its device memory (after synchronizing its
+ * stream).  NULL is ignored. */
+void mpm_free(mpm_handle *h);
+
+/* Last error code set on the calling thread. */
+int mpm_last_error(void);
+
+/* Static description of an error code. */
+const char *mpm_strerror(int code);
+
+/* Sets the CUDA stream (a cudaStream_t, e.g. PyTorch's current stream) on
+ * which the handle enqueues all later work.  NULL selects stream 0. */
+int mpm_set_stream(mpm_handle *h, void *stream);
+
+/* The parameters the handle resolved (no zeros / negatives left) and the
+ * sizes that follow from them; info may be NULL. */
+int mpm_get_params(const mpm_handle *h, mpm_params *out, mpm_table_info *info);
+
+/* Counters of the last search or scan on this handle. */
+int mpm_get_stats(const mpm_handle *h, mpm_stats *out);
+
+/* ---------------------------------------------- host-only planning calls */
+
+/*
+ * Resolves automatic parameters exactly as mpm_build would, without any GPU
+ * work.  P, r, m, sigma and in are as for mpm_build; out receives the
+ * resolved parameters and info (may be NULL) the derived sizes.
+ */
+int mpm_plan(const uint8_t *P, size_t r, size_t m, int sigma, const mpm_params *in,
+             mpm_params *out, mpm_table_info *info);
+
+/*
+ * Builds, on the host only, the tables mpm_build would upload: mu[256] (the
+ * byte -> reduced symbol map, Section 3.3) and the Shift-Or mask table
+ * (Sections 2, 3.2): entry c (q-gram code, first symbol most significant,
+ * c = sum_t mu(S[t]) * sigma_r^(q-1-t)), entry_bytes little-endian bytes,
+ * bit p (p < positions) is 0 iff some pattern, at some shift s < q, has code
+ * c as its p-th non-overlapping q-gram; bits >= positions are 1.  table
+ * (host memory) must hold table_bytes bytes (mpm_plan); mu or table may be
+ * NULL to skip them.
+ */
+int mpm_host_tables(const uint8_t *P, size_t r, size_t m, int sigma,
+                    const mpm_params *params, uint8_t *mu, void *table,
+                    size_t table_bytes);
+
+/* ----------------------------------------------- single steps of a search */
+
+/*
+ * SMAG encode (Section 3.2): codes[h] = code of text q-gram h (bytes
+ * T[hq..hq+q), mu applied, first symbol most significant) for
+ * h < floor(n/q).  T and codes are device pointers; codes holds
+ * floor(n/q) uint32 entries.
+ */
+int mpm_encode(mpm_handle *h, const uint8_t *T, size_t n, uint32_t *codes);
+
+/*
+ * The filter alone (Sections 3.1, 3.2): the AOSO Shift-Or scan of the
+ * sampled q-grams h = k-1 (mod k) of T (device), with candidate compaction.
+ * Each record is ((uint64)fired << 32) | h where h is the sampled q-gram
+ * index and bit j of fired says subpattern j matched, i.e. the window of
+ * q-grams starting at h - (m'-1)k - j is a candidate.  Records come in no
+ * particular order.  *count is in: capacity of cand (device, entries), out:
+ * number of records (MPM_ECAPACITY if it exceeds the capacity).
+ */
+int mpm_scan(mpm_handle *h, const uint8_t *T, size_t n, uint64_t *cand,
+             size_t *count);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MPM_H */

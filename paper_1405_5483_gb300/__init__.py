@@ -1,0 +1,195 @@
+"""Exact multiple pattern matching on GB300: MAG / SMAG (arXiv 1405.5483).
+
+A thin Python binding of the C ABI in include/mpm.h: every step of a search
+runs in the library's CUDA kernels; this module only marshals arguments.
+PyTorch supplies device memory and the current CUDA stream.
+
+    import paper_1405_5483_gb300 as mpm
+    m = mpm.Matcher(P, sigma=20)          # P: uint8 (r, m), host memory
+    pos, pid = m.search(T)                # T: uint8 CUDA tensor (or numpy)
+"""
+import ctypes
+
+import numpy as np
+
+from ._native import (MAP_AUTO, MAP_GREEDY, MAP_LOWBITS, MAP_RANK, MPM_ECAPACITY,  # noqa: F401
+                      MPM_EINVAL, MPM_OK, TABLE_AUTO, TABLE_GLOBAL, TABLE_SMEM, MpmError,
+                      Params, Stats, TableInfo, declared_functions, lib)
+
+__all__ = ["Matcher", "plan", "host_tables", "MpmError", "lib", "declared_functions"]
+
+
+def _torch():
+    import torch
+    return torch
+
+
+def make_params(q=0, sigma_r=0, k=0, map_kind=MAP_AUTO, map_shift=-1, table_place=TABLE_AUTO,
+                smag=0, chunk=0):
+    return Params(q, sigma_r, k, map_kind, map_shift, table_place, smag, chunk)
+
+
+def _patterns(P):
+    if isinstance(P, (list, tuple)):
+        P = np.stack([np.frombuffer(bytes(p), np.uint8) for p in P])
+    if hasattr(P, "detach"):
+        P = P.detach().cpu().numpy()
+    P = np.ascontiguousarray(np.asarray(P, dtype=np.uint8))
+    if P.ndim != 2:
+        raise ValueError("patterns must be an (r, m) uint8 array")
+    return P
+
+
+def plan(P, sigma, **kw):
+    """Parameters mpm_build would choose, and the sizes that follow (host only)."""
+    P = _patterns(P)
+    out, info = Params(), TableInfo()
+    rc = lib().mpm_plan(P.ctypes.data, P.shape[0], P.shape[1], sigma,
+                        ctypes.byref(make_params(**kw)), ctypes.byref(out), ctypes.byref(info))
+    if rc:
+        raise MpmError(rc, "mpm_plan")
+    return out.as_dict(), info.as_dict()
+
+
+def host_tables(P, sigma, **kw):
+    """(mu uint8[256], mask table uint8[table_bytes], info) built on the host."""
+    P = _patterns(P)
+    params, info = plan(P, sigma, **kw)
+    mu = np.zeros(256, np.uint8)
+    table = np.zeros(int(info["table_bytes"]), np.uint8)
+    rc = lib().mpm_host_tables(P.ctypes.data, P.shape[0], P.shape[1], sigma,
+                               ctypes.byref(make_params(**kw)), mu.ctypes.data,
+                               table.ctypes.data, table.size)
+    if rc:
+        raise MpmError(rc, "mpm_host_tables")
+    return mu, table, dict(info, **params)
+
+
+def _ptr(x):
+    if x is None:
+        return None
+    if hasattr(x, "data_ptr"):
+        return x.data_ptr()
+    return x.ctypes.data
+
+
+def _numel(x):
+    return x.numel() if hasattr(x, "numel") else x.size
+
+
+class Matcher:
+    """A built pattern set (mpm_build) and searches over texts (mpm_search)."""
+
+    def __init__(self, P, sigma=256, **params):
+        P = _patterns(P)
+        self.r, self.m = P.shape
+        self.sigma = sigma
+        self._h = lib().mpm_build(P.ctypes.data, self.r, self.m, sigma,
+                                  ctypes.byref(make_params(**params)))
+        if not self._h:
+            raise MpmError(lib().mpm_last_error(), "mpm_build")
+        self._cap = max(1024, 4 * self.r)
+
+    # -------------------------------------------------------------- info
+    @property
+    def params(self):
+        p, i = Params(), TableInfo()
+        self._check(lib().mpm_get_params(self._h, ctypes.byref(p), ctypes.byref(i)), "params")
+        return p.as_dict()
+
+    @property
+    def info(self):
+        p, i = Params(), TableInfo()
+        self._check(lib().mpm_get_params(self._h, ctypes.byref(p), ctypes.byref(i)), "params")
+        return i.as_dict()
+
+    @property
+    def stats(self):
+        s = Stats()
+        self._check(lib().mpm_get_stats(self._h, ctypes.byref(s)), "stats")
+        return s.as_dict()
+
+    def _check(self, rc, what):
+        if rc:
+            raise MpmError(rc, what)
+
+    def _stream(self, T):
+        if hasattr(T, "is_cuda") and T.is_cuda:
+            torch = _torch()
+            lib().mpm_set_stream(self._h, ctypes.c_void_p(torch.cuda.current_stream().cuda_stream))
+        else:
+            lib().mpm_set_stream(self._h, None)
+
+    # ------------------------------------------------------------ search
+    def search_into(self, T, out_pos, out_pid):
+        """Writes the sorted occurrences into out_pos/out_pid (device or host,
+        32-bit); returns z.  Raises MpmError(MPM_ECAPACITY) with .z set when
+        they are too small."""
+        self._stream(T)
+        z = ctypes.c_size_t(min(_numel(out_pos), _numel(out_pid)))
+        rc = lib().mpm_search(self._h, _ptr(T), _numel(T), _ptr(out_pos), _ptr(out_pid),
+                              ctypes.byref(z))
+        if rc:
+            e = MpmError(rc, "mpm_search")
+            e.z = z.value
+            raise e
+        return z.value
+
+    def search(self, T):
+        """All occurrences in T as (pos, pid), 32-bit, sorted by (pos, pid).
+        CUDA tensor in -> int32 CUDA tensors out (values are unsigned);
+        numpy in -> uint32 numpy out."""
+        on_dev = hasattr(T, "is_cuda") and T.is_cuda
+        while True:
+            if on_dev:
+                torch = _torch()
+                pos = torch.empty(self._cap, dtype=torch.int32, device=T.device)
+                pid = torch.empty(self._cap, dtype=torch.int32, device=T.device)
+            else:
+                T = np.ascontiguousarray(np.asarray(T, dtype=np.uint8))
+                pos = np.empty(self._cap, np.uint32)
+                pid = np.empty(self._cap, np.uint32)
+            try:
+                z = self.search_into(T, pos, pid)
+            except MpmError as e:
+                if e.code == MPM_ECAPACITY:
+                    self._cap = int(e.z) + 1024
+                    continue
+                raise
+            return pos[:z], pid[:z]
+
+    def scan(self, T, cap=None):
+        """The filter alone: candidate records ((fired << 32) | h) as an int64
+        CUDA tensor, in no particular order."""
+        torch = _torch()
+        cap = cap or max(1 << 16, _numel(T) // 16)
+        while True:
+            cand = torch.empty(cap, dtype=torch.int64, device=T.device)
+            self._stream(T)
+            cnt = ctypes.c_size_t(cap)
+            rc = lib().mpm_scan(self._h, _ptr(T), _numel(T), _ptr(cand), ctypes.byref(cnt))
+            if rc == MPM_ECAPACITY:
+                cap = int(cnt.value) + 1024
+                continue
+            self._check(rc, "mpm_scan")
+            return cand[:cnt.value]
+
+    def encode(self, T):
+        """SMAG encoding: the code of every non-overlapping q-gram of T."""
+        torch = _torch()
+        q = self.params["q"]
+        codes = torch.empty(max(1, _numel(T) // q), dtype=torch.int32, device=T.device)
+        self._stream(T)
+        self._check(lib().mpm_encode(self._h, _ptr(T), _numel(T), _ptr(codes)), "mpm_encode")
+        return codes[: _numel(T) // q]
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().mpm_free(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

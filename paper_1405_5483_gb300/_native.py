@@ -1,0 +1,100 @@
+"""ctypes declarations of the C ABI in include/mpm.h.
+
+Loads paper_1405_5483_gb300/_build/libmpm.so and fails loudly when it is
+missing: there is no other implementation to fall back to.
+"""
+import ctypes
+import os
+import re
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "_build", "libmpm.so")
+HEADER = os.path.join(os.path.dirname(HERE), "include", "mpm.h")
+
+MPM_OK, MPM_EINVAL, MPM_ENOMEM, MPM_ECUDA, MPM_ECAPACITY, MPM_ETIMEOUT, MPM_ENOTSUP = range(7)
+MAP_AUTO, MAP_RANK, MAP_GREEDY, MAP_LOWBITS = range(4)
+TABLE_AUTO, TABLE_SMEM, TABLE_GLOBAL = range(3)
+
+
+class Params(ctypes.Structure):
+    _fields_ = [("q", ctypes.c_int), ("sigma_r", ctypes.c_int), ("k", ctypes.c_int),
+                ("map_kind", ctypes.c_int), ("map_shift", ctypes.c_int),
+                ("table_place", ctypes.c_int), ("smag", ctypes.c_int), ("chunk", ctypes.c_int)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+class TableInfo(ctypes.Structure):
+    _fields_ = [("L", ctypes.c_int), ("mprime", ctypes.c_int), ("positions", ctypes.c_int),
+                ("entry_bytes", ctypes.c_int), ("entries", ctypes.c_uint64),
+                ("table_bytes", ctypes.c_uint64), ("est_candidate_rate", ctypes.c_double)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+class Stats(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_uint64), ("sampled", ctypes.c_uint64),
+                ("candidates", ctypes.c_uint64), ("z", ctypes.c_uint64),
+                ("launches", ctypes.c_uint32), ("retries", ctypes.c_uint32)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+class MpmError(RuntimeError):
+    def __init__(self, code, what=""):
+        self.code = code
+        super().__init__("%s: %s (code %d)" % (what, _strerror(code), code))
+
+
+_lib = None
+
+
+def _strerror(code):
+    try:
+        return lib().mpm_strerror(code).decode()
+    except Exception:
+        return "error"
+
+
+def lib():
+    """The loaded libmpm.so (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise ImportError("libmpm.so is not built (%s); run __graft_entry__.build() or "
+                          "python -m paper_1405_5483_gb300.build_lib" % LIB_PATH)
+    L = ctypes.CDLL(LIB_PATH)
+    vp, sz, u8p = ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p
+    Pp, Ip, Sp = ctypes.POINTER(Params), ctypes.POINTER(TableInfo), ctypes.POINTER(Stats)
+    szp = ctypes.POINTER(ctypes.c_size_t)
+    sig = {
+        "mpm_build": (vp, [u8p, sz, sz, ctypes.c_int, Pp]),
+        "mpm_search": (ctypes.c_int, [vp, u8p, sz, vp, vp, szp]),
+        "mpm_free": (None, [vp]),
+        "mpm_last_error": (ctypes.c_int, []),
+        "mpm_strerror": (ctypes.c_char_p, [ctypes.c_int]),
+        "mpm_set_stream": (ctypes.c_int, [vp, vp]),
+        "mpm_get_params": (ctypes.c_int, [vp, Pp, Ip]),
+        "mpm_get_stats": (ctypes.c_int, [vp, Sp]),
+        "mpm_plan": (ctypes.c_int, [u8p, sz, sz, ctypes.c_int, Pp, Pp, Ip]),
+        "mpm_host_tables": (ctypes.c_int, [u8p, sz, sz, ctypes.c_int, Pp, vp, vp, sz]),
+        "mpm_encode": (ctypes.c_int, [vp, u8p, sz, vp]),
+        "mpm_scan": (ctypes.c_int, [vp, u8p, sz, vp, szp]),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(L, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = L
+    return L
+
+
+def declared_functions():
+    """Names of the functions include/mpm.h declares."""
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(mpm_[a-z_0-9]+)\s*\(", text)))

@@ -1,0 +1,450 @@
+// C ABI: handle life cycle and the orchestration of one search.
+//
+// mpm_search enqueues, on the handle's stream: the counter reset, the MAG
+// scan (or SMAG encode + scan), the verification kernel and a 16-byte
+// read-back of the counters; it waits for that read-back, grows an internal
+// buffer and re-runs if one overflowed, then enqueues the sort that writes
+// the caller's outputs.
+#include <algorithm>
+#include <cstdio>
+#include <cstring>
+#include <new>
+
+#include "kernels.h"
+
+struct mpm_handle {
+    mpm::Plan plan;
+    mpm::HostTables host;
+    int device = 0;
+    int num_sms = 0;
+    cudaStream_t stream = nullptr;
+
+    uint8_t* d_mu = nullptr;
+    void* d_table = nullptr;
+    uint32_t table_bytes_padded = 0;
+    mpm::Slot* d_slots = nullptr;
+    uint8_t* d_pat = nullptr;
+    uint32_t* d_pid = nullptr;
+
+    // scratch, grown on demand
+    uint64_t* d_cand = nullptr;
+    size_t cand_cap = 0;
+    uint64_t* d_occ = nullptr;
+    uint64_t* d_occ_tmp = nullptr;
+    size_t occ_cap = 0;
+    uint32_t* d_hist = nullptr;
+    size_t hist_cap = 0;
+    uint32_t* d_counters = nullptr;
+    uint32_t* h_counters = nullptr;  // pinned
+    uint8_t* d_text = nullptr;       // staging for host text
+    size_t text_cap = 0;
+    uint32_t* d_codes = nullptr;     // SMAG codes
+    size_t codes_cap = 0;
+    uint32_t* d_out = nullptr;       // staging for host outputs (pos | pid)
+    size_t out_cap = 0;
+
+    mpm_stats stats{};
+};
+
+namespace mpm {
+
+static thread_local int t_last_error = MPM_OK;
+
+int set_error(int code) {
+    t_last_error = code;
+    return code;
+}
+
+}  // namespace mpm
+
+namespace {
+
+using mpm::set_error;
+
+template <typename T>
+int grow(T** p, size_t* cap, size_t want) {
+    if (*cap >= want && *p) return MPM_OK;
+    if (*p) cudaFree(*p);
+    *p = nullptr;
+    *cap = 0;
+    size_t n = std::max<size_t>(want, 16);
+    if (cudaMalloc(reinterpret_cast<void**>(p), n * sizeof(T)) != cudaSuccess) {
+        cudaGetLastError();
+        return MPM_ENOMEM;
+    }
+    *cap = n;
+    return MPM_OK;
+}
+
+bool is_device_ptr(const void* p) {
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+mpm::FilterDev filter_dev(const mpm_handle* h) {
+    mpm::FilterDev f;
+    f.table = h->d_table;
+    f.table_bytes = h->table_bytes_padded;
+    f.entry_bytes = h->plan.info.entry_bytes;
+    f.smem_table = h->plan.p.table_place == MPM_TABLE_SMEM;
+    f.mu = h->d_mu;
+    f.map_kind = h->plan.p.map_kind;
+    f.q = h->plan.p.q;
+    f.k = h->plan.p.k;
+    f.ell = h->plan.ell;
+    f.shift = h->plan.p.map_shift;
+    f.mprime = h->plan.info.mprime;
+    f.positions = h->plan.info.positions;
+    return f;
+}
+
+void release(mpm_handle* h) {
+    if (!h) return;
+    if (h->stream) cudaStreamSynchronize(h->stream);
+    else cudaDeviceSynchronize();
+    cudaFree(h->d_mu);
+    cudaFree(h->d_table);
+    cudaFree(h->d_slots);
+    cudaFree(h->d_pat);
+    cudaFree(h->d_pid);
+    cudaFree(h->d_cand);
+    cudaFree(h->d_occ);
+    cudaFree(h->d_occ_tmp);
+    cudaFree(h->d_hist);
+    cudaFree(h->d_counters);
+    if (h->h_counters) cudaFreeHost(h->h_counters);
+    cudaFree(h->d_text);
+    cudaFree(h->d_codes);
+    cudaFree(h->d_out);
+    cudaGetLastError();
+    delete h;
+}
+
+int bits_for(uint64_t v) {
+    int b = 0;
+    while (b < 64 && (v >> b)) b++;
+    return b;
+}
+
+// Scan + verify on device text; leaves counters in h->h_counters.
+int run_filter(mpm_handle* h, const uint8_t* dT, uint32_t n, int* launches) {
+    cudaStream_t s = h->stream;
+    const mpm::FilterDev f = filter_dev(h);
+    if (cudaMemsetAsync(h->d_counters, 0, mpm::kNumCounters * sizeof(uint32_t), s) != cudaSuccess)
+        return MPM_ECUDA;
+    int l;
+    if (h->plan.p.smag) {
+        const size_t nq = n / (uint32_t)f.q;
+        if (grow(&h->d_codes, &h->codes_cap, nq)) return MPM_ENOMEM;
+        l = mpm::launch_encode(dT, n, f, h->d_codes, s);
+        if (l < 0) return MPM_ECUDA;
+        *launches += l;
+        l = mpm::launch_scan_codes(h->d_codes, (uint32_t)nq, f, h->d_cand, (uint32_t)h->cand_cap,
+                                   h->d_counters, s);
+    } else {
+        mpm::ScanArgs a{};
+        a.T = dT;
+        a.n = n;
+        a.f = f;
+        a.P = (uint32_t)(f.k * f.q);
+        const uint32_t wb = (uint32_t)(f.mprime - 1) * a.P;
+        a.warm_bytes = (wb + 3) & ~3u;
+        a.cand = h->d_cand;
+        a.cap = (uint32_t)h->cand_cap;
+        a.counters = h->d_counters;
+        l = mpm::launch_scan(a, h->num_sms, h->plan.p.chunk, s);
+        if (l == -2) return MPM_ENOTSUP;
+    }
+    if (l < 0) return MPM_ECUDA;
+    *launches += l;
+    mpm::VerifyArgs v{};
+    v.T = dT;
+    v.n = n;
+    v.m = (uint32_t)h->plan.m;
+    v.q = f.q;
+    v.k = f.k;
+    v.mprime = f.mprime;
+    v.cand = h->d_cand;
+    v.cand_cap = (uint32_t)h->cand_cap;
+    v.slots = h->d_slots;
+    v.slot_mask = (uint32_t)h->host.slots.size() - 1;
+    v.pat = h->d_pat;
+    v.pid = h->d_pid;
+    v.key_bytes = h->host.key_bytes;
+    v.occ = h->d_occ;
+    v.occ_cap = (uint32_t)h->occ_cap;
+    v.counters = h->d_counters;
+    if (n >= h->plan.m) {
+        if (mpm::launch_verify(v, h->num_sms, s) < 0) return MPM_ECUDA;
+        *launches += 1;
+    }
+    if (cudaMemcpyAsync(h->h_counters, h->d_counters, mpm::kNumCounters * sizeof(uint32_t),
+                        cudaMemcpyDeviceToHost, s) != cudaSuccess)
+        return MPM_ECUDA;
+    if (cudaStreamSynchronize(s) != cudaSuccess) return MPM_ECUDA;
+    if (h->h_counters[mpm::kErrorFlag]) return (int)h->h_counters[mpm::kErrorFlag];
+    return MPM_OK;
+}
+
+int prepare(mpm_handle* h) {
+    cudaError_t e = cudaSetDevice(h->device);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return MPM_ECUDA;
+    }
+    return MPM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int mpm_last_error(void) { return mpm::t_last_error; }
+
+const char* mpm_strerror(int code) {
+    switch (code) {
+        case MPM_OK: return "ok";
+        case MPM_EINVAL: return "invalid argument or infeasible parameter";
+        case MPM_ENOMEM: return "out of memory";
+        case MPM_ECUDA: return "CUDA error (no device, launch or copy failure)";
+        case MPM_ECAPACITY: return "output capacity too small";
+        case MPM_ETIMEOUT: return "bounded device wait timed out";
+        case MPM_ENOTSUP: return "unsupported combination";
+        default: return "unknown error";
+    }
+}
+
+mpm_handle* mpm_build(const uint8_t* P, size_t r, size_t m, int sigma, const mpm_params* params) {
+    mpm_handle* h = new (std::nothrow) mpm_handle();
+    if (!h) {
+        set_error(MPM_ENOMEM);
+        return nullptr;
+    }
+    int rc = mpm::make_plan(P, r, m, sigma, params, &h->plan);
+    if (rc) {
+        delete h;
+        set_error(rc);
+        return nullptr;
+    }
+    // host tables
+    try {
+        mpm::make_mu(P, r, m, h->plan.p.map_kind, h->plan.p.sigma_r, h->plan.p.map_shift,
+                     h->host.mu);
+        h->table_bytes_padded = (uint32_t)((h->plan.info.table_bytes + 15) & ~uint64_t(15));
+        h->host.table.assign(h->table_bytes_padded, 0xFF);
+        mpm::make_mask_table(P, h->plan, h->host.mu, h->host.table.data());
+        mpm::make_verify_tables(P, r, m, &h->host);
+    } catch (const std::bad_alloc&) {
+        delete h;
+        set_error(MPM_ENOMEM);
+        return nullptr;
+    }
+    if (cudaGetDevice(&h->device) != cudaSuccess ||
+        cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, h->device) !=
+            cudaSuccess) {
+        cudaGetLastError();
+        delete h;
+        set_error(MPM_ECUDA);
+        return nullptr;
+    }
+    bool ok = cudaMalloc(&h->d_mu, 256) == cudaSuccess &&
+              cudaMalloc(&h->d_table, h->table_bytes_padded) == cudaSuccess &&
+              cudaMalloc(&h->d_slots, h->host.slots.size() * sizeof(mpm::Slot)) == cudaSuccess &&
+              cudaMalloc(&h->d_pat, h->host.sorted_pat.size()) == cudaSuccess &&
+              cudaMalloc(&h->d_pid, h->host.sorted_pid.size() * 4) == cudaSuccess &&
+              cudaMalloc(&h->d_counters, mpm::kNumCounters * 4) == cudaSuccess &&
+              cudaMallocHost(&h->h_counters, mpm::kNumCounters * 4) == cudaSuccess;
+    ok = ok && cudaMemcpy(h->d_mu, h->host.mu, 256, cudaMemcpyHostToDevice) == cudaSuccess &&
+         cudaMemcpy(h->d_table, h->host.table.data(), h->table_bytes_padded,
+                    cudaMemcpyHostToDevice) == cudaSuccess &&
+         cudaMemcpy(h->d_slots, h->host.slots.data(), h->host.slots.size() * sizeof(mpm::Slot),
+                    cudaMemcpyHostToDevice) == cudaSuccess &&
+         cudaMemcpy(h->d_pat, h->host.sorted_pat.data(), h->host.sorted_pat.size(),
+                    cudaMemcpyHostToDevice) == cudaSuccess &&
+         cudaMemcpy(h->d_pid, h->host.sorted_pid.data(), h->host.sorted_pid.size() * 4,
+                    cudaMemcpyHostToDevice) == cudaSuccess;
+    if (!ok) {
+        cudaGetLastError();
+        release(h);
+        set_error(MPM_ECUDA);
+        return nullptr;
+    }
+    h->host.table.clear();
+    h->host.table.shrink_to_fit();
+    set_error(MPM_OK);
+    return h;
+}
+
+void mpm_free(mpm_handle* h) { release(h); }
+
+int mpm_set_stream(mpm_handle* h, void* stream) {
+    if (!h) return set_error(MPM_EINVAL);
+    h->stream = reinterpret_cast<cudaStream_t>(stream);
+    return set_error(MPM_OK);
+}
+
+int mpm_get_params(const mpm_handle* h, mpm_params* out, mpm_table_info* info) {
+    if (!h || !out) return set_error(MPM_EINVAL);
+    *out = h->plan.p;
+    if (info) *info = h->plan.info;
+    return set_error(MPM_OK);
+}
+
+int mpm_get_stats(const mpm_handle* h, mpm_stats* out) {
+    if (!h || !out) return set_error(MPM_EINVAL);
+    *out = h->stats;
+    return set_error(MPM_OK);
+}
+
+int mpm_search(mpm_handle* h, const uint8_t* T, size_t n, uint32_t* out_pos, uint32_t* out_pid,
+               size_t* z) {
+    if (!h || !z || (n > 0 && !T) || n >= (1ull << 32)) return set_error(MPM_EINVAL);
+    if (*z > 0 && (!out_pos || !out_pid)) return set_error(MPM_EINVAL);
+    int rc = prepare(h);
+    if (rc) return set_error(rc);
+    const size_t out_capacity = *z;
+    h->stats = mpm_stats{};
+    h->stats.n = n;
+    const uint32_t q = (uint32_t)h->plan.p.q, k = (uint32_t)h->plan.p.k;
+    h->stats.sampled = (n / q) / k;
+    int launches = 0;
+    if (n < h->plan.m) {
+        *z = 0;
+        return set_error(MPM_OK);
+    }
+    // the text on the device
+    const uint8_t* dT = T;
+    if (!is_device_ptr(T)) {
+        if (grow(&h->d_text, &h->text_cap, n)) return set_error(MPM_ENOMEM);
+        if (cudaMemcpyAsync(h->d_text, T, n, cudaMemcpyHostToDevice, h->stream) != cudaSuccess)
+            return set_error(MPM_ECUDA);
+        dT = h->d_text;
+    }
+    // first-call capacities: a candidate rate of 1/64 per byte, 64K occurrences
+    if (grow(&h->d_cand, &h->cand_cap, std::max<size_t>(1 << 16, n / 64 + 1024)))
+        return set_error(MPM_ENOMEM);
+    if (!h->d_occ || h->occ_cap < (1u << 16)) {
+        size_t c = 0;
+        if (grow(&h->d_occ, &h->occ_cap, 1 << 16) || grow(&h->d_occ_tmp, &c, 1 << 16))
+            return set_error(MPM_ENOMEM);
+    }
+    for (int attempt = 0;; attempt++) {
+        rc = run_filter(h, dT, (uint32_t)n, &launches);
+        if (rc) return set_error(rc);
+        const uint32_t nc = h->h_counters[mpm::kCandCount];
+        const uint32_t nz = h->h_counters[mpm::kOccCount];
+        bool again = false;
+        if (nc > h->cand_cap) {
+            if (grow(&h->d_cand, &h->cand_cap, (size_t)nc + nc / 4 + 1024))
+                return set_error(MPM_ENOMEM);
+            again = true;
+        }
+        if (nz > h->occ_cap) {
+            size_t want = (size_t)nz + nz / 4 + 1024, c2 = 0;
+            cudaFree(h->d_occ_tmp);
+            h->d_occ_tmp = nullptr;
+            if (grow(&h->d_occ, &h->occ_cap, want) || grow(&h->d_occ_tmp, &c2, want))
+                return set_error(MPM_ENOMEM);
+            again = true;
+        }
+        if (!again) break;
+        h->stats.retries++;
+        if (attempt > 4) return set_error(MPM_ENOMEM);
+    }
+    const uint32_t zz = h->h_counters[mpm::kOccCount];
+    h->stats.candidates = h->h_counters[mpm::kCandCount];
+    h->stats.z = zz;
+    *z = zz;
+    if (zz > out_capacity) {
+        h->stats.launches = launches;
+        return set_error(MPM_ECAPACITY);
+    }
+    if (zz > 0) {
+        if (grow(&h->d_hist, &h->hist_cap, mpm::sort_hist_entries(zz))) return set_error(MPM_ENOMEM);
+        const bool dev_out = is_device_ptr(out_pos) && is_device_ptr(out_pid);
+        uint32_t* op = out_pos;
+        uint32_t* oi = out_pid;
+        if (!dev_out) {
+            if (grow(&h->d_out, &h->out_cap, 2 * (size_t)zz)) return set_error(MPM_ENOMEM);
+            op = h->d_out;
+            oi = h->d_out + zz;
+        }
+        const uint32_t key_bits =
+            ((uint32_t)bits_for(n) << 16) | (uint32_t)bits_for(h->plan.r > 1 ? h->plan.r - 1 : 1);
+        int l = mpm::launch_sort_output(h->d_occ, h->d_occ_tmp, h->d_hist, h->hist_cap, zz,
+                                        key_bits, op, oi, h->stream);
+        if (l < 0) return set_error(MPM_ECUDA);
+        launches += l;
+        if (!dev_out) {
+            if (cudaMemcpyAsync(out_pos, op, (size_t)zz * 4, cudaMemcpyDeviceToHost, h->stream) !=
+                    cudaSuccess ||
+                cudaMemcpyAsync(out_pid, oi, (size_t)zz * 4, cudaMemcpyDeviceToHost, h->stream) !=
+                    cudaSuccess ||
+                cudaStreamSynchronize(h->stream) != cudaSuccess)
+                return set_error(MPM_ECUDA);
+        }
+    }
+    h->stats.launches = launches;
+    return set_error(MPM_OK);
+}
+
+int mpm_encode(mpm_handle* h, const uint8_t* T, size_t n, uint32_t* codes) {
+    if (!h || (n > 0 && (!T || !codes)) || n >= (1ull << 32)) return set_error(MPM_EINVAL);
+    int rc = prepare(h);
+    if (rc) return set_error(rc);
+    const mpm::FilterDev f = filter_dev(h);
+    int l = mpm::launch_encode(T, (uint32_t)n, f, codes, h->stream);
+    if (l < 0) return set_error(MPM_ECUDA);
+    if (cudaStreamSynchronize(h->stream) != cudaSuccess) return set_error(MPM_ECUDA);
+    return set_error(MPM_OK);
+}
+
+int mpm_scan(mpm_handle* h, const uint8_t* T, size_t n, uint64_t* cand, size_t* count) {
+    if (!h || !count || (n > 0 && !T) || n >= (1ull << 32)) return set_error(MPM_EINVAL);
+    if (*count > 0 && !cand) return set_error(MPM_EINVAL);
+    int rc = prepare(h);
+    if (rc) return set_error(rc);
+    cudaStream_t s = h->stream;
+    const mpm::FilterDev f = filter_dev(h);
+    if (cudaMemsetAsync(h->d_counters, 0, mpm::kNumCounters * 4, s) != cudaSuccess)
+        return set_error(MPM_ECUDA);
+    int l = 0;
+    if (h->plan.p.smag) {
+        const size_t nq = n / (uint32_t)f.q;
+        if (grow(&h->d_codes, &h->codes_cap, nq)) return set_error(MPM_ENOMEM);
+        if (mpm::launch_encode(T, (uint32_t)n, f, h->d_codes, s) < 0) return set_error(MPM_ECUDA);
+        l = mpm::launch_scan_codes(h->d_codes, (uint32_t)nq, f, cand, (uint32_t)*count,
+                                   h->d_counters, s);
+    } else {
+        mpm::ScanArgs a{};
+        a.T = T;
+        a.n = (uint32_t)n;
+        a.f = f;
+        a.P = (uint32_t)(f.k * f.q);
+        const uint32_t wb = (uint32_t)(f.mprime - 1) * a.P;
+        a.warm_bytes = (wb + 3) & ~3u;
+        a.cand = cand;
+        a.cap = (uint32_t)*count;
+        a.counters = h->d_counters;
+        l = mpm::launch_scan(a, h->num_sms, h->plan.p.chunk, s);
+        if (l == -2) return set_error(MPM_ENOTSUP);
+    }
+    if (l < 0) return set_error(MPM_ECUDA);
+    if (cudaMemcpyAsync(h->h_counters, h->d_counters, mpm::kNumCounters * 4,
+                        cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess)
+        return set_error(MPM_ECUDA);
+    if (h->h_counters[mpm::kErrorFlag]) return set_error((int)h->h_counters[mpm::kErrorFlag]);
+    const size_t cap = *count;
+    *count = h->h_counters[mpm::kCandCount];
+    h->stats = mpm_stats{};
+    h->stats.n = n;
+    h->stats.candidates = *count;
+    return set_error(*count > cap ? MPM_ECAPACITY : MPM_OK);
+}
+
+}  // extern "C"

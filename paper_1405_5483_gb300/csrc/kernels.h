@@ -1,0 +1,86 @@
+// Launch interfaces of the search kernels (host side).
+#pragma once
+
+#include <cstdint>
+#include <cuda.h>
+#include <cuda_runtime.h>
+
+#include "mpm_internal.h"
+
+namespace mpm {
+
+// Indices into the per-search counter block in device memory.
+enum Counter : int {
+    kCandCount = 0,   // candidate records produced by the scan
+    kOccCount = 1,    // occurrences produced by verification
+    kErrorFlag = 2,   // MPM_ETIMEOUT when a bounded wait gave up
+    kNumCounters = 4
+};
+
+// Filter description shared by the scan, encode and verify kernels.
+struct FilterDev {
+    const void* table;        // mask table, global memory
+    uint32_t table_bytes;     // padded to a multiple of 16
+    int entry_bytes;          // 1, 2, 4 or 8
+    int smem_table;           // copy the table into shared memory
+    const uint8_t* mu;        // 256-entry byte -> reduced symbol map
+    int map_kind, q, k, ell, shift, mprime, positions;
+};
+
+// The scan's view of one text.
+struct ScanArgs {
+    const uint8_t* T;
+    uint32_t n;
+    FilterDev f;
+    uint32_t P;           // k * q, bytes per sampled q-gram period
+    // rows handled through TMA: R rows of Lst bytes, in groups of 32
+    uint32_t Lst, R, RG, warm_bytes;
+    // bytes [pa, n) handled with plain loads, in streams of Ls bytes
+    uint32_t pa, Ls, nstreams;
+    uint64_t* cand;
+    uint32_t cap;
+    uint32_t* counters;
+};
+
+struct VerifyArgs {
+    const uint8_t* T;
+    uint32_t n, m;
+    int q, k, mprime;
+    const uint64_t* cand;
+    uint32_t cand_cap;
+    const Slot* slots;
+    uint32_t slot_mask;
+    const uint8_t* pat;   // sorted patterns, r * m
+    const uint32_t* pid;  // pattern id of each sorted row
+    int key_bytes;
+    uint64_t* occ;        // (pos << 32) | pid
+    uint32_t occ_cap;
+    uint32_t* counters;
+};
+
+// Text bytes per row and per stage of the TMA scan.
+constexpr uint32_t kScanRowBytes = 48;
+constexpr int kScanWarps = 8;
+constexpr int kScanStages = 4;
+
+// Launches the MAG scan (fused encode + AOSO Shift-Or + compaction) over
+// T[0..n).  Chooses the TMA row path for the 16-byte aligned bulk and plain
+// loads for the rest.  Returns the number of kernels launched, or -1.
+int launch_scan(const ScanArgs& base, int num_sms, int chunk, cudaStream_t s);
+
+// SMAG: K1 encodes all q-grams, then the scan reads the codes.
+int launch_encode(const uint8_t* T, uint32_t n, const FilterDev& f, uint32_t* codes,
+                  cudaStream_t s);
+int launch_scan_codes(const uint32_t* codes, uint32_t nq, const FilterDev& f, uint64_t* cand,
+                      uint32_t cap, uint32_t* counters, cudaStream_t s);
+
+int launch_verify(const VerifyArgs& a, int num_sms, cudaStream_t s);
+
+// Sorts z keys (in d_keys, device count unknown to the kernels: z is passed)
+// and writes out_pos/out_pid.  tmp must hold z keys; returns launches or -1.
+int launch_sort_output(uint64_t* d_keys, uint64_t* d_tmp, uint32_t* d_hist, size_t hist_cap,
+                       uint32_t z, uint32_t key_bits, uint32_t* out_pos, uint32_t* out_pid,
+                       cudaStream_t s);
+size_t sort_hist_entries(uint32_t z);
+
+}  // namespace mpm

@@ -1,0 +1,203 @@
+// K4: deterministic order of the occurrence list.  The paper fixes no output
+// order; verification appends occurrences through atomics in an order that
+// varies from run to run, so the keys (pos << 32) | pid are sorted.
+//
+// Up to 8192 keys: one block, bitonic sort in shared memory.
+// More: least-significant-digit radix sort, 8-bit digits, only over the
+// digit positions that can be non-zero (pid bits and position bits).  Each
+// pass is a per-block digit histogram, one exclusive scan over
+// (digit, block), and a stable scatter in which each warp ranks its keys
+// with __match_any_sync, warps and blocks in key order.
+#include <vector>
+
+#include "device_common.cuh"
+#include "kernels.h"
+
+namespace mpm {
+
+namespace {
+
+constexpr int kSmallSort = 8192;
+constexpr int kRadixThreads = 256;
+constexpr int kRadixWarps = kRadixThreads / 32;
+constexpr int kRadixTile = 4096;  // keys per block
+constexpr int kWarpTile = kRadixTile / kRadixWarps;
+
+__global__ void __launch_bounds__(1024)
+    sort_small_kernel(const uint64_t* keys, uint32_t z, uint32_t npow2, uint32_t* out_pos,
+                      uint32_t* out_pid) {
+    extern __shared__ uint64_t sk[];
+    for (uint32_t i = threadIdx.x; i < npow2; i += blockDim.x) sk[i] = i < z ? keys[i] : ~0ull;
+    __syncthreads();
+    for (uint32_t size = 2; size <= npow2; size <<= 1) {
+        for (uint32_t stride = size >> 1; stride > 0; stride >>= 1) {
+            for (uint32_t i = threadIdx.x; i < npow2; i += blockDim.x) {
+                const uint32_t j = i ^ stride;
+                if (j > i) {
+                    const bool up = (i & size) == 0;
+                    const uint64_t a = sk[i], b = sk[j];
+                    if ((a > b) == up) {
+                        sk[i] = b;
+                        sk[j] = a;
+                    }
+                }
+            }
+            __syncthreads();
+        }
+    }
+    for (uint32_t i = threadIdx.x; i < z; i += blockDim.x) {
+        out_pos[i] = (uint32_t)(sk[i] >> 32);
+        out_pid[i] = (uint32_t)sk[i];
+    }
+}
+
+__global__ void __launch_bounds__(kRadixThreads)
+    radix_hist_kernel(const uint64_t* keys, uint32_t z, int shift, uint32_t* hist,
+                      uint32_t nblocks) {
+    __shared__ uint32_t h[256];
+    for (int i = threadIdx.x; i < 256; i += blockDim.x) h[i] = 0;
+    __syncthreads();
+    const uint32_t a = blockIdx.x * kRadixTile;
+    const uint32_t b = min(z, a + kRadixTile);
+    for (uint32_t i = a + threadIdx.x; i < b; i += blockDim.x)
+        atomicAdd(&h[(keys[i] >> shift) & 0xFF], 1u);
+    __syncthreads();
+    for (int d = threadIdx.x; d < 256; d += blockDim.x) hist[(size_t)d * nblocks + blockIdx.x] = h[d];
+}
+
+// Exclusive prefix sum over hist[0 .. len) in place, one block.
+__global__ void __launch_bounds__(1024) radix_scan_kernel(uint32_t* hist, uint32_t len) {
+    __shared__ uint32_t warp_sums[32];
+    __shared__ uint32_t carry;
+    if (threadIdx.x == 0) carry = 0;
+    __syncthreads();
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (uint32_t base = 0; base < len; base += blockDim.x) {
+        const uint32_t i = base + threadIdx.x;
+        const uint32_t v = i < len ? hist[i] : 0;
+        uint32_t x = v;
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, x, o);
+            if (lane >= o) x += y;
+        }
+        if (lane == 31) warp_sums[warp] = x;
+        __syncthreads();
+        if (warp == 0) {
+            const int nw = blockDim.x / 32;
+            uint32_t s = lane < nw ? warp_sums[lane] : 0;
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, s, o);
+                if (lane >= o) s += y;
+            }
+            if (lane < nw) warp_sums[lane] = s;  // inclusive over warps
+        }
+        __syncthreads();
+        const uint32_t before = (warp > 0 ? warp_sums[warp - 1] : 0) + carry;
+        if (i < len) hist[i] = before + x - v;
+        __syncthreads();
+        if (threadIdx.x == blockDim.x - 1) carry = before + x;
+        __syncthreads();
+    }
+}
+
+__global__ void __launch_bounds__(kRadixThreads)
+    radix_scatter_kernel(const uint64_t* in, uint64_t* out, uint32_t z, int shift,
+                         const uint32_t* offs, uint32_t nblocks) {
+    __shared__ uint32_t cnt[kRadixWarps][256];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int i = threadIdx.x; i < kRadixWarps * 256; i += blockDim.x) (&cnt[0][0])[i] = 0;
+    __syncthreads();
+    const uint32_t a = blockIdx.x * kRadixTile + warp * kWarpTile;
+    const uint32_t b = min(z, a + kWarpTile);
+    // per-warp digit counts
+    for (uint32_t c = a; c < b; c += 32) {
+        const uint32_t i = c + lane;
+        const bool live = i < b;
+        const uint32_t d = live ? (uint32_t)((in[i] >> shift) & 0xFF) : 256u + lane;
+        const uint32_t peers = __match_any_sync(0xFFFFFFFFu, d);
+        if (live && lane == __ffs(peers) - 1) cnt[warp][d] += __popc(peers);
+        __syncwarp();
+    }
+    __syncthreads();
+    // starting offset of each (warp, digit)
+    for (int d = threadIdx.x; d < 256; d += blockDim.x) {
+        uint32_t run = offs[(size_t)d * nblocks + blockIdx.x];
+        for (int w = 0; w < kRadixWarps; w++) {
+            const uint32_t c = cnt[w][d];
+            cnt[w][d] = run;
+            run += c;
+        }
+    }
+    __syncthreads();
+    for (uint32_t c = a; c < b; c += 32) {
+        const uint32_t i = c + lane;
+        const bool live = i < b;
+        const uint64_t key = live ? in[i] : 0;
+        const uint32_t d = live ? (uint32_t)((key >> shift) & 0xFF) : 256u + lane;
+        const uint32_t peers = __match_any_sync(0xFFFFFFFFu, d);
+        if (live) {
+            const uint32_t rank = __popc(peers & lanemask_lt());
+            out[cnt[warp][d] + rank] = key;
+        }
+        __syncwarp();
+        if (live && lane == __ffs(peers) - 1) cnt[warp][d] += __popc(peers);
+        __syncwarp();
+    }
+}
+
+__global__ void split_kernel(const uint64_t* keys, uint32_t z, uint32_t* out_pos,
+                             uint32_t* out_pid) {
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < z; i += gridDim.x * blockDim.x) {
+        const uint64_t k = keys[i];
+        out_pos[i] = (uint32_t)(k >> 32);
+        out_pid[i] = (uint32_t)k;
+    }
+}
+
+}  // namespace
+
+size_t sort_hist_entries(uint32_t z) {
+    const size_t nblocks = (z + kRadixTile - 1) / kRadixTile;
+    return 256 * (nblocks ? nblocks : 1);
+}
+
+int launch_sort_output(uint64_t* d_keys, uint64_t* d_tmp, uint32_t* d_hist, size_t hist_cap,
+                       uint32_t z, uint32_t key_bits, uint32_t* out_pos, uint32_t* out_pid,
+                       cudaStream_t s) {
+    if (z == 0) return 0;
+    if (z <= (uint32_t)kSmallSort) {
+        uint32_t p2 = 1;
+        while (p2 < z) p2 <<= 1;
+        const size_t smem = (size_t)p2 * 8;
+        cudaFuncSetAttribute(sort_small_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)(kSmallSort * 8));
+        sort_small_kernel<<<1, 1024, smem, s>>>(d_keys, z, p2, out_pos, out_pid);
+        return cudaPeekAtLastError() == cudaSuccess ? 1 : -1;
+    }
+    const uint32_t nblocks = (z + kRadixTile - 1) / kRadixTile;
+    if (sort_hist_entries(z) > hist_cap) return -1;
+    // digit positions that can hold non-zero bits: the low word carries the
+    // pattern id (< 2^pid_bits), the high word the position
+    const uint32_t pid_bits = key_bits & 0xFFFF, pos_bits = key_bits >> 16;
+    std::vector<int> shifts;
+    for (uint32_t b = 0; b < pid_bits; b += 8) shifts.push_back((int)b);
+    for (uint32_t b = 0; b < pos_bits; b += 8) shifts.push_back(32 + (int)b);
+    int launches = 0;
+    uint64_t* src = d_keys;
+    uint64_t* dst = d_tmp;
+    for (int sh : shifts) {
+        radix_hist_kernel<<<nblocks, kRadixThreads, 0, s>>>(src, z, sh, d_hist, nblocks);
+        radix_scan_kernel<<<1, 1024, 0, s>>>(d_hist, 256 * nblocks);
+        radix_scatter_kernel<<<nblocks, kRadixThreads, 0, s>>>(src, dst, z, sh, d_hist, nblocks);
+        launches += 3;
+        uint64_t* t = src;
+        src = dst;
+        dst = t;
+    }
+    split_kernel<<<(z + 255) / 256 < 4096 ? (z + 255) / 256 : 4096, 256, 0, s>>>(src, z, out_pos,
+                                                                                 out_pid);
+    launches++;
+    return cudaPeekAtLastError() == cudaSuccess ? launches : -1;
+}
+
+}  // namespace mpm

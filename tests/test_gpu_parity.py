@@ -1,0 +1,261 @@
+"""GPU parity: the CUDA path, called through the C ABI, against the oracle.
+
+Every comparison is element by element and bit-exact (the method is integer
+work end to end):
+  K1  SMAG encode          codes == oracle text_codes (Section 3.2)
+  K2  scan + compaction    candidate windows == oracle aoso_scan (3.1, 3.2)
+  K3+K4 verify + sort      occurrence list == Aho-Corasick / naive oracle
+The sizes span many TMA row groups plus a ragged plain-load tail; the
+full-size cases run the workloads and the launch configuration bench.py
+times.
+"""
+import os
+
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+from oracle import filter as F  # noqa: E402
+from paper_1405_5483_gb300 import workloads as W  # noqa: E402
+
+KIND = {1: "rank", 2: "greedy", 3: "lowbits"}
+
+
+@pytest.fixture(scope="module")
+def mpm():
+    if not torch.cuda.is_available():
+        pytest.skip("needs a CUDA device")
+    from paper_1405_5483_gb300 import build_lib
+    build_lib.build()
+    import paper_1405_5483_gb300 as mpm
+    return mpm
+
+
+@pytest.fixture(scope="module")
+def native():
+    from oracle import native
+    native.build()
+    return native
+
+
+def _threads():
+    return max(1, min(32, os.cpu_count() or 1))
+
+
+def dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def as_u32(t):
+    if hasattr(t, "cpu"):
+        t = t.cpu().numpy()
+    return np.asarray(t).view(np.uint32)
+
+
+def oracle_fp(P, p):
+    return F.make_params(P, p["q"], p["sigma_r"], p["k"], KIND[p["map_kind"]],
+                         shift=p["map_shift"], order="msd")
+
+
+def oracle_windows(T, P, p):
+    fp = oracle_fp(P, p)
+    cls = F.pattern_classes(P, fp)
+    return F.aoso_scan(F.text_codes(T, fp), F.mask_table(cls, fp), fp, len(cls))
+
+
+def windows_of(records, p, info):
+    rec = records.cpu().numpy().view(np.uint64)
+    h = (rec & np.uint64(0xFFFFFFFF)).astype(np.int64)
+    fired = (rec >> np.uint64(32)).astype(np.int64)
+    out = []
+    lead = (info["mprime"] - 1) * p["k"]
+    for j in range(p["k"]):
+        sel = (fired >> j) & 1 == 1
+        out.append(h[sel] - lead - j)
+    w = np.sort(np.concatenate(out)) if out else np.zeros(0, np.int64)
+    return w
+
+
+def check_search(mpm, native, T, P, sigma, T_dev=None, **kw):
+    m = mpm.Matcher(P, sigma=sigma, **kw)
+    pos, pid = m.search(dev(T) if T_dev is None else T_dev)
+    torch.cuda.synchronize()
+    wp, wi = native.aho_corasick(T, P, threads=_threads())
+    gp, gi = as_u32(pos), as_u32(pid)
+    assert gp.size == wp.size, (gp.size, wp.size, m.params)
+    assert np.array_equal(gp, wp) and np.array_equal(gi, wi), m.params
+    return m, gp.size
+
+
+# ------------------------------------------------------------------ K1
+
+ENCODE_CASES = [
+    ("dna", dict(q=8, sigma_r=4, k=1, map_kind=3, map_shift=1)),
+    ("dna", dict(q=5, sigma_r=4, k=1, map_kind=2)),
+    ("protein", dict(q=3, sigma_r=16, k=2, map_kind=2)),
+    ("protein", dict(q=4, sigma_r=8, k=1, map_kind=1)),
+    ("english", dict(q=2, sigma_r=32, k=3, map_kind=2)),
+    ("english", dict(q=3, sigma_r=16, k=1, map_kind=3, map_shift=0)),
+]
+
+
+def _case(kind, n, r, m, planted):
+    return {"dna": W.dna_case, "protein": W.protein_case, "english": W.english_case}[kind](
+        n, r, m, planted)
+
+
+@pytest.mark.parametrize("kind,kw", ENCODE_CASES)
+@pytest.mark.parametrize("offset", [0, 3])
+def test_encode_matches_oracle(mpm, kind, kw, offset):
+    c = _case(kind, 150_001, 40, 32, 20)
+    m = mpm.Matcher(c.P, sigma=c.sigma, **kw)
+    p = m.params
+    buf = dev(c.T)
+    codes = m.encode(buf[offset:])
+    torch.cuda.synchronize()
+    want = F.text_codes(c.T[offset:], oracle_fp(c.P, p))
+    assert np.array_equal(as_u32(codes).astype(np.int64), want)
+
+
+# ------------------------------------------------------------------ K2
+
+SCAN_CASES = [
+    ("dna", 16, dict(q=8, sigma_r=4, k=1, map_kind=3, map_shift=1)),          # u8, m''=1
+    ("dna", 16, dict(q=4, sigma_r=4, k=2, map_kind=3, map_shift=1)),          # low-bit window
+    ("dna", 32, dict(q=6, sigma_r=4, k=2, map_kind=2)),                       # LUT reduced
+    ("dna", 64, dict(q=2, sigma_r=4, k=2, map_kind=3, map_shift=1)),          # u32 entries
+    ("dna", 64, dict(q=1, sigma_r=4, k=1, map_kind=3, map_shift=1)),          # u64, 64 positions
+    ("protein", 32, dict(q=3, sigma_r=16, k=2, map_kind=2)),                  # LUT raw, u16
+    ("protein", 32, dict(q=4, sigma_r=16, k=2, map_kind=2, table_place=2)),   # global table
+    ("protein", 32, dict(q=4, sigma_r=8, k=3, map_kind=1)),
+    ("protein", 32, dict(q=3, sigma_r=16, k=2, map_kind=2, smag=1)),          # SMAG
+    ("english", 16, dict(q=2, sigma_r=32, k=3, map_kind=2)),
+    ("english", 8, dict(q=3, sigma_r=16, k=1, map_kind=3, map_shift=0)),     # low bits, ell=4
+    ("english", 64, dict(q=5, sigma_r=16, k=4, map_kind=2)),
+]
+
+
+@pytest.mark.parametrize("kind,mlen,kw", SCAN_CASES)
+def test_scan_candidates_match_oracle(mpm, kind, mlen, kw):
+    c = _case(kind, 300_007, 60, mlen, 30)
+    m = mpm.Matcher(c.P, sigma=c.sigma, **kw)
+    p, info = m.params, m.info
+    rec = m.scan(dev(c.T))
+    torch.cuda.synchronize()
+    got = windows_of(rec, p, info)
+    assert np.unique(got).size == got.size, "a window was reported twice"
+    want = np.array(oracle_windows(c.T, c.P, p), dtype=np.int64)
+    assert np.array_equal(got, want), (p, got.size, want.size)
+
+
+def test_scan_chunk_sizes_do_not_change_candidates(mpm):
+    c = W.protein_case(400_000, 100, 32, 50)
+    base = None
+    for chunk in (0, 96, 480, 4800, 48000):
+        m = mpm.Matcher(c.P, sigma=20, q=3, sigma_r=16, k=2, map_kind=2, chunk=chunk)
+        w = windows_of(m.scan(dev(c.T)), m.params, m.info)
+        base = w if base is None else base
+        assert np.array_equal(w, base), chunk
+
+
+# --------------------------------------------------------------- K3 + K4
+
+def test_search_config1_matches_oracle(mpm, native):
+    c = W.config1()
+    m, z = check_search(mpm, native, c.T, c.P, 4)
+    assert z >= 50
+    st = m.stats
+    assert st["z"] == z and st["n"] == c.n
+
+
+@pytest.mark.parametrize("kind,mlen,kw", SCAN_CASES)
+def test_search_parameter_grid_matches_oracle(mpm, native, kind, mlen, kw):
+    c = _case(kind, 500_003, 80, mlen, 40)
+    check_search(mpm, native, c.T, c.P, c.sigma, **kw)
+
+
+def test_search_host_text_and_host_outputs(mpm, native):
+    c = W.protein_case(200_000, 50, 32, 25)
+    m = mpm.Matcher(c.P, sigma=20)
+    pos, pid = m.search(c.T)  # numpy in: host text, host outputs
+    wp, wi = native.aho_corasick(c.T, c.P)
+    assert np.array_equal(pos, wp) and np.array_equal(pid, wi)
+
+
+@pytest.mark.parametrize("offset", [1, 2, 3, 5])
+def test_search_unaligned_text(mpm, native, offset):
+    c = W.dna_case(300_000, 100, 16, 50)
+    buf = dev(c.T)
+    m = mpm.Matcher(c.P, sigma=4)
+    pos, pid = m.search(buf[offset:])
+    wp, wi = native.aho_corasick(c.T[offset:], c.P)
+    assert np.array_equal(as_u32(pos), wp) and np.array_equal(as_u32(pid), wi)
+
+
+def test_search_edge_cases(mpm, native):
+    rng = np.random.default_rng(5)
+    # empty text, text shorter than m, text equal to one pattern
+    P = np.frombuffer(b"ACGTACGTACGTACGT", np.uint8).reshape(1, 16)
+    m = mpm.Matcher(P, sigma=4)
+    for T in (np.zeros(0, np.uint8), P[0, :10].copy(), P[0].copy()):
+        if T.size == 0:
+            pos, pid = m.search(T)
+        else:
+            pos, pid = m.search(dev(T))
+        wp, wi = native.aho_corasick(T, P) if T.size else (np.zeros(0), np.zeros(0))
+        assert np.array_equal(as_u32(pos), wp.astype(np.uint32))
+    # one pattern, duplicates, m = 1, bytes absent from the text
+    T = rng.integers(0, 3, size=100_000).astype(np.uint8) + 97
+    P1 = T[500:520].reshape(1, 20).copy()
+    check_search(mpm, native, T, P1, 3)
+    Pd = np.stack([T[10:22], T[10:22], T[900:912], np.frombuffer(b"zzzzzzzzzzzz", np.uint8)])
+    check_search(mpm, native, T, Pd, 256)
+    Pm1 = np.array([[97], [99], [99]], np.uint8)
+    check_search(mpm, native, T, Pm1, 3)
+    # a run of one symbol: an occurrence at every position (z ~ n), which
+    # exercises the multi-pass radix sort
+    Tr = np.full(200_000, 65, np.uint8)
+    Tr[::9973] = 66
+    Pr = np.full((3, 8), 65, np.uint8)
+    m2, z = check_search(mpm, native, Tr, Pr, 2)
+    assert z > 100_000
+
+
+def test_capacity_error_reports_required_size(mpm, native):
+    c = W.dna_case(200_000, 100, 16, 100)
+    m = mpm.Matcher(c.P, sigma=4)
+    T = dev(c.T)
+    pos = torch.empty(10, dtype=torch.int32, device="cuda")
+    pid = torch.empty(10, dtype=torch.int32, device="cuda")
+    with pytest.raises(mpm.MpmError) as e:
+        m.search_into(T, pos, pid)
+    assert e.value.code == mpm.MPM_ECAPACITY
+    wp, _ = native.aho_corasick(c.T, c.P)
+    assert e.value.z == wp.size
+
+
+# ------------------------------------------------------ full-size configs
+
+def test_full_size_protein_config(mpm, native):
+    """The benchmark's workload: 256 MiB protein-like text, r = 1000, m = 32,
+    automatic parameters, the same launch configuration bench.py times."""
+    c = W.config2()
+    m, z = check_search(mpm, native, c.T, c.P, 20)
+    assert z >= 500
+
+
+def test_full_size_dna_scaled(mpm, native):
+    c = W.config1_scaled()
+    m, z = check_search(mpm, native, c.T, c.P, 4)
+    assert z >= 50
+
+
+@pytest.mark.parametrize("r,mlen", [(100_000, 32), (10_000, 16), (10_000, 64)])
+def test_full_size_dna_large_sets(mpm, native, r, mlen):
+    c = W.config3(r=r, m=mlen)
+    m, z = check_search(mpm, native, c.T, c.P, 4)
+    # every planted pattern occurs at its planting offset
+    pos_set = z
+    assert pos_set >= r // 10

@@ -1,0 +1,111 @@
+"""Host-side checks that need no GPU: the library loads and exports every
+symbol include/mpm.h declares, parameter planning validates its input, and
+the host builder's byte map mu and Shift-Or mask table equal the oracle's
+(the alphabet reduction of Section 3.3 and the superimposed q-gram classes of
+Sections 2 and 3.2)."""
+import ctypes
+
+import numpy as np
+import pytest
+
+from oracle import filter as F
+
+
+@pytest.fixture(scope="module")
+def mpm():
+    from paper_1405_5483_gb300 import build_lib
+    build_lib.build()
+    import paper_1405_5483_gb300 as mpm
+    return mpm
+
+
+def test_library_exports_every_declared_symbol(mpm):
+    names = mpm.declared_functions()
+    assert "mpm_build" in names and "mpm_search" in names and "mpm_free" in names
+    L = ctypes.CDLL(mpm._native.LIB_PATH)
+    missing = [n for n in names if not hasattr(L, n)]
+    assert not missing, missing
+
+
+def test_strerror_and_invalid_arguments(mpm):
+    L = mpm.lib()
+    assert L.mpm_strerror(0) == b"ok"
+    P = np.frombuffer(b"ACGTACGT", np.uint8).reshape(1, 8)
+    with pytest.raises(mpm.MpmError):
+        mpm.plan(P, 4, q=5)        # L' = floor((8-5+1)/5) = 0: infeasible
+    with pytest.raises(mpm.MpmError):
+        mpm.plan(P, 4, sigma_r=3)  # not a power of two
+    with pytest.raises(mpm.MpmError):
+        mpm.plan(P, 4, sigma_r=8)  # above the declared alphabet
+    with pytest.raises(mpm.MpmError):
+        mpm.plan(P, 4, k=33)
+    with pytest.raises(mpm.MpmError):
+        mpm.plan(P, 300)
+    p, info = mpm.plan(P, 4, q=2, sigma_r=4, k=1)
+    assert (p["q"], p["sigma_r"], p["k"]) == (2, 4, 1)
+    assert info["L"] == (8 - 2 + 1) // 2 and info["positions"] == info["L"]
+
+
+def test_auto_plan_dna_uses_low_bits_with_shift_one(mpm):
+    from paper_1405_5483_gb300 import workloads as W
+    c = W.dna_case(1 << 16, 100, 16, 50)
+    p, info = mpm.plan(c.P, 4)
+    assert p["map_kind"] == mpm.MAP_LOWBITS and p["sigma_r"] == 4 and p["map_shift"] == 1
+    assert 1 <= p["k"] <= info["L"]
+
+
+def _oracle_tables(P, p):
+    fp = F.FilterParams(p["q"], p["sigma_r"], p["k"], _oracle_mu(P, p), "msd")
+    cls = F.pattern_classes(P, fp)
+    return fp.mu, F.mask_table(cls, fp), len(cls)
+
+
+def _oracle_mu(P, p):
+    kind = {1: "rank", 2: "greedy", 3: "lowbits"}[p["map_kind"]]
+    return F.make_params(P, p["q"], p["sigma_r"], p["k"], kind, shift=p["map_shift"]).mu
+
+
+def _table_positions(table, entry_bytes, positions):
+    t = table.reshape(-1, entry_bytes).astype(np.uint64)
+    v = np.zeros(t.shape[0], np.uint64)
+    for b in range(entry_bytes):
+        v |= t[:, b] << np.uint64(8 * b)
+    mask = np.uint64((1 << positions) - 1) if positions < 64 else np.uint64(0xFFFFFFFFFFFFFFFF)
+    return v & mask
+
+
+@pytest.mark.parametrize("seed", range(40))
+def test_host_tables_equal_oracle(mpm, seed):
+    rng = np.random.default_rng(100 + seed)
+    sigma = int(rng.choice([2, 4, 5, 20, 95]))
+    r = int(rng.integers(1, 60))
+    m = int(rng.choice([4, 8, 12, 16, 32, 40]))
+    kind = int(rng.integers(1, 4))
+    sr = int(rng.choice([s for s in (2, 4, 8, 16) if s <= max(2, sigma)]))
+    q = int(rng.integers(1, 5))
+    while q * int(np.log2(sr)) > 20 or (m - q + 1) // q < 1:
+        q -= 1
+    Lc = (m - q + 1) // q
+    k = int(rng.integers(1, min(Lc, 32) + 1))
+    base = 33 if sigma > 20 else 65
+    P = (rng.integers(0, sigma, size=(r, m)) + base).astype(np.uint8)
+    kw = dict(q=q, sigma_r=sr, k=k, map_kind=kind,
+              map_shift=int(rng.integers(0, 3)) if kind == 3 else -1)
+    mu, table, info = mpm.host_tables(P, sigma, **kw)
+    p = dict(q=q, sigma_r=sr, k=k, map_kind=kind, map_shift=info["map_shift"])
+    omu, otab, npos = _oracle_tables(P, p)
+    assert np.array_equal(mu, omu), "mu differs from the oracle"
+    assert info["positions"] == npos
+    got = _table_positions(table, info["entry_bytes"], npos)
+    assert np.array_equal(got, otab.astype(np.uint64)), "mask table differs from the oracle"
+
+
+def test_host_tables_auto_params_equal_oracle(mpm):
+    from paper_1405_5483_gb300 import workloads as W
+    for case in (W.dna_case(1 << 14, 50, 16, 25), W.protein_case(1 << 14, 100, 32, 50),
+                 W.english_case(1 << 14, 80, 16, 40)):
+        mu, table, info = mpm.host_tables(case.P, case.sigma)
+        omu, otab, npos = _oracle_tables(case.P, info)
+        assert np.array_equal(mu, omu)
+        got = _table_positions(table, info["entry_bytes"], npos)
+        assert np.array_equal(got, otab.astype(np.uint64))
