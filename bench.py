@@ -1,0 +1,305 @@
+"""Benchmark: text GB/s of exact multiple pattern matching (MAG) on GB300.
+
+One step = one mpm_search over the whole text: the fused encode + AOSO
+Shift-Or scan, verification, the occurrence count read-back and the sort of
+the occurrence list.  The default workload is the protein-like one: a
+256 MiB text over 20 symbols (Zipf s = 0.8), r = 1000 patterns of length
+m = 32, half planted.  The text is larger than the 129 MB L2, so no flush is
+needed between steps.
+
+Prints one JSON line.  --impl reference times the oracle (textbook
+Aho-Corasick in C, threaded) on the host cores instead.
+Multi-GPU: launched under torchrun, every rank searches its own text
+(weak scaling); rank 0 prints the aggregate.
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "text GB/s scanned (bit-exact), % of HBM peak; batched+learned vs plain form"
+
+WORKLOADS = {
+    # name: (generator, sigma, description)
+    "protein-256MiB": ("config2", 20,
+                       "protein-like text 256 MiB, 20 symbols Zipf s=0.8, r=1000, m=32, "
+                       "half planted"),
+    "dna-1GiB": ("config1_scaled", 4,
+                 "uniform DNA text 1 GiB, r=100, m=16, half planted (config-1 shape at scale)"),
+    "dna-1MiB": ("config1", 4, "uniform DNA text 1 MiB, r=100, m=16, half planted"),
+}
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons, sampled every 200 ms."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", "clocks_bench_%d.csv" % os.getpid())
+
+    def __enter__(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.FIELDS,
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            self.f.close()
+
+    def summary(self):
+        if not self.proc or not os.path.exists(self.path):
+            return None
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx = float(parts[2])
+            except ValueError:
+                continue
+            for name, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(name)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def make_case(name):
+    from paper_1405_5483_gb300 import workloads as W
+    gen, sigma, desc = WORKLOADS[name]
+    return getattr(W, gen)(), sigma, desc
+
+
+def cpu_baseline(case, sample_bytes):
+    """The oracle (Aho-Corasick, C, all host cores) on the first sample_bytes."""
+    from oracle import native
+    threads = os.cpu_count() or 1
+    n = min(case.n, sample_bytes)
+    T = np.ascontiguousarray(case.T[:n])
+    ac = native.AhoCorasick(case.P)
+    t0 = time.perf_counter()
+    pos, _ = ac.search(T, threads=threads)
+    dt = time.perf_counter() - t0
+    ac.close()
+    return {"value": n / dt / 1e9, "unit": "GB/s", "cores": threads, "kind": "oracle",
+            "sample": "first %d MiB of the text, all %d patterns, Aho-Corasick over %d threads "
+                      "(%.2f s, %d occurrences)" % (n >> 20, case.r, threads, dt, pos.size)}
+
+
+def run_reference(args, rank):
+    if rank != 0:
+        return
+    case, sigma, desc = make_case(args.workload)
+    sample = args.ref_sample_mib << 20
+    from oracle import native
+    threads = os.cpu_count() or 1
+    ac = native.AhoCorasick(case.P)
+    n = min(case.n, sample)
+    T = np.ascontiguousarray(case.T[:n])
+    for _ in range(args.warmup):
+        ac.search(T, threads=threads)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        ac.search(T, threads=threads)
+    dt = time.perf_counter() - t0
+    value = n * args.steps / dt / 1e9
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "GB/s",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": dt * 1e3 / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "u8", "data": "synthetic",
+        "config": {"workload": args.workload, "description": desc, "n": n, "r": case.r,
+                   "m": case.m},
+        "cpu_baseline": {"value": value, "unit": "GB/s", "cores": threads, "kind": "oracle",
+                         "sample": "first %d MiB of the text per step, Aho-Corasick over %d "
+                                   "threads" % (n >> 20, threads)},
+        "e2e": {"value": value, "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="protein-256MiB", choices=sorted(WORKLOADS))
+    ap.add_argument("--cpu-sample-mib", type=int, default=64)
+    ap.add_argument("--ref-sample-mib", type=int, default=64)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+
+    if args.impl == "reference":
+        run_reference(args, rank)
+        return
+
+    import torch
+    import torch.distributed as dist
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+
+    import paper_1405_5483_gb300 as mpm
+
+    case, sigma, desc = make_case(args.workload)
+    T = torch.from_numpy(case.T).to(dev)
+    m = mpm.Matcher(case.P, sigma=sigma)
+    m.set_timing(True)
+    cap = max(1 << 16, 8 * case.r)
+    out_pos = torch.empty(cap, dtype=torch.int32, device=dev)
+    out_pid = torch.empty(cap, dtype=torch.int32, device=dev)
+    stream = torch.cuda.current_stream()
+
+    def step():
+        return m.search_into(T, out_pos, out_pid)
+
+    for _ in range(max(3, args.warmup)):
+        z = step()
+    torch.cuda.synchronize()
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    scan_ms, verify_ms, launches = [], [], 0
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        barrier()
+        ev0.record(stream)
+        for _ in range(args.steps):
+            z = step()
+            st = m.stats
+            scan_ms.append(st["ms_scan"])
+            verify_ms.append(st["ms_verify"])
+            launches += st["launches"]
+        ev1.record(stream)
+        barrier()
+    elapsed_ms = ev0.elapsed_time(ev1)
+    if world > 1:
+        t = torch.tensor([elapsed_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        elapsed_ms = float(t.item())
+    total_bytes = case.n * args.steps * world
+    value = total_bytes / (elapsed_ms * 1e-3) / 1e9
+    peak, peak_kind = peaks()
+
+    # end to end through the public API with host buffers: pinned host text,
+    # host outputs, copies inside the timed region
+    hT = torch.from_numpy(case.T).pin_memory()
+    hpos = np.empty(cap, np.uint32)
+    hpid = np.empty(cap, np.uint32)
+    e2e_steps = max(2, min(args.steps, 5))
+    m.search_into(hT, hpos, hpid)
+    torch.cuda.synchronize()
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        ze = m.search_into(hT, hpos, hpid)
+    torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - t0
+    e2e_value = case.n * e2e_steps * world / e2e_s / 1e9
+
+    # the dominant kernel: the scan.  Algorithmic bytes per launch = the
+    # text read once plus 8 bytes per candidate record written.
+    st = m.stats
+    scan_avg = statistics.mean(scan_ms)
+    algo_bytes = case.n + 8 * st["candidates"]
+    achieved = algo_bytes / (scan_avg * 1e-3) / 1e9
+    traffic = None
+    tpath = os.path.join(ROOT, "profiles", "scan_traffic.json")
+    if os.path.exists(tpath):
+        with open(tpath) as f:
+            tj = json.load(f)
+        if tj.get("workload") == args.workload and tj.get("kernel_rev") == kernel_rev():
+            traffic = tj.get("traffic_bytes_per_launch")
+
+    if rank == 0:
+        cpu = None
+        if not args.no_cpu_baseline and world == 1:
+            cpu = cpu_baseline(case, args.cpu_sample_mib << 20)
+        line = {
+            "metric": METRIC, "value": value, "unit": "GB/s", "n_gpus": world,
+            "steps": args.steps, "warmup": max(3, args.warmup),
+            "ms_per_step": elapsed_ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "u8", "data": "synthetic",
+            "config": {"workload": args.workload, "description": desc, "n": case.n,
+                       "r": case.r, "m": case.m, "params": m.params,
+                       "l2": "inputs larger than L2 (no flush)",
+                       "parallelism": "replicas" if world > 1 else "single GPU"},
+            "hbm_frac_of_%s_peak" % peak_kind: value / peak,
+            "occurrences": z,
+            "candidates_per_step": st["candidates"],
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "traffic": traffic,
+                         "kernel": "scan_tma_kernel (+ plain-load tail)",
+                         "peak_kind": peak_kind, "scan_ms": scan_avg,
+                         "verify_ms": statistics.mean(verify_ms)},
+            "e2e": {"value": e2e_value, "unit": "GB/s", "h2d_bytes_per_step": case.n,
+                    "d2h_bytes_per_step": 16 + 8 * ze},
+            "gpu_launches": launches,
+            "clocks": clk.summary(),
+            "cpu_baseline": cpu,
+        }
+        print(json.dumps(line))
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def kernel_rev():
+    """A hash of the scan kernel's source, to tie stored counters to it."""
+    import hashlib
+    h = hashlib.sha1()
+    for f in ("scan.cu", "device_common.cuh", "kernels.h"):
+        with open(os.path.join(ROOT, "paper_1405_5483_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:12]
+
+
+if __name__ == "__main__":
+    main()

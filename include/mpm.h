@@ -100,6 +100,8 @@ typedef struct {
     uint64_t z;            /* occurrences found                               */
     uint32_t launches;     /* kernels launched by the call                    */
     uint32_t retries;      /* re-runs after growing an internal buffer        */
+    float ms_scan;         /* device time of the scan kernels (timing on)     */
+    float ms_verify;       /* device time of the verification kernel          */
 } mpm_stats;
 
 typedef struct mpm_handle mpm_handle;
@@ -155,6 +157,12 @@ int mpm_get_params(const mpm_handle *h, mpm_params *out, mpm_table_info *info);
 
 /* Counters of the last search or scan on this handle. */
 int mpm_get_stats(const mpm_handle *h, mpm_stats *out);
+
+/* on != 0: mpm_search records CUDA events around its scan and verification
+ * launches on the handle's stream and reports their device times in
+ * mpm_stats (read after the search's own count read-back, so no extra
+ * synchronisation).  Off by default. */
+int mpm_set_timing(mpm_handle *h, int on);
 
 /* ---------------------------------------------- host-only planning calls */
 

@@ -109,6 +109,10 @@ class Matcher:
         self._check(lib().mpm_get_stats(self._h, ctypes.byref(s)), "stats")
         return s.as_dict()
 
+    def set_timing(self, on=True):
+        """Device times of the scan and verification kernels in .stats."""
+        self._check(lib().mpm_set_timing(self._h, 1 if on else 0), "mpm_set_timing")
+
     def _check(self, rc, what):
         if rc:
             raise MpmError(rc, what)

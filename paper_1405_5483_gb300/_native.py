@@ -37,7 +37,8 @@ class TableInfo(ctypes.Structure):
 class Stats(ctypes.Structure):
     _fields_ = [("n", ctypes.c_uint64), ("sampled", ctypes.c_uint64),
                 ("candidates", ctypes.c_uint64), ("z", ctypes.c_uint64),
-                ("launches", ctypes.c_uint32), ("retries", ctypes.c_uint32)]
+                ("launches", ctypes.c_uint32), ("retries", ctypes.c_uint32),
+                ("ms_scan", ctypes.c_float), ("ms_verify", ctypes.c_float)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}
@@ -80,6 +81,7 @@ def lib():
         "mpm_set_stream": (ctypes.c_int, [vp, vp]),
         "mpm_get_params": (ctypes.c_int, [vp, Pp, Ip]),
         "mpm_get_stats": (ctypes.c_int, [vp, Sp]),
+        "mpm_set_timing": (ctypes.c_int, [vp, ctypes.c_int]),
         "mpm_plan": (ctypes.c_int, [u8p, sz, sz, ctypes.c_int, Pp, Pp, Ip]),
         "mpm_host_tables": (ctypes.c_int, [u8p, sz, sz, ctypes.c_int, Pp, vp, vp, sz]),
         "mpm_encode": (ctypes.c_int, [vp, u8p, sz, vp]),

@@ -44,6 +44,8 @@ struct mpm_handle {
     size_t out_cap = 0;
 
     mpm_stats stats{};
+    int timing = 0;
+    cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};
 };
 
 namespace mpm {
@@ -120,6 +122,8 @@ void release(mpm_handle* h) {
     cudaFree(h->d_text);
     cudaFree(h->d_codes);
     cudaFree(h->d_out);
+    for (auto& e : h->ev)
+        if (e) cudaEventDestroy(e);
     cudaGetLastError();
     delete h;
 }
@@ -156,7 +160,9 @@ int run_filter(mpm_handle* h, const uint8_t* dT, uint32_t n, int* launches) {
         a.cand = h->d_cand;
         a.cap = (uint32_t)h->cand_cap;
         a.counters = h->d_counters;
+        if (h->timing) cudaEventRecord(h->ev[0], s);
         l = mpm::launch_scan(a, h->num_sms, h->plan.p.chunk, s);
+        if (h->timing) cudaEventRecord(h->ev[1], s);
         if (l == -2) return MPM_ENOTSUP;
     }
     if (l < 0) return MPM_ECUDA;
@@ -182,11 +188,19 @@ int run_filter(mpm_handle* h, const uint8_t* dT, uint32_t n, int* launches) {
         if (mpm::launch_verify(v, h->num_sms, s) < 0) return MPM_ECUDA;
         *launches += 1;
     }
+    if (h->timing) cudaEventRecord(h->ev[2], s);
     if (cudaMemcpyAsync(h->h_counters, h->d_counters, mpm::kNumCounters * sizeof(uint32_t),
                         cudaMemcpyDeviceToHost, s) != cudaSuccess)
         return MPM_ECUDA;
     if (cudaStreamSynchronize(s) != cudaSuccess) return MPM_ECUDA;
     if (h->h_counters[mpm::kErrorFlag]) return (int)h->h_counters[mpm::kErrorFlag];
+    if (h->timing && !h->plan.p.smag) {
+        float a = 0.f, b = 0.f;
+        cudaEventElapsedTime(&a, h->ev[0], h->ev[1]);
+        cudaEventElapsedTime(&b, h->ev[1], h->ev[2]);
+        h->stats.ms_scan += a;
+        h->stats.ms_verify += b;
+    }
     return MPM_OK;
 }
 
@@ -291,6 +305,19 @@ int mpm_get_params(const mpm_handle* h, mpm_params* out, mpm_table_info* info) {
     if (!h || !out) return set_error(MPM_EINVAL);
     *out = h->plan.p;
     if (info) *info = h->plan.info;
+    return set_error(MPM_OK);
+}
+
+int mpm_set_timing(mpm_handle* h, int on) {
+    if (!h) return set_error(MPM_EINVAL);
+    if (on && !h->ev[0]) {
+        for (auto& e : h->ev)
+            if (cudaEventCreate(&e) != cudaSuccess) {
+                cudaGetLastError();
+                return set_error(MPM_ECUDA);
+            }
+    }
+    h->timing = on ? 1 : 0;
     return set_error(MPM_OK);
 }
 
