@@ -41,6 +41,7 @@ extern "C" {
 #define MPM_ECAPACITY  4  /* output capacity too small; *z = required count  */
 #define MPM_ETIMEOUT   5  /* a bounded device wait gave up; results invalid  */
 #define MPM_ENOTSUP    6  /* combination not supported by this build         */
+#define MPM_ESCRATCH   7  /* mpm_search_noalloc: its fixed scratch is too small */
 
 /* ----------------------------------------------------- parameter choices */
 #define MPM_MAP_AUTO     0
@@ -209,6 +210,45 @@ int mpm_encode(mpm_handle *h, const uint8_t *T, size_t n, uint32_t *codes);
  */
 int mpm_scan(mpm_handle *h, const uint8_t *T, size_t n, uint64_t *cand,
              size_t *count);
+
+/* ------------------------------------------- search that allocates nothing */
+
+/*
+ * The paper has no counterpart to this call; it exists for callers of this
+ * library that must not allocate device memory when they search: programs
+ * whose GPU memory is all handed out by their own pool or caching allocator
+ * (a stray cudaMalloc there can fail or fragment the pool), and
+ * latency-sensitive servers, where cudaMalloc and cudaFree can synchronise
+ * the device and stall every other stream.  mpm_search grows its scratch
+ * buffers with cudaMalloc on first use and when a search needs more; this
+ * call instead keeps all of its scratch (counters, candidate records and
+ * occurrence keys) in one fixed array of device memory inside the library,
+ * MPM_NOALLOC_SCRATCH_BYTES bytes, that every GPU which loads the library
+ * holds until the process exits.  It calls no cudaMalloc, cudaFree or other
+ * allocating routine.
+ *
+ * Arguments and results are those of mpm_search, except: T, out_pos and
+ * out_pid must be device memory (host memory would need a staging buffer:
+ * MPM_EINVAL), the handle must not use SMAG (MPM_ENOTSUP), and a search that
+ * produces more than MPM_NOALLOC_MAX_CANDIDATES candidate records or more
+ * than MPM_NOALLOC_MAX_OCCURRENCES occurrences is rejected with
+ * MPM_ESCRATCH (*z is then the occurrence count when it is known, else 0);
+ * mpm_search handles such searches.
+ *
+ * The first call on a device looks up that device's address of the array
+ * (cudaGetSymbolAddress, with the device current); make that first call
+ * before any stream capture.  Every call on a device shares the one array
+ * and leaves its contents behind; each call clears the counters it needs.
+ * Calls whose work overlaps on the GPU (different streams, threads or
+ * handles on the same device) race on the array and must be serialised by
+ * the caller.
+ */
+#define MPM_NOALLOC_MAX_CANDIDATES  (1u << 21)
+#define MPM_NOALLOC_MAX_OCCURRENCES 8192u
+#define MPM_NOALLOC_SCRATCH_BYTES   (256u + 8u * (MPM_NOALLOC_MAX_CANDIDATES + MPM_NOALLOC_MAX_OCCURRENCES))
+
+int mpm_search_noalloc(mpm_handle *h, const uint8_t *T, size_t n, uint32_t *out_pos,
+                       uint32_t *out_pid, size_t *z);
 
 #ifdef __cplusplus
 }

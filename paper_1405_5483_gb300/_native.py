@@ -11,7 +11,10 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "_build", "libmpm.so")
 HEADER = os.path.join(os.path.dirname(HERE), "include", "mpm.h")
 
-MPM_OK, MPM_EINVAL, MPM_ENOMEM, MPM_ECUDA, MPM_ECAPACITY, MPM_ETIMEOUT, MPM_ENOTSUP = range(7)
+(MPM_OK, MPM_EINVAL, MPM_ENOMEM, MPM_ECUDA, MPM_ECAPACITY, MPM_ETIMEOUT, MPM_ENOTSUP,
+ MPM_ESCRATCH) = range(8)
+NOALLOC_MAX_CANDIDATES = 1 << 21
+NOALLOC_MAX_OCCURRENCES = 8192
 MAP_AUTO, MAP_RANK, MAP_GREEDY, MAP_LOWBITS = range(4)
 TABLE_AUTO, TABLE_SMEM, TABLE_GLOBAL = range(3)
 
@@ -86,6 +89,7 @@ def lib():
         "mpm_host_tables": (ctypes.c_int, [u8p, sz, sz, ctypes.c_int, Pp, vp, vp, sz]),
         "mpm_encode": (ctypes.c_int, [vp, u8p, sz, vp]),
         "mpm_scan": (ctypes.c_int, [vp, u8p, sz, vp, szp]),
+        "mpm_search_noalloc": (ctypes.c_int, [vp, u8p, sz, vp, vp, szp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(L, name)

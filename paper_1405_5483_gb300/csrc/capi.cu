@@ -8,6 +8,7 @@
 #include <algorithm>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <new>
 
 #include "kernels.h"
@@ -228,6 +229,9 @@ const char* mpm_strerror(int code) {
         case MPM_ECAPACITY: return "output capacity too small";
         case MPM_ETIMEOUT: return "bounded device wait timed out";
         case MPM_ENOTSUP: return "unsupported combination";
+        case MPM_ESCRATCH:
+            return "the search needs more scratch than the fixed buffer of "
+                   "mpm_search_noalloc holds; use mpm_search";
         default: return "unknown error";
     }
 }
@@ -475,3 +479,134 @@ int mpm_scan(mpm_handle* h, const uint8_t* T, size_t n, uint64_t* cand, size_t* 
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// mpm_search_noalloc: the same filter, verification and sort as mpm_search,
+// with every scratch buffer carved out of one file-scope device array, so
+// that the call itself allocates no device memory.
+//
+// Layout of the array: [counters, 256 B][candidate records][occurrence keys].
+// The occurrence limit keeps the sort on its one-block path, which needs no
+// further scratch.
+
+namespace {
+
+constexpr size_t kNaCounterBytes = 256;
+constexpr size_t kNaMaxCand = MPM_NOALLOC_MAX_CANDIDATES;
+constexpr size_t kNaMaxOcc = MPM_NOALLOC_MAX_OCCURRENCES;
+constexpr size_t kNaBytes = MPM_NOALLOC_SCRATCH_BYTES;
+static_assert(kNaBytes == kNaCounterBytes + 8 * (kNaMaxCand + kNaMaxOcc), "scratch layout");
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNaBytes];
+
+// The array's address on each device, looked up once per device.  In host
+// code g_noalloc_scratch names a host-side stand-in, never the device memory.
+constexpr int kNaMaxDevices = 128;
+std::mutex g_na_mutex;
+void* g_na_base[kNaMaxDevices] = {};
+
+int noalloc_base(int device, unsigned char** out) {
+    if (device < 0 || device >= kNaMaxDevices) return MPM_ECUDA;
+    std::lock_guard<std::mutex> lock(g_na_mutex);
+    if (!g_na_base[device]) {
+        void* p = nullptr;
+        if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) {
+            cudaGetLastError();
+            return MPM_ECUDA;
+        }
+        g_na_base[device] = p;
+    }
+    *out = static_cast<unsigned char*>(g_na_base[device]);
+    return MPM_OK;
+}
+
+}  // namespace
+
+extern "C" int mpm_search_noalloc(mpm_handle* h, const uint8_t* T, size_t n, uint32_t* out_pos,
+                                  uint32_t* out_pid, size_t* z) {
+    if (!h || !z || (n > 0 && !T) || n >= (1ull << 32)) return set_error(MPM_EINVAL);
+    if (*z > 0 && (!out_pos || !out_pid)) return set_error(MPM_EINVAL);
+    if (h->plan.p.smag) return set_error(MPM_ENOTSUP);
+    int rc = prepare(h);
+    if (rc) return set_error(rc);
+    if (n > 0 && !is_device_ptr(T)) return set_error(MPM_EINVAL);
+    if (*z > 0 && (!is_device_ptr(out_pos) || !is_device_ptr(out_pid)))
+        return set_error(MPM_EINVAL);
+    unsigned char* base = nullptr;
+    rc = noalloc_base(h->device, &base);
+    if (rc) return set_error(rc);
+    uint32_t* counters = reinterpret_cast<uint32_t*>(base);
+    uint64_t* cand = reinterpret_cast<uint64_t*>(base + kNaCounterBytes);
+    uint64_t* occ = cand + kNaMaxCand;
+
+    const size_t out_capacity = *z;
+    h->stats = mpm_stats{};
+    h->stats.n = n;
+    h->stats.sampled = (n / (uint32_t)h->plan.p.q) / (uint32_t)h->plan.p.k;
+    if (n < h->plan.m) {
+        *z = 0;
+        return set_error(MPM_OK);
+    }
+    cudaStream_t s = h->stream;
+    const mpm::FilterDev f = filter_dev(h);
+    if (cudaMemsetAsync(counters, 0, kNaCounterBytes, s) != cudaSuccess)
+        return set_error(MPM_ECUDA);
+    mpm::ScanArgs a{};
+    a.T = T;
+    a.n = (uint32_t)n;
+    a.f = f;
+    a.P = (uint32_t)(f.k * f.q);
+    const uint32_t wb = (uint32_t)(f.mprime - 1) * a.P;
+    a.warm_bytes = (wb + 3) & ~3u;
+    a.cand = cand;
+    a.cap = (uint32_t)kNaMaxCand;
+    a.counters = counters;
+    int launches = mpm::launch_scan(a, h->num_sms, h->plan.p.chunk, s);
+    if (launches == -2) return set_error(MPM_ENOTSUP);
+    if (launches < 0) return set_error(MPM_ECUDA);
+    mpm::VerifyArgs v{};
+    v.T = T;
+    v.n = (uint32_t)n;
+    v.m = (uint32_t)h->plan.m;
+    v.q = f.q;
+    v.k = f.k;
+    v.mprime = f.mprime;
+    v.cand = cand;
+    v.cand_cap = (uint32_t)kNaMaxCand;
+    v.slots = h->d_slots;
+    v.slot_mask = (uint32_t)h->host.slots.size() - 1;
+    v.pat = h->d_pat;
+    v.pid = h->d_pid;
+    v.key_bytes = h->host.key_bytes;
+    v.occ = occ;
+    v.occ_cap = (uint32_t)kNaMaxOcc;
+    v.counters = counters;
+    if (mpm::launch_verify(v, h->num_sms, s) < 0) return set_error(MPM_ECUDA);
+    launches++;
+    if (cudaMemcpyAsync(h->h_counters, counters, mpm::kNumCounters * sizeof(uint32_t),
+                        cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess)
+        return set_error(MPM_ECUDA);
+    if (h->h_counters[mpm::kErrorFlag]) return set_error((int)h->h_counters[mpm::kErrorFlag]);
+    const uint32_t nc = h->h_counters[mpm::kCandCount];
+    const uint32_t zz = h->h_counters[mpm::kOccCount];
+    h->stats.candidates = nc;
+    h->stats.launches = (uint32_t)launches;
+    if (nc > kNaMaxCand) {
+        *z = 0;
+        return set_error(MPM_ESCRATCH);
+    }
+    *z = zz;
+    h->stats.z = zz;
+    if (zz > kNaMaxOcc) return set_error(MPM_ESCRATCH);
+    if (zz > out_capacity) return set_error(MPM_ECAPACITY);
+    if (zz > 0) {
+        const uint32_t key_bits =
+            ((uint32_t)bits_for(n) << 16) | (uint32_t)bits_for(h->plan.r > 1 ? h->plan.r - 1 : 1);
+        // at most kNaMaxOcc keys: the one-block sort, no temporary buffers
+        int l = mpm::launch_sort_output(occ, nullptr, nullptr, 0, zz, key_bits, out_pos, out_pid, s);
+        if (l < 0) return set_error(MPM_ECUDA);
+        h->stats.launches += (uint32_t)l;
+    }
+    return set_error(MPM_OK);
+}
