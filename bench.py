@@ -16,7 +16,6 @@ import argparse
 import json
 import os
 import statistics
-import subprocess
 import sys
 import time
 
@@ -48,59 +47,84 @@ def peaks():
 
 
 class ClockSampler:
-    """nvidia-smi clocks and throttle reasons, sampled every 200 ms."""
+    """SM clocks and clock-event (throttle) reasons of the benchmarked GPU,
+    read through NVML every 5 ms on a background thread while the timed
+    region runs (nvidia-smi's 200 ms period is longer than a short region)."""
 
-    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
-              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
-              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+    REASONS = {0x4: "sw_power_cap", 0x8: "hw_slowdown", 0x20: "sw_thermal_slowdown",
+               0x40: "hw_thermal_slowdown", 0x80: "hw_power_brake_slowdown"}
 
-    def __init__(self, gpu_index):
-        self.gpu = gpu_index
-        self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", "clocks_bench_%d.csv" % os.getpid())
+    def __init__(self, torch_index, period=0.005):
+        import threading
+        self.period = period
+        self.samples = []
+        self.max_mhz = None
+        self.handle = None
+        self._stop = threading.Event()
+        self._thread = None
+        try:
+            import ctypes
+            nv = ctypes.CDLL("libnvidia-ml.so.1")
+            if nv.nvmlInit_v2() != 0:
+                return
+            h = ctypes.c_void_p()
+            bus = None
+            try:
+                import torch
+                pr = torch.cuda.get_device_properties(torch_index)
+                bus = "%08x:%02x:%02x.0" % (pr.pci_domain_id, pr.pci_bus_id, pr.pci_device_id)
+            except Exception:
+                bus = None
+            ok = bus is not None and nv.nvmlDeviceGetHandleByPciBusId_v2(bus.encode(),
+                                                                         ctypes.byref(h)) == 0
+            if not ok and nv.nvmlDeviceGetHandleByIndex_v2(torch_index, ctypes.byref(h)) != 0:
+                return
+            self.nv, self.handle, self.ct = nv, h, ctypes
+            mx = ctypes.c_uint()
+            if nv.nvmlDeviceGetMaxClockInfo(h, 1, ctypes.byref(mx)) == 0:
+                self.max_mhz = mx.value
+        except Exception:
+            self.handle = None
+
+    def sample(self):
+        ct = self.ct
+        mhz, reasons = ct.c_uint(), ct.c_ulonglong()
+        if self.nv.nvmlDeviceGetClockInfo(self.handle, 1, ct.byref(mhz)) != 0:
+            return
+        if self.nv.nvmlDeviceGetCurrentClocksEventReasons(self.handle, ct.byref(reasons)) != 0:
+            self.nv.nvmlDeviceGetCurrentClocksThrottleReasons(self.handle, ct.byref(reasons))
+        self.samples.append((mhz.value, reasons.value))
+
+    def _run(self):
+        while not self._stop.is_set():
+            self.sample()
+            self._stop.wait(self.period)
 
     def __enter__(self):
-        try:
-            os.makedirs(os.path.dirname(self.path), exist_ok=True)
-            self.f = open(self.path, "w")
-            self.proc = subprocess.Popen(
-                ["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.FIELDS,
-                 "--format=csv,noheader,nounits", "-lms", "200"],
-                stdout=self.f, stderr=subprocess.DEVNULL)
-        except Exception:
-            self.proc = None
+        if self.handle is not None:
+            import threading
+            self.sample()
+            self._thread = threading.Thread(target=self._run, daemon=True)
+            self._thread.start()
         return self
 
     def __exit__(self, *a):
-        if self.proc:
-            self.proc.terminate()
-            try:
-                self.proc.wait(timeout=5)
-            except Exception:
-                self.proc.kill()
-            self.f.close()
+        if self._thread is not None:
+            self._stop.set()
+            self._thread.join()
+            self.sample()
 
     def summary(self):
-        if not self.proc or not os.path.exists(self.path):
+        if not self.samples:
             return None
-        sm, mx, reasons = [], None, set()
-        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for line in open(self.path):
-            parts = [x.strip() for x in line.split(",")]
-            if len(parts) < 9:
-                continue
-            try:
-                sm.append(float(parts[1]))
-                mx = float(parts[2])
-            except ValueError:
-                continue
-            for name, v in zip(names, parts[5:9]):
-                if v.lower() == "active":
+        reasons = set()
+        for _, r in self.samples:
+            for bit, name in self.REASONS.items():
+                if r & bit:
                     reasons.add(name)
-        if not sm:
-            return None
-        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons),
-                "samples": len(sm)}
+        return {"sm_mhz": statistics.median(m for m, _ in self.samples),
+                "sm_max_mhz": self.max_mhz, "reasons": sorted(reasons),
+                "samples": len(self.samples), "source": "nvml"}
 
 
 def make_case(name):
@@ -129,7 +153,9 @@ def run_reference(args, rank):
     if rank != 0:
         return
     case, sigma, desc = make_case(args.workload)
-    sample = args.ref_sample_mib << 20
+    # per-step sample: at most 64 MiB, and about 2 GiB over all steps, so
+    # that the whole run stays within a few minutes on the host cores
+    sample = max(4 << 20, min(args.ref_sample_mib << 20, (2 << 30) // max(1, args.steps)))
     from oracle import native
     threads = os.cpu_count() or 1
     ac = native.AhoCorasick(case.P)
@@ -160,11 +186,11 @@ def run_reference(args, rank):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=500)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="protein-256MiB", choices=sorted(WORKLOADS))
-    ap.add_argument("--cpu-sample-mib", type=int, default=64)
+    ap.add_argument("--cpu-sample-mib", type=int, default=256)
     ap.add_argument("--ref-sample-mib", type=int, default=64)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
@@ -277,7 +303,8 @@ def main():
             "candidates_per_step": st["candidates"],
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": traffic,
-                         "kernel": "scan_tma_kernel (+ plain-load tail)",
+                         "kernel": ("mpm_scan_jit (specialised)" if st["specialised"]
+                                    else "scan_tma_kernel (generic)"),
                          "peak_kind": peak_kind, "scan_ms": scan_avg,
                          "verify_ms": statistics.mean(verify_ms)},
             "e2e": {"value": e2e_value, "unit": "GB/s", "h2d_bytes_per_step": case.n,

@@ -69,7 +69,14 @@ extern "C" {
  *   smag     0: MAG, q-gram codes computed on the fly inside the scan;
  *            1: SMAG, the whole text is encoded first (Section 3.2).
  *   chunk    text bytes one scan thread handles before it moves on, or 0.
+ *   kernel   MPM_KERNEL_*: the scan kernel compiled at build time for
+ *            these parameters (NVRTC, sm_103a), or the precompiled generic
+ *            one; AUTO takes the specialised kernel when it compiles.
  */
+#define MPM_KERNEL_AUTO        0
+#define MPM_KERNEL_GENERIC     1
+#define MPM_KERNEL_SPECIALISED 2
+
 typedef struct {
     int q;
     int sigma_r;
@@ -79,6 +86,7 @@ typedef struct {
     int table_place;
     int smag;
     int chunk;
+    int kernel;
 } mpm_params;
 
 /* Sizes that follow from resolved parameters and m (Sections 3.1, 3.2). */
@@ -103,6 +111,8 @@ typedef struct {
     uint32_t retries;      /* re-runs after growing an internal buffer        */
     float ms_scan;         /* device time of the scan kernels (timing on)     */
     float ms_verify;       /* device time of the verification kernel          */
+    uint32_t specialised;  /* 1 if the scan ran the specialised kernel        */
+    uint32_t reserved;
 } mpm_stats;
 
 typedef struct mpm_handle mpm_handle;
@@ -113,7 +123,8 @@ typedef struct mpm_handle mpm_handle;
  * Builds the filter for r patterns of length m (row-major, r*m bytes of host
  * memory at P; copied, the caller keeps ownership).  sigma is the declared
  * alphabet size (1..256; used to choose parameters and to validate
- * sigma_r <= max(2, sigma) when sigma_r is given).  params may be NULL (all
+ * sigma_r <= the smallest power of two >= max(2, sigma) when sigma_r is
+ * given).  params may be NULL (all
  * automatic).  Host work (Sections 2, 3.2, 3.3): pattern histogram, mapping
  * mu, the q shifts of every pattern cut into non-overlapping q-grams, their
  * superimposition into the mask table, and a hash of the patterns for
@@ -188,6 +199,16 @@ int mpm_plan(const uint8_t *P, size_t r, size_t m, int sigma, const mpm_params *
 int mpm_host_tables(const uint8_t *P, size_t r, size_t m, int sigma,
                     const mpm_params *params, uint8_t *mu, void *table,
                     size_t table_bytes);
+
+/*
+ * Host-only check that the specialised scan kernel for these parameters
+ * compiles (NVRTC, sm_103a), without loading it on a device.  Returns
+ * MPM_OK, MPM_ENOTSUP (parameters outside the specialised kernel, or NVRTC
+ * missing) or MPM_ECUDA (compile error; the compiler log is copied to log,
+ * log_bytes bytes at most, when log is not NULL).
+ */
+int mpm_jit_compile(const uint8_t *P, size_t r, size_t m, int sigma, const mpm_params *params,
+                    char *log, size_t log_bytes);
 
 /* ----------------------------------------------- single steps of a search */
 

@@ -12,8 +12,9 @@ import ctypes
 
 import numpy as np
 
-from ._native import (MAP_AUTO, MAP_GREEDY, MAP_LOWBITS, MAP_RANK, MPM_ECAPACITY,  # noqa: F401
-                      MPM_EINVAL, MPM_OK, TABLE_AUTO, TABLE_GLOBAL, TABLE_SMEM, MpmError,
+from ._native import (KERNEL_AUTO, KERNEL_GENERIC, KERNEL_SPECIALISED,  # noqa: F401
+                      MAP_AUTO, MAP_GREEDY, MAP_LOWBITS, MAP_RANK, MPM_ECAPACITY, MPM_EINVAL,
+                      MPM_ENOTSUP, MPM_OK, TABLE_AUTO, TABLE_GLOBAL, TABLE_SMEM, MpmError,
                       Params, Stats, TableInfo, declared_functions, lib)
 
 __all__ = ["Matcher", "plan", "host_tables", "MpmError", "lib", "declared_functions"]
@@ -25,8 +26,18 @@ def _torch():
 
 
 def make_params(q=0, sigma_r=0, k=0, map_kind=MAP_AUTO, map_shift=-1, table_place=TABLE_AUTO,
-                smag=0, chunk=0):
-    return Params(q, sigma_r, k, map_kind, map_shift, table_place, smag, chunk)
+                smag=0, chunk=0, kernel=KERNEL_AUTO):
+    return Params(q, sigma_r, k, map_kind, map_shift, table_place, smag, chunk, kernel)
+
+
+def jit_compile(P, sigma, **kw):
+    """Host-only: compiles the specialised scan for these parameters;
+    returns (code, compiler log)."""
+    P = _patterns(P)
+    buf = ctypes.create_string_buffer(1 << 16)
+    rc = lib().mpm_jit_compile(P.ctypes.data, P.shape[0], P.shape[1], sigma,
+                               ctypes.byref(make_params(**kw)), buf, len(buf))
+    return rc, buf.value.decode(errors="replace")
 
 
 def _patterns(P):

@@ -17,12 +17,14 @@ NOALLOC_MAX_CANDIDATES = 1 << 21
 NOALLOC_MAX_OCCURRENCES = 8192
 MAP_AUTO, MAP_RANK, MAP_GREEDY, MAP_LOWBITS = range(4)
 TABLE_AUTO, TABLE_SMEM, TABLE_GLOBAL = range(3)
+KERNEL_AUTO, KERNEL_GENERIC, KERNEL_SPECIALISED = range(3)
 
 
 class Params(ctypes.Structure):
     _fields_ = [("q", ctypes.c_int), ("sigma_r", ctypes.c_int), ("k", ctypes.c_int),
                 ("map_kind", ctypes.c_int), ("map_shift", ctypes.c_int),
-                ("table_place", ctypes.c_int), ("smag", ctypes.c_int), ("chunk", ctypes.c_int)]
+                ("table_place", ctypes.c_int), ("smag", ctypes.c_int), ("chunk", ctypes.c_int),
+                ("kernel", ctypes.c_int)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}
@@ -41,7 +43,8 @@ class Stats(ctypes.Structure):
     _fields_ = [("n", ctypes.c_uint64), ("sampled", ctypes.c_uint64),
                 ("candidates", ctypes.c_uint64), ("z", ctypes.c_uint64),
                 ("launches", ctypes.c_uint32), ("retries", ctypes.c_uint32),
-                ("ms_scan", ctypes.c_float), ("ms_verify", ctypes.c_float)]
+                ("ms_scan", ctypes.c_float), ("ms_verify", ctypes.c_float),
+                ("specialised", ctypes.c_uint32), ("reserved", ctypes.c_uint32)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}
@@ -90,6 +93,7 @@ def lib():
         "mpm_encode": (ctypes.c_int, [vp, u8p, sz, vp]),
         "mpm_scan": (ctypes.c_int, [vp, u8p, sz, vp, szp]),
         "mpm_search_noalloc": (ctypes.c_int, [vp, u8p, sz, vp, vp, szp]),
+        "mpm_jit_compile": (ctypes.c_int, [u8p, sz, sz, ctypes.c_int, Pp, ctypes.c_char_p, sz]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(L, name)

@@ -18,7 +18,11 @@ INCLUDE = os.path.join(ROOT, "include")
 OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "libmpm.so")
 
-SOURCES = ["host_build.cpp", "capi.cu", "scan.cu", "encode.cu", "verify.cu", "sort.cu"]
+SOURCES = ["host_build.cpp", "capi.cu", "scan.cu", "encode.cu", "verify.cu", "sort.cu", "jit.cpp"]
+# files concatenated, in this order, into the source of the scan kernel that
+# is compiled at run time
+JIT_PARTS = ["scan_jit_args.h", "ptx_common.cuh", "scan_jit.cuh"]
+GEN = os.path.join(OUT, "gen")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
@@ -31,7 +35,22 @@ def _nvcc():
 
 def _flags():
     return ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC",
-                   "-I" + INCLUDE, "-I" + CSRC]
+                   "-I" + INCLUDE, "-I" + CSRC, "-I" + GEN]
+
+
+def _write_jit_source():
+    """Embeds the run-time compiled kernel's source as a C++ raw string."""
+    os.makedirs(GEN, exist_ok=True)
+    text = ""
+    for part in JIT_PARTS:
+        with open(os.path.join(CSRC, part)) as f:
+            text += "// ---- %s\n" % part + f.read().replace("#pragma once", "") + "\n"
+    assert ")MPMJIT\"" not in text
+    out = os.path.join(GEN, "scan_jit_src.inc")
+    body = 'R"MPMJIT(' + text + ')MPMJIT"\n'
+    if not os.path.exists(out) or open(out).read() != body:
+        with open(out, "w") as f:
+            f.write(body)
 
 
 def _deps_mtime():
@@ -45,6 +64,7 @@ def build(force=False, verbose=False):
     if not force and os.path.exists(LIB) and os.path.getmtime(LIB) >= _deps_mtime():
         return LIB
     nvcc = _nvcc()
+    _write_jit_source()
     objdir = os.path.join(OUT, "obj")
     os.makedirs(objdir, exist_ok=True)
 
@@ -63,7 +83,7 @@ def build(force=False, verbose=False):
     with concurrent.futures.ThreadPoolExecutor(max_workers=len(SOURCES)) as ex:
         objs = list(ex.map(compile_one, SOURCES))
     tmp = LIB + ".%d.tmp" % os.getpid()
-    cmd = [nvcc] + ARCH + ["-shared", "-Xcompiler", "-fPIC", "-o", tmp] + objs
+    cmd = [nvcc] + ARCH + ["-shared", "-Xcompiler", "-fPIC", "-o", tmp] + objs + ["-ldl"]
     p = subprocess.run(cmd, capture_output=True, text=True)
     if p.returncode != 0:
         raise RuntimeError("link failed:\n%s\n%s" % (" ".join(cmd), p.stderr))

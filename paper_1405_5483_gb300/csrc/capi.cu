@@ -10,6 +10,7 @@
 #include <cstring>
 #include <mutex>
 #include <new>
+#include <string>
 
 #include "kernels.h"
 
@@ -45,6 +46,7 @@ struct mpm_handle {
     size_t out_cap = 0;
 
     mpm_stats stats{};
+    const mpm::JitKernel* jit = nullptr;  // specialised scan, when compiled
     int timing = 0;
     cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};
 };
@@ -129,6 +131,12 @@ void release(mpm_handle* h) {
     delete h;
 }
 
+// The scan kernel the handle uses: the specialised one when it compiled.
+int scan_launch(const mpm_handle* h, const mpm::ScanArgs& a, cudaStream_t s) {
+    if (h->jit) return mpm::launch_scan_jit(a, h->jit, h->num_sms, h->plan.p.chunk, s);
+    return mpm::launch_scan(a, h->num_sms, h->plan.p.chunk, s);
+}
+
 int bits_for(uint64_t v) {
     int b = 0;
     while (b < 64 && (v >> b)) b++;
@@ -162,7 +170,7 @@ int run_filter(mpm_handle* h, const uint8_t* dT, uint32_t n, int* launches) {
         a.cap = (uint32_t)h->cand_cap;
         a.counters = h->d_counters;
         if (h->timing) cudaEventRecord(h->ev[0], s);
-        l = mpm::launch_scan(a, h->num_sms, h->plan.p.chunk, s);
+        l = scan_launch(h, a, s);
         if (h->timing) cudaEventRecord(h->ev[1], s);
         if (l == -2) return MPM_ENOTSUP;
     }
@@ -293,6 +301,17 @@ mpm_handle* mpm_build(const uint8_t* P, size_t r, size_t m, int sigma, const mpm
     }
     h->host.table.clear();
     h->host.table.shrink_to_fit();
+    if (!h->plan.p.smag && h->plan.p.kernel != MPM_KERNEL_GENERIC) {
+        int err = MPM_OK;
+        std::string log;
+        h->jit = mpm::jit_scan_kernel(filter_dev(h), h->device, &err, &log);
+        if (!h->jit && h->plan.p.kernel == MPM_KERNEL_SPECIALISED) {
+            if (!log.empty()) std::fprintf(stderr, "mpm: specialised scan failed:\n%s\n", log.c_str());
+            release(h);
+            set_error(err ? err : MPM_ENOTSUP);
+            return nullptr;
+        }
+    }
     set_error(MPM_OK);
     return h;
 }
@@ -340,6 +359,7 @@ int mpm_search(mpm_handle* h, const uint8_t* T, size_t n, uint32_t* out_pos, uin
     const size_t out_capacity = *z;
     h->stats = mpm_stats{};
     h->stats.n = n;
+    h->stats.specialised = h->jit && !h->plan.p.smag ? 1u : 0u;
     const uint32_t q = (uint32_t)h->plan.p.q, k = (uint32_t)h->plan.p.k;
     h->stats.sampled = (n / q) / k;
     int launches = 0;
@@ -423,6 +443,32 @@ int mpm_search(mpm_handle* h, const uint8_t* T, size_t n, uint32_t* out_pos, uin
     return set_error(MPM_OK);
 }
 
+int mpm_jit_compile(const uint8_t* P, size_t r, size_t m, int sigma, const mpm_params* params,
+                    char* log, size_t log_bytes) {
+    mpm::Plan plan;
+    int rc = mpm::make_plan(P, r, m, sigma, params, &plan);
+    if (rc) return set_error(rc);
+    mpm::FilterDev f{};
+    f.table_bytes = (uint32_t)((plan.info.table_bytes + 15) & ~uint64_t(15));
+    f.entry_bytes = plan.info.entry_bytes;
+    f.smem_table = plan.p.table_place == MPM_TABLE_SMEM;
+    f.map_kind = plan.p.map_kind;
+    f.q = plan.p.q;
+    f.k = plan.p.k;
+    f.ell = plan.ell;
+    f.shift = plan.p.map_shift;
+    f.mprime = plan.info.mprime;
+    f.positions = plan.info.positions;
+    std::string text;
+    rc = mpm::jit_compile_only(f, &text);
+    if (log && log_bytes) {
+        const size_t c = std::min(log_bytes - 1, text.size());
+        std::memcpy(log, text.data(), c);
+        log[c] = 0;
+    }
+    return set_error(rc);
+}
+
 int mpm_encode(mpm_handle* h, const uint8_t* T, size_t n, uint32_t* codes) {
     if (!h || (n > 0 && (!T || !codes)) || n >= (1ull << 32)) return set_error(MPM_EINVAL);
     int rc = prepare(h);
@@ -461,7 +507,7 @@ int mpm_scan(mpm_handle* h, const uint8_t* T, size_t n, uint64_t* cand, size_t* 
         a.cand = cand;
         a.cap = (uint32_t)*count;
         a.counters = h->d_counters;
-        l = mpm::launch_scan(a, h->num_sms, h->plan.p.chunk, s);
+        l = scan_launch(h, a, s);
         if (l == -2) return set_error(MPM_ENOTSUP);
     }
     if (l < 0) return set_error(MPM_ECUDA);
@@ -475,6 +521,7 @@ int mpm_scan(mpm_handle* h, const uint8_t* T, size_t n, uint64_t* cand, size_t* 
     h->stats = mpm_stats{};
     h->stats.n = n;
     h->stats.candidates = *count;
+    h->stats.specialised = h->jit && !h->plan.p.smag ? 1u : 0u;
     return set_error(*count > cap ? MPM_ECAPACITY : MPM_OK);
 }
 
@@ -543,6 +590,7 @@ extern "C" int mpm_search_noalloc(mpm_handle* h, const uint8_t* T, size_t n, uin
     h->stats = mpm_stats{};
     h->stats.n = n;
     h->stats.sampled = (n / (uint32_t)h->plan.p.q) / (uint32_t)h->plan.p.k;
+    h->stats.specialised = h->jit ? 1u : 0u;
     if (n < h->plan.m) {
         *z = 0;
         return set_error(MPM_OK);
@@ -561,7 +609,7 @@ extern "C" int mpm_search_noalloc(mpm_handle* h, const uint8_t* T, size_t n, uin
     a.cand = cand;
     a.cap = (uint32_t)kNaMaxCand;
     a.counters = counters;
-    int launches = mpm::launch_scan(a, h->num_sms, h->plan.p.chunk, s);
+    int launches = scan_launch(h, a, s);
     if (launches == -2) return set_error(MPM_ENOTSUP);
     if (launches < 0) return set_error(MPM_ECUDA);
     mpm::VerifyArgs v{};

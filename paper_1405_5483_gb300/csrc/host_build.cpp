@@ -208,13 +208,14 @@ int make_plan(const uint8_t* P, size_t r, size_t m, int sigma, const mpm_params*
     if (req.q < 0 || req.q > 16) return MPM_EINVAL;
     if (req.sigma_r != 0 &&
         (!is_pow2(req.sigma_r) || req.sigma_r < 2 || req.sigma_r > 256 ||
-         req.sigma_r > std::max(2, sigma)))
+         req.sigma_r > std::max(2, pow2_ceil(sigma))))
         return MPM_EINVAL;
     if (req.k < 0 || req.k > kMaxK) return MPM_EINVAL;
     if (req.map_kind < 0 || req.map_kind > MPM_MAP_LOWBITS) return MPM_EINVAL;
     if (req.map_shift > 7) return MPM_EINVAL;
     if (req.table_place < 0 || req.table_place > MPM_TABLE_GLOBAL) return MPM_EINVAL;
     if (req.smag < 0 || req.smag > 1 || req.chunk < 0) return MPM_EINVAL;
+    if (req.kernel < MPM_KERNEL_AUTO || req.kernel > MPM_KERNEL_SPECIALISED) return MPM_EINVAL;
 
     uint64_t h[256];
     histogram(P, r, m, h);

@@ -1,0 +1,341 @@
+// Run-time specialisation of the scan kernel (scan_jit.cuh).
+//
+// mpm_build compiles the kernel once per distinct filter (q, k, m', symbol
+// width, shift, map kind, entry width, table placement) with NVRTC for
+// sm_103a, loads the cubin into the device's primary context and keeps it in
+// a process-wide cache.  NVRTC is opened with dlopen, so the library loads
+// and the generic kernel runs where NVRTC is absent.
+#include <dlfcn.h>
+
+#include <algorithm>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <map>
+#include <memory>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include <cudaTypedefs.h>
+#include <nvrtc.h>
+
+#include "kernels.h"
+#include "scan_jit_args.h"
+
+namespace mpm {
+
+namespace {
+
+const char kJitSource[] =
+#include "scan_jit_src.inc"
+    ;
+
+struct NvrtcApi {
+    bool ok = false;
+    nvrtcResult (*create)(nvrtcProgram*, const char*, const char*, int, const char* const*,
+                          const char* const*) = nullptr;
+    nvrtcResult (*compile)(nvrtcProgram, int, const char* const*) = nullptr;
+    nvrtcResult (*log_size)(nvrtcProgram, size_t*) = nullptr;
+    nvrtcResult (*log)(nvrtcProgram, char*) = nullptr;
+    nvrtcResult (*cubin_size)(nvrtcProgram, size_t*) = nullptr;
+    nvrtcResult (*cubin)(nvrtcProgram, char*) = nullptr;
+    nvrtcResult (*destroy)(nvrtcProgram*) = nullptr;
+};
+
+const NvrtcApi& nvrtc() {
+    static NvrtcApi api;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        std::vector<std::string> names;
+        if (const char* e = std::getenv("MPM_NVRTC")) names.push_back(e);
+        names.push_back("libnvrtc.so.13");
+        names.push_back("libnvrtc.so");
+        if (const char* e = std::getenv("CUDA_HOME"))
+            names.push_back(std::string(e) + "/lib64/libnvrtc.so.13");
+        names.push_back("/usr/local/cuda/lib64/libnvrtc.so.13");
+        names.push_back("/usr/local/cuda/lib64/libnvrtc.so");
+        void* h = nullptr;
+        for (auto& n : names)
+            if ((h = dlopen(n.c_str(), RTLD_NOW | RTLD_LOCAL))) break;
+        if (!h) return;
+        api.create = reinterpret_cast<decltype(api.create)>(dlsym(h, "nvrtcCreateProgram"));
+        api.compile = reinterpret_cast<decltype(api.compile)>(dlsym(h, "nvrtcCompileProgram"));
+        api.log_size = reinterpret_cast<decltype(api.log_size)>(dlsym(h, "nvrtcGetProgramLogSize"));
+        api.log = reinterpret_cast<decltype(api.log)>(dlsym(h, "nvrtcGetProgramLog"));
+        api.cubin_size = reinterpret_cast<decltype(api.cubin_size)>(dlsym(h, "nvrtcGetCUBINSize"));
+        api.cubin = reinterpret_cast<decltype(api.cubin)>(dlsym(h, "nvrtcGetCUBIN"));
+        api.destroy = reinterpret_cast<decltype(api.destroy)>(dlsym(h, "nvrtcDestroyProgram"));
+        api.ok = api.create && api.compile && api.log_size && api.log && api.cubin_size &&
+                 api.cubin && api.destroy;
+    });
+    return api;
+}
+
+struct DriverApi {
+    bool ok = false;
+    PFN_cuModuleLoadData_v2000 load = nullptr;
+    PFN_cuModuleGetFunction_v2000 get = nullptr;
+    PFN_cuFuncSetAttribute_v9000 set_attr = nullptr;
+    PFN_cuLaunchKernel_v4000 launch = nullptr;
+    PFN_cuOccupancyMaxActiveBlocksPerMultiprocessor_v6050 occupancy = nullptr;
+    PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
+};
+
+template <typename F>
+void entry(const char* name, unsigned ver, F* out) {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion(name, &p, ver, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+        *out = reinterpret_cast<F>(p);
+    else
+        cudaGetLastError();
+}
+
+const DriverApi& driver() {
+    static DriverApi api;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        entry("cuModuleLoadData", 2000, &api.load);
+        entry("cuModuleGetFunction", 2000, &api.get);
+        entry("cuFuncSetAttribute", 9000, &api.set_attr);
+        entry("cuLaunchKernel", 4000, &api.launch);
+        entry("cuOccupancyMaxActiveBlocksPerMultiprocessor", 6050, &api.occupancy);
+        entry("cuTensorMapEncodeTiled", 12000, &api.encode);
+        api.ok = api.load && api.get && api.set_attr && api.launch && api.occupancy && api.encode;
+    });
+    return api;
+}
+
+uint32_t gcd_u(uint32_t a, uint32_t b) {
+    while (b) {
+        uint32_t t = a % b;
+        a = b;
+        b = t;
+    }
+    return a;
+}
+
+uint32_t lcm_u(uint32_t a, uint32_t b) { return a / gcd_u(a, b) * b; }
+
+constexpr size_t kSmemLimit = 227 * 1024;
+
+}  // namespace
+
+// Compile-time constants of one specialisation and its launch geometry.
+struct JitSpec {
+    int q, k, mp, ell, shift, mode, eb, smem, table_bytes, C, S, warps;
+    size_t smem_bytes;
+
+    std::string defines() const {
+        char buf[512];
+        std::snprintf(buf, sizeof(buf),
+                      "-DMPM_Q=%d -DMPM_K=%d -DMPM_MP=%d -DMPM_ELL=%d -DMPM_SHIFT=%d "
+                      "-DMPM_MODE=%d -DMPM_EB=%d -DMPM_SMEM=%d -DMPM_TABLE_BYTES=%du "
+                      "-DMPM_C=%d -DMPM_S=%d -DMPM_WARPS=%d",
+                      q, k, mp, ell, shift, mode, eb, smem, table_bytes, C, S, warps);
+        return buf;
+    }
+};
+
+struct JitKernel {
+    JitSpec spec;
+    CUfunction fn = nullptr;
+    int blocks_per_sm = 1;
+};
+
+// The specialisation for a filter, or false when the filter is outside what
+// the specialised kernel handles (then the generic kernel runs).
+bool jit_spec(const FilterDev& f, JitSpec* out) {
+    JitSpec s{};
+    s.q = f.q;
+    s.k = f.k;
+    s.mp = f.mprime;
+    s.ell = f.ell;
+    s.shift = f.map_kind == MPM_MAP_LOWBITS ? f.shift : 0;
+    s.mode = f.map_kind == MPM_MAP_LOWBITS ? 0 : 1;
+    s.eb = f.entry_bytes;
+    s.smem = f.smem_table ? 1 : 0;
+    s.table_bytes = f.smem_table ? (int)f.table_bytes : 0;
+    const uint32_t P = (uint32_t)(f.k * f.q);
+    const uint32_t base = lcm_u(P, 16);
+    if (base > 256) return false;
+    uint32_t C = base;
+    if ((base / 16) % 2 == 1)
+        while (C + 2 * base <= 48) C += 2 * base;  // odd multiples keep C/16 odd
+    if ((C / P) * (uint32_t)f.k > 64) return false;
+    s.C = (int)C;
+    s.warps = C <= 48 ? 32 : 16;
+    const size_t fixed = (size_t)s.table_bytes + 256 + 8 * 32 * 4 + 128;
+    for (;;) {
+        const size_t per_stage = (size_t)s.warps * 32 * C;
+        const size_t budget = kSmemLimit > fixed ? kSmemLimit - fixed : 0;
+        s.S = (int)std::min<size_t>(4, budget / per_stage);
+        if (s.S >= 2) break;
+        if (s.warps <= 4) return false;
+        s.warps /= 2;
+    }
+    const size_t stage_off = ((size_t)s.table_bytes + 256 + 8 * s.warps * s.S + 127) / 128 * 128;
+    s.smem_bytes = stage_off + (size_t)s.warps * s.S * 32 * C;
+    *out = s;
+    return true;
+}
+
+static int compile_spec(const JitSpec& s, std::string* cubin, std::string* log) {
+    const NvrtcApi& nv = nvrtc();
+    if (!nv.ok) {
+        if (log) *log = "NVRTC not found";
+        return MPM_ENOTSUP;
+    }
+    nvrtcProgram prog;
+    if (nv.create(&prog, kJitSource, "mpm_scan_jit.cu", 0, nullptr, nullptr) != NVRTC_SUCCESS)
+        return MPM_ECUDA;
+    std::vector<std::string> opts = {"--gpu-architecture=sm_103a", "--std=c++17", "-lineinfo"};
+    if (std::getenv("MPM_JIT_VERBOSE")) opts.push_back("--ptxas-options=-v");
+    {
+        std::string d = s.defines();
+        size_t pos = 0;
+        while (pos < d.size()) {
+            size_t e = d.find(' ', pos);
+            if (e == std::string::npos) e = d.size();
+            if (e > pos) opts.push_back(d.substr(pos, e - pos));
+            pos = e + 1;
+        }
+    }
+    std::vector<const char*> argv;
+    for (auto& o : opts) argv.push_back(o.c_str());
+    const nvrtcResult rc = nv.compile(prog, (int)argv.size(), argv.data());
+    size_t ls = 0;
+    nv.log_size(prog, &ls);
+    if (log) {
+        log->assign(ls, '\0');
+        if (ls) nv.log(prog, &(*log)[0]);
+    }
+    int ret = MPM_OK;
+    if (rc != NVRTC_SUCCESS) {
+        ret = MPM_ECUDA;
+    } else if (cubin) {
+        size_t cs = 0;
+        nv.cubin_size(prog, &cs);
+        cubin->assign(cs, '\0');
+        if (!cs || nv.cubin(prog, &(*cubin)[0]) != NVRTC_SUCCESS) ret = MPM_ECUDA;
+    }
+    nv.destroy(&prog);
+    return ret;
+}
+
+int jit_compile_only(const FilterDev& f, std::string* log) {
+    JitSpec s;
+    if (!jit_spec(f, &s)) {
+        if (log) *log = "filter outside the specialised kernel";
+        return MPM_ENOTSUP;
+    }
+    std::string cubin;
+    return compile_spec(s, &cubin, log);
+}
+
+const JitKernel* jit_scan_kernel(const FilterDev& f, int device, int* err, std::string* log) {
+    static std::mutex mu;
+    static std::map<std::string, std::unique_ptr<JitKernel>> cache;
+    *err = MPM_OK;
+    JitSpec s;
+    if (!jit_spec(f, &s)) {
+        *err = MPM_ENOTSUP;
+        return nullptr;
+    }
+    const DriverApi& drv = driver();
+    if (!drv.ok) {
+        *err = MPM_ENOTSUP;
+        return nullptr;
+    }
+    const std::string key = std::to_string(device) + " " + s.defines();
+    std::lock_guard<std::mutex> lock(mu);
+    auto it = cache.find(key);
+    if (it != cache.end()) return it->second.get();
+    std::string cubin;
+    int rc = compile_spec(s, &cubin, log);
+    if (rc) {
+        *err = rc;
+        return nullptr;
+    }
+    CUmodule mod;
+    CUfunction fn;
+    if (drv.load(&mod, cubin.data()) != CUDA_SUCCESS ||
+        drv.get(&fn, mod, "mpm_scan_jit") != CUDA_SUCCESS ||
+        drv.set_attr(fn, CU_FUNC_ATTRIBUTE_MAX_DYNAMIC_SHARED_SIZE_BYTES, (int)s.smem_bytes) !=
+            CUDA_SUCCESS) {
+        *err = MPM_ECUDA;
+        return nullptr;
+    }
+    auto k = std::make_unique<JitKernel>();
+    k->spec = s;
+    k->fn = fn;
+    int per_sm = 0;
+    if (drv.occupancy(&per_sm, fn, s.warps * 32, s.smem_bytes) != CUDA_SUCCESS || per_sm < 1)
+        per_sm = 1;
+    k->blocks_per_sm = per_sm;
+    const JitKernel* out = k.get();
+    cache.emplace(key, std::move(k));
+    return out;
+}
+
+int launch_scan_jit(const ScanArgs& A, const JitKernel* K, int num_sms, int chunk,
+                    cudaStream_t stream) {
+    if (A.n == 0) return 0;
+    const DriverApi& drv = driver();
+    const JitSpec& s = K->spec;
+    const uint32_t n = A.n;
+    const uint32_t C = (uint32_t)s.C;
+    const uint32_t P = (uint32_t)(s.k * s.q);
+    const uint32_t blocks = (uint32_t)(num_sms * K->blocks_per_sm);
+    const uint32_t GW = blocks * (uint32_t)s.warps;
+    const uint32_t warm = ((uint32_t)((s.mp - 1) * s.q * s.k) + C - 1) / C * C;
+    const uint32_t row_warps = GW > 1 ? GW - 1 : 1;
+    uint64_t Lst = chunk > 0 ? (uint64_t)chunk : ((uint64_t)n + 32ull * row_warps - 1) / (32ull * row_warps);
+    Lst = (Lst + C - 1) / C * C;
+    Lst = std::max<uint64_t>(Lst, std::max<uint64_t>(4ull * C, warm + C));
+    const bool aligned = (reinterpret_cast<uintptr_t>(A.T) & 15) == 0;
+    const uint64_t R = aligned ? n / Lst : 0;
+
+    JitScanArgs J{};
+    J.T = A.T;
+    J.table = A.f.table;
+    J.mu = A.f.mu;
+    J.cand = reinterpret_cast<unsigned long long*>(A.cand);
+    J.counters = A.counters;
+    J.n = n;
+    J.cap = A.cap;
+    J.Lst = (uint32_t)Lst;
+    J.R = (uint32_t)R;
+    J.RG = (uint32_t)((R + 31) / 32);
+    J.row_warps = row_warps;
+    J.pa = (uint32_t)(R * Lst);
+    const uint32_t rest = n - J.pa;
+    const uint32_t lanes = R > 0 ? 32u : GW * 32u;
+    uint32_t Ls = (rest + lanes - 1) / lanes;
+    Ls = std::max<uint32_t>((Ls + P - 1) / P * P, 4 * P);
+    J.Ls = Ls;
+    J.nstreams = rest ? (rest + Ls - 1) / Ls : 0;
+
+    alignas(64) CUtensorMap tmap;
+    std::memset(&tmap, 0, sizeof(tmap));
+    if (R > 0) {
+        cuuint64_t dims[2] = {Lst, R};
+        cuuint64_t strides[1] = {Lst};
+        cuuint32_t box[2] = {C, 32};
+        cuuint32_t estr[2] = {1, 1};
+        if (drv.encode(&tmap, CU_TENSOR_MAP_DATA_TYPE_UINT8, 2, const_cast<uint8_t*>(A.T), dims,
+                       strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                       CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                       CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+            return -1;
+    }
+    void* params[2] = {&J, &tmap};
+    if (drv.launch(K->fn, blocks, 1, 1, (unsigned)(s.warps * 32), 1, 1, (unsigned)s.smem_bytes,
+                   reinterpret_cast<CUstream>(stream), params, nullptr) != CUDA_SUCCESS)
+        return -1;
+    return 1;
+}
+
+}  // namespace mpm

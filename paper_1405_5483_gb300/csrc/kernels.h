@@ -2,6 +2,7 @@
 #pragma once
 
 #include <cstdint>
+#include <string>
 #include <cuda.h>
 #include <cuda_runtime.h>
 
@@ -75,6 +76,16 @@ int launch_scan_codes(const uint32_t* codes, uint32_t nq, const FilterDev& f, ui
                       uint32_t cap, uint32_t* counters, cudaStream_t s);
 
 int launch_verify(const VerifyArgs& a, int num_sms, cudaStream_t s);
+
+// The scan specialised at run time for one filter (jit.cpp).
+struct JitKernel;
+// Compiles (NVRTC) and loads the specialised scan for this filter on the
+// current device, cached per process; nullptr with *err = MPM_ENOTSUP when
+// the filter is outside the specialised kernel or NVRTC is missing.
+const JitKernel* jit_scan_kernel(const FilterDev& f, int device, int* err, std::string* log);
+// Host-only: compiles the specialisation without loading it.
+int jit_compile_only(const FilterDev& f, std::string* log);
+int launch_scan_jit(const ScanArgs& a, const JitKernel* k, int num_sms, int chunk, cudaStream_t s);
 
 // Sorts z keys (in d_keys, device count unknown to the kernels: z is passed)
 // and writes out_pos/out_pid.  tmp must hold z keys; returns launches or -1.

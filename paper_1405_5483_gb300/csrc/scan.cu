@@ -53,7 +53,7 @@ struct Stepper {
 
     __device__ __forceinline__ void push(uint32_t x) {
         if (MODE == kLow2) {
-            uint32_t y = (x >> shift) & 0x03030303u;
+            uint32_t y = (x >> shift) & lowmask4;
             W = (W << 8) | ((y * 0x40100401u) >> 24);
         } else if (MODE == kLowG) {
             uint32_t y = (x >> shift) & lowmask4;
@@ -93,7 +93,8 @@ struct Stepper {
         shift = f.shift;
         raw_base = 8 * (8 - f.q);
         qmask = (f.q * f.ell >= 32) ? 0xFFFFFFFFu : ((1u << (f.q * f.ell)) - 1u);
-        lowmask4 = (uint32_t)((1u << f.ell) - 1u) * 0x01010101u;
+        // per byte: the ell bits above the shift, never bits of the next byte
+        lowmask4 = (((1u << f.ell) - 1u) & (0xFFu >> f.shift)) * 0x01010101u;
         W = 0;
         D = ~(DT)0;
     }

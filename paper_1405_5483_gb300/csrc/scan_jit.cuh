@@ -1,0 +1,327 @@
+// Specialised MAG scan: the fused encode + average-optimal Shift-Or filter
+// of Sections 3.1 and 3.2 with the filter's parameters compiled in.  This
+// file is compiled at run time (NVRTC) once per parameter set, after
+// scan_jit_args.h and ptx_common.cuh, with these macros defined:
+//   MPM_Q, MPM_K      q-gram length and sampling step
+//   MPM_MP            AOSO subpattern length m' (filter positions k*m')
+//   MPM_ELL, MPM_SHIFT reduced symbol width log2(sigma') and, for the
+//                     low-bit map, the right shift applied to each byte
+//   MPM_MODE          0: low-bit map (Section 3.3, combined mapping and
+//                     q-gram generation), 1: byte map mu through a table
+//   MPM_EB            bytes per mask-table entry (1, 2, 4, 8)
+//   MPM_SMEM          1: mask table copied to shared memory
+//   MPM_TABLE_BYTES   mask-table bytes (padded to 16)
+//   MPM_C             bytes of a row per stage: a multiple of 16 and of k*q
+//   MPM_S, MPM_WARPS  stages per warp, warps per block
+//
+// Layout and flow.  Rows of Lst bytes (a multiple of C, starting on a
+// multiple of k*q) are owned by threads; a warp streams its 32 rows through
+// shared memory with 2-D TMA boxes of 32 rows x C bytes, MPM_S stages deep,
+// on its own mbarriers.  Because C is a multiple of P = k*q, every stage
+// holds exactly C/P sampled q-grams at the same byte offsets: the sampled
+// q-gram u of a stage is bytes [u*P + (k-1)*q, (u+1)*P).  The per-stage loop
+// is therefore straight-line code with constant offsets: cut the q-gram
+// code, one table lookup, D <- (D << k) | B[code], and the k report bits of
+// D go into a per-stage bit mask.  Only after the stage, if some lane of the
+// warp has a bit set, are records (fired << 32) | h appended, one atomicAdd
+// per warp and round.  The bytes after the last full row are scanned by the
+// last lanes of the grid with plain loads while the other warps stream rows.
+
+typedef unsigned char u8;
+typedef unsigned short u16;
+typedef unsigned int u32;
+typedef unsigned long long u64;
+typedef long long i64;
+
+namespace mpm {
+
+template <bool B, class X, class Y>
+struct Cond {
+    typedef X T;
+};
+template <class X, class Y>
+struct Cond<false, X, Y> {
+    typedef Y T;
+};
+
+constexpr int Q = MPM_Q, K = MPM_K, MP = MPM_MP, ELL = MPM_ELL, SHIFT = MPM_SHIFT;
+constexpr int P = Q * K;
+constexpr int C = MPM_C;
+constexpr int NS = C / P;
+constexpr int S = MPM_S;
+constexpr int WARPS = MPM_WARPS;
+constexpr int WB = (MP - 1) * P;  // bytes of the samples that precede a row
+constexpr int WSTAGES = (WB + C - 1) / C;
+constexpr int RSH = (MP - 1) * K;
+constexpr u32 KMASK = K >= 32 ? 0xFFFFFFFFu : ((1u << K) - 1u);
+constexpr u32 QMASK = Q * ELL >= 32 ? 0xFFFFFFFFu : ((1u << (Q * ELL)) - 1u);
+constexpr u32 SYMMASK = ((1u << ELL) - 1u) & (0xFFu >> SHIFT);
+constexpr u32 SLOT = 32u * C;
+
+#if MPM_EB == 1
+typedef u8 ET;
+#elif MPM_EB == 2
+typedef u16 ET;
+#elif MPM_EB == 4
+typedef u32 ET;
+#else
+typedef u64 ET;
+#endif
+typedef Cond<(MPM_EB == 8), u64, u32>::T DT;
+typedef Cond<(NS * K > 32), u64, u32>::T FT;
+
+enum { kCandCountJ = 0, kOccCountJ = 1, kErrorFlagJ = 2 };
+
+static_assert(C % 16 == 0 && C % P == 0, "stage bytes");
+static_assert(NS * K <= 64, "fired mask");
+
+// Reduced symbols of the four bytes of a word, first byte most significant.
+__device__ __forceinline__ u32 pack_word(u32 x) {
+    if (ELL == 2) {
+        const u32 y = (x >> SHIFT) & (SYMMASK * 0x01010101u);
+        return (y * 0x40100401u) >> 24;  // the multiply trick of Section 3.3
+    } else if (ELL == 1) {
+        const u32 y = (x >> SHIFT) & (SYMMASK * 0x01010101u);
+        return (y * 0x80402010u) >> 28;
+    } else if (ELL == 4) {
+        const u32 y = (x >> SHIFT) & (SYMMASK * 0x01010101u);
+        const u32 z = __byte_perm(y, 0, 0x0123);
+        const u32 t = (z & 0x000F000Fu) | ((z >> 4) & 0x00F000F0u);
+        return (t & 0xFFu) | ((t >> 8) & 0xFF00u);
+    } else {
+        u32 v = 0;
+#pragma unroll
+        for (int j = 0; j < 4; j++) v = (v << ELL) | ((x >> (8 * j + SHIFT)) & SYMMASK);
+        return v;
+    }
+}
+
+// Code of the q-gram at byte offset o of the stage (o constant after
+// unrolling), first symbol most significant.
+__device__ __forceinline__ u32 code_at(const u32* w, const u32* rw, const u8* smu, int o) {
+    if (MPM_MODE == 0) {
+        const int first = o >> 2, last = (o + Q - 1) >> 2;
+        u64 acc = 0;
+#pragma unroll
+        for (int i = first; i <= last; i++) acc = (acc << (4 * ELL)) | rw[i];
+        const int after = (last + 1) * 4 - (o + Q);
+        return (u32)(acc >> (after * ELL)) & QMASK;
+    } else {
+        u32 c = 0;
+#pragma unroll
+        for (int t = 0; t < Q; t++) {
+            const int p = o + t;
+            const u32 b = (w[p >> 2] >> (8 * (p & 3))) & 0xFFu;
+            c = (c << ELL) | smu[b];
+        }
+        return c;
+    }
+}
+
+// One stage of C bytes: the NS sampled q-grams fold into D; with REPORT the
+// report bits after each go into fm (k bits per sample).
+template <bool REPORT>
+__device__ __forceinline__ void run_stage(const u32* w, DT& D, FT& fm, const ET* tab,
+                                          const u8* smu) {
+    u32 rw[C / 4];
+    if (MPM_MODE == 0) {
+#pragma unroll
+        for (int i = 0; i < C / 4; i++) rw[i] = pack_word(w[i]);
+    }
+#pragma unroll
+    for (int u = 0; u < NS; u++) {
+        const u32 c = code_at(w, rw, smu, u * P + (K - 1) * Q);
+        D = (D << K) | (DT)tab[c];
+        if (REPORT) fm |= ((FT)((u32)(~D >> RSH) & KMASK)) << (u * K);
+    }
+}
+
+// Appends the records of one stage: for every lane, every sample u with
+// report bits, ((bits) << 32) | (h0 + u*k + k-1).
+__device__ __forceinline__ void emit_stage(FT fm, u32 h0, u64* cand, u32 cap, u32* counters) {
+    const int lane = threadIdx.x & 31;
+    while (true) {
+        const bool has = fm != 0;
+        const u32 bal = __ballot_sync(0xFFFFFFFFu, has);
+        if (bal == 0) break;
+        u32 h = 0, fired = 0;
+        if (has) {
+            const int bit = (sizeof(FT) == 8) ? (__ffsll((long long)fm) - 1) : (__ffs((int)fm) - 1);
+            const int u = bit / K;
+            fired = (u32)(fm >> (u * K)) & KMASK;
+            fm &= ~((FT)KMASK << (u * K));
+            h = h0 + (u32)(u * K + (K - 1));
+        }
+        const int leader = __ffs(bal) - 1;
+        u32 base = 0;
+        if (lane == leader) base = atomicAdd(&counters[kCandCountJ], (u32)__popc(bal));
+        base = __shfl_sync(0xFFFFFFFFu, base, leader);
+        if (has) {
+            const u32 idx = base + __popc(bal & lanemask_lt());
+            if (idx < cap) cand[idx] = ((u64)fired << 32) | h;
+        }
+    }
+}
+
+// The q-gram code of text bytes [st, st + q) read with byte loads.
+__device__ __forceinline__ u32 code_bytes(const u8* T, u32 st, const u8* smu) {
+    u32 c = 0;
+#pragma unroll
+    for (int t = 0; t < Q; t++) {
+        const u32 b = __ldg(T + st + t);
+        const u32 s = (MPM_MODE == 0) ? ((b >> SHIFT) & SYMMASK) : (u32)smu[b];
+        c = (c << ELL) | s;
+    }
+    return c;
+}
+
+struct __align__(64) TmapParam {
+    u64 v[16];
+};
+
+extern "C" __global__ void __launch_bounds__(MPM_WARPS * 32, 1)
+    mpm_scan_jit(const JitScanArgs A, const __grid_constant__ TmapParam tmap) {
+    extern __shared__ __align__(128) u8 smem[];
+    // shared layout: [mask table?][mu, 256][mbarriers][stages, 128-aligned]
+    constexpr u32 TAB = MPM_SMEM ? MPM_TABLE_BYTES : 0u;
+    constexpr u32 STAGE_OFF = (TAB + 256u + 8u * WARPS * S + 127u) / 128u * 128u;
+    u8* s_tab = smem;
+    u8* s_mu = smem + TAB;
+    u64* s_bar = reinterpret_cast<u64*>(s_mu + 256);
+    u8* s_stage = smem + STAGE_OFF;
+
+    if (TAB) {
+        for (u32 i = threadIdx.x; i < TAB / 16; i += blockDim.x)
+            reinterpret_cast<uint4*>(s_tab)[i] = reinterpret_cast<const uint4*>(A.table)[i];
+    }
+    for (u32 i = threadIdx.x; i < 256; i += blockDim.x) s_mu[i] = A.mu[i];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    u64* bars = s_bar + warp * S;
+    u8* stage = s_stage + (u64)warp * S * SLOT;
+    if (lane == 0) {
+        for (int i = 0; i < S; i++) mbar_init(smem_addr(&bars[i]), 1);
+        mbar_fence_init();
+    }
+    __syncthreads();
+    const ET* tab = MPM_SMEM ? reinterpret_cast<const ET*>(s_tab)
+                             : reinterpret_cast<const ET*>(A.table);
+    const u32 gw = blockIdx.x * WARPS + warp;
+    const u32 GW = gridDim.x * WARPS;
+
+    // ------------------------------------------------ rows through TMA
+    const u32 nst = A.Lst / C;
+    const u32 RW = A.row_warps;
+    const u32 my_rg = (gw < RW && A.RG > gw) ? (A.RG - gw + RW - 1) / RW : 0;
+    const u32 total = my_rg * nst;
+    if (total > 0) {
+        if (lane == 0) {
+            for (u32 i = 0; i < (u32)S && i < total; i++) {
+                const u32 bar = smem_addr(&bars[i]);
+                mbar_arrive_expect_tx(bar, SLOT);
+                tma_load_2d(smem_addr(stage + i * SLOT), &tmap, (int)((i % nst) * C),
+                            (int)((gw + (i / nst) * RW) * 32), bar);
+            }
+        }
+        __syncwarp();
+        u32 it = 0;
+        for (u32 r = 0; r < my_rg; r++) {
+            const u32 rg = gw + r * RW;
+            const u32 row = rg * 32 + lane;
+            const bool valid = row < A.R;
+            const u32 row_start = row * A.Lst;
+            DT D = ~(DT)0;
+            FT fm = 0;
+            if (WB > 0 && valid && row_start > 0) {
+                // the samples before the row: whole stages ending at row_start
+                const u8* wp = A.T + row_start - (u32)(WSTAGES * C);
+#pragma unroll 1
+                for (int ws = 0; ws < WSTAGES; ws++) {
+                    u32 w[C / 4];
+#pragma unroll
+                    for (int i = 0; i < C / 16; i++) {
+                        const uint4 v = ldg_v4(wp + ws * C + 16 * i);
+                        w[4 * i] = v.x;
+                        w[4 * i + 1] = v.y;
+                        w[4 * i + 2] = v.z;
+                        w[4 * i + 3] = v.w;
+                    }
+                    run_stage<false>(w, D, fm, tab, s_mu);
+                }
+            }
+            const u32 h_row = row_start / (u32)Q;
+            for (u32 st = 0; st < nst; st++, it++) {
+                const u32 slot = it % S;
+                const bool ok = mbar_wait_bounded(smem_addr(&bars[slot]), (it / S) & 1u);
+                if (!__all_sync(0xFFFFFFFFu, ok)) {
+                    if (lane == 0) {
+                        atomicExch(&A.counters[kErrorFlagJ], 5u /* MPM_ETIMEOUT */);
+                        const u32 issued = min(total, it + (u32)S);
+                        for (u32 j = it; j < issued; j++)
+                            mbar_wait_bounded(smem_addr(&bars[j % S]), (j / S) & 1u);
+                    }
+                    __syncwarp();
+                    return;
+                }
+                u32 w[C / 4];
+                const u32 base = smem_addr(stage + slot * SLOT + lane * C);
+#pragma unroll
+                for (int i = 0; i < C / 16; i++) {
+                    const uint4 v = lds128(base + 16 * i);
+                    w[4 * i] = v.x;
+                    w[4 * i + 1] = v.y;
+                    w[4 * i + 2] = v.z;
+                    w[4 * i + 3] = v.w;
+                }
+                fm = 0;
+                run_stage<true>(w, D, fm, tab, s_mu);
+                // the slot's words are consumed: refill it
+                __syncwarp();
+                if (lane == 0 && it + S < total) {
+                    const u32 j = it + S;
+                    const u32 bar = smem_addr(&bars[slot]);
+                    mbar_arrive_expect_tx(bar, SLOT);
+                    tma_load_2d(smem_addr(stage + slot * SLOT), &tmap, (int)((j % nst) * C),
+                                (int)((gw + (j / nst) * RW) * 32), bar);
+                }
+                if (!valid) fm = 0;
+                if (__any_sync(0xFFFFFFFFu, fm != 0))
+                    emit_stage(fm, h_row + st * (u32)(C / Q), A.cand, A.cap, A.counters);
+            }
+        }
+    }
+
+    // ------------------------------------- bytes after the rows, plain loads
+    const u32 GL = GW * 32;
+    const u32 rev = GL - 1 - (gw * 32 + lane);
+    for (u32 s = rev; s < A.nstreams; s += GL) {
+        const u32 a = A.pa + s * A.Ls;
+        const u32 b = min(A.n, a + A.Ls);
+        DT D = ~(DT)0;
+        // the m'-1 samples that end at a, a-P, ...; those starting before
+        // the text are virtual and leave D at all ones
+        for (int j = MP - 2; j >= 0; j--) {
+            const i64 e = (i64)a - (i64)j * P;
+            if (e - Q < 0) continue;
+            D = (D << K) | (DT)tab[code_bytes(A.T, (u32)(e - Q), s_mu)];
+        }
+        for (u32 e = a + P; e <= b; e += P) {
+            const u32 st = e - Q;
+            D = (D << K) | (DT)tab[code_bytes(A.T, st, s_mu)];
+            const u32 fired = (u32)(~D >> RSH) & KMASK;
+            const u32 act = __activemask();
+            const u32 bal = __ballot_sync(act, fired != 0);
+            if (bal) {
+                const int leader = __ffs(bal) - 1;
+                u32 base = 0;
+                if (lane == leader) base = atomicAdd(&A.counters[kCandCountJ], (u32)__popc(bal));
+                base = __shfl_sync(act, base, leader);
+                if (fired) {
+                    const u32 idx = base + __popc(bal & lanemask_lt());
+                    if (idx < A.cap) A.cand[idx] = ((u64)fired << 32) | (st / (u32)Q);
+                }
+            }
+        }
+    }
+}
+
+}  // namespace mpm

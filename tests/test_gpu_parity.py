@@ -134,27 +134,36 @@ SCAN_CASES = [
     ("english", 16, dict(q=2, sigma_r=32, k=3, map_kind=2)),
     ("english", 8, dict(q=3, sigma_r=16, k=1, map_kind=3, map_shift=0)),     # low bits, ell=4
     ("english", 64, dict(q=5, sigma_r=16, k=4, map_kind=2)),
+    ("english", 16, dict(q=3, sigma_r=4, k=1, map_kind=3, map_shift=7)),     # shift+ell > 8
+    ("english", 32, dict(q=2, sigma_r=16, k=2, map_kind=3, map_shift=6)),
+    ("protein", 32, dict(q=5, sigma_r=16, k=1, map_kind=2, table_place=2)),  # 1 MB table in L2
 ]
+KERNELS = [1, 2]  # generic, specialised
 
 
+@pytest.mark.parametrize("kernel", KERNELS)
 @pytest.mark.parametrize("kind,mlen,kw", SCAN_CASES)
-def test_scan_candidates_match_oracle(mpm, kind, mlen, kw):
+def test_scan_candidates_match_oracle(mpm, kind, mlen, kw, kernel):
     c = _case(kind, 300_007, 60, mlen, 30)
-    m = mpm.Matcher(c.P, sigma=c.sigma, **kw)
+    m = mpm.Matcher(c.P, sigma=c.sigma, kernel=kernel, **kw)
     p, info = m.params, m.info
     rec = m.scan(dev(c.T))
     torch.cuda.synchronize()
+    if not kw.get("smag"):
+        assert m.stats["specialised"] == (1 if kernel == 2 else 0)
     got = windows_of(rec, p, info)
     assert np.unique(got).size == got.size, "a window was reported twice"
     want = np.array(oracle_windows(c.T, c.P, p), dtype=np.int64)
     assert np.array_equal(got, want), (p, got.size, want.size)
 
 
-def test_scan_chunk_sizes_do_not_change_candidates(mpm):
+@pytest.mark.parametrize("kernel", KERNELS)
+def test_scan_chunk_sizes_do_not_change_candidates(mpm, kernel):
     c = W.protein_case(400_000, 100, 32, 50)
     base = None
     for chunk in (0, 96, 480, 4800, 48000):
-        m = mpm.Matcher(c.P, sigma=20, q=3, sigma_r=16, k=2, map_kind=2, chunk=chunk)
+        m = mpm.Matcher(c.P, sigma=20, q=3, sigma_r=16, k=2, map_kind=2, chunk=chunk,
+                        kernel=kernel)
         w = windows_of(m.scan(dev(c.T)), m.params, m.info)
         base = w if base is None else base
         assert np.array_equal(w, base), chunk
@@ -170,10 +179,11 @@ def test_search_config1_matches_oracle(mpm, native):
     assert st["z"] == z and st["n"] == c.n
 
 
+@pytest.mark.parametrize("kernel", KERNELS)
 @pytest.mark.parametrize("kind,mlen,kw", SCAN_CASES)
-def test_search_parameter_grid_matches_oracle(mpm, native, kind, mlen, kw):
+def test_search_parameter_grid_matches_oracle(mpm, native, kind, mlen, kw, kernel):
     c = _case(kind, 500_003, 80, mlen, 40)
-    check_search(mpm, native, c.T, c.P, c.sigma, **kw)
+    check_search(mpm, native, c.T, c.P, c.sigma, kernel=kernel, **kw)
 
 
 def test_search_host_text_and_host_outputs(mpm, native):
@@ -184,14 +194,27 @@ def test_search_host_text_and_host_outputs(mpm, native):
     assert np.array_equal(pos, wp) and np.array_equal(pid, wi)
 
 
+@pytest.mark.parametrize("kernel", KERNELS)
 @pytest.mark.parametrize("offset", [1, 2, 3, 5])
-def test_search_unaligned_text(mpm, native, offset):
+def test_search_unaligned_text(mpm, native, offset, kernel):
     c = W.dna_case(300_000, 100, 16, 50)
     buf = dev(c.T)
-    m = mpm.Matcher(c.P, sigma=4)
+    m = mpm.Matcher(c.P, sigma=4, kernel=kernel)
     pos, pid = m.search(buf[offset:])
     wp, wi = native.aho_corasick(c.T[offset:], c.P)
     assert np.array_equal(as_u32(pos), wp) and np.array_equal(as_u32(pid), wi)
+
+
+@pytest.mark.parametrize("kernel", KERNELS)
+def test_search_small_texts(mpm, native, kernel):
+    # texts from below one row group to a few rows, every length mod 16
+    c = W.protein_case(40_000, 200, 32, 100)
+    m = mpm.Matcher(c.P, sigma=20, kernel=kernel)
+    ac = native.AhoCorasick(c.P)
+    for n in (33, 100, 1000, 4097, 6000 + 7, 20_000 + 13, 40_000):
+        pos, pid = m.search(dev(c.T[:n]))
+        wp, wi = ac.search(c.T[:n])
+        assert np.array_equal(as_u32(pos), wp) and np.array_equal(as_u32(pid), wi), n
 
 
 def test_search_edge_cases(mpm, native):

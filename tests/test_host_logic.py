@@ -109,3 +109,31 @@ def test_host_tables_auto_params_equal_oracle(mpm):
         assert np.array_equal(mu, omu)
         got = _table_positions(table, info["entry_bytes"], npos)
         assert np.array_equal(got, otab.astype(np.uint64))
+
+
+JIT_GRID = [
+    # (alphabet, m, params): low-bit and byte-table maps, every entry width,
+    # shared-memory and global tables, odd and even periods k*q
+    ("dna", 16, dict(q=8, sigma_r=4, k=1, map_kind=3, map_shift=1)),
+    ("dna", 32, dict(q=5, sigma_r=4, k=3, map_kind=3, map_shift=1)),
+    ("dna", 64, dict(q=1, sigma_r=4, k=1, map_kind=3, map_shift=1)),
+    ("protein", 32, dict(q=3, sigma_r=32, k=1, map_kind=3, map_shift=0)),
+    ("protein", 32, dict(q=3, sigma_r=16, k=2, map_kind=2)),
+    ("protein", 32, dict(q=4, sigma_r=16, k=2, map_kind=1)),
+    ("protein", 32, dict(q=5, sigma_r=16, k=1, map_kind=2, table_place=2)),
+    ("english", 64, dict(q=7, sigma_r=8, k=2, map_kind=2)),
+    ("english", 16, dict(q=3, sigma_r=4, k=1, map_kind=3, map_shift=7)),
+]
+
+
+@pytest.mark.parametrize("alpha,mlen,kw", JIT_GRID)
+def test_specialised_scan_compiles(mpm, alpha, mlen, kw):
+    """The run-time specialised scan kernel compiles (NVRTC, sm_103a) for a
+    spread of filters, on a machine without a GPU."""
+    from paper_1405_5483_gb300 import workloads as W
+    make = {"dna": W.dna_case, "protein": W.protein_case, "english": W.english_case}[alpha]
+    c = make(1 << 12, 50, mlen, 10)
+    rc, log = mpm.jit_compile(c.P, c.sigma, **kw)
+    if rc == mpm.MPM_ENOTSUP and "NVRTC not found" in log:
+        pytest.skip("NVRTC is not installed here")
+    assert rc == mpm.MPM_OK, log
