@@ -201,8 +201,10 @@ int mpm_host_tables(const uint8_t *P, size_t r, size_t m, int sigma,
                     size_t table_bytes);
 
 /*
- * Host-only check that the specialised scan kernel for these parameters
- * compiles (NVRTC, sm_103a), without loading it on a device.  Returns
+ * Host-only check that the specialised scan kernels for these parameters
+ * (the variant mpm_search runs, which verifies its candidates itself, and
+ * the candidate variant of mpm_scan) compile (NVRTC, sm_103a), without
+ * loading them on a device.  Returns
  * MPM_OK, MPM_ENOTSUP (parameters outside the specialised kernel, or NVRTC
  * missing) or MPM_ECUDA (compile error; the compiler log is copied to log,
  * log_bytes bytes at most, when log is not NULL).

@@ -46,7 +46,9 @@ struct mpm_handle {
     size_t out_cap = 0;
 
     mpm_stats stats{};
-    const mpm::JitKernel* jit = nullptr;  // specialised scan, when compiled
+    const mpm::JitKernel* jit = nullptr;       // specialised scan that verifies
+    const mpm::JitKernel* jit_cand = nullptr;  // specialised scan, candidates only
+    bool jit_cand_tried = false;
     int timing = 0;
     cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};
 };
@@ -131,24 +133,65 @@ void release(mpm_handle* h) {
     delete h;
 }
 
-// The scan kernel the handle uses: the specialised one when it compiled.
-int scan_launch(const mpm_handle* h, const mpm::ScanArgs& a, cudaStream_t s) {
-    if (h->jit) return mpm::launch_scan_jit(a, h->jit, h->num_sms, h->plan.p.chunk, s);
-    return mpm::launch_scan(a, h->num_sms, h->plan.p.chunk, s);
-}
-
 int bits_for(uint64_t v) {
     int b = 0;
     while (b < 64 && (v >> b)) b++;
     return b;
 }
 
-// Scan + verify on device text; leaves counters in h->h_counters.
-int run_filter(mpm_handle* h, const uint8_t* dT, uint32_t n, int* launches) {
+mpm::ScanArgs scan_args(const mpm_handle* h, const uint8_t* dT, uint32_t n, uint64_t* cand,
+                        uint32_t cap, uint32_t* counters) {
+    mpm::ScanArgs a{};
+    a.T = dT;
+    a.n = n;
+    a.f = filter_dev(h);
+    a.P = (uint32_t)(a.f.k * a.f.q);
+    const uint32_t wb = (uint32_t)(a.f.mprime - 1) * a.P;
+    a.warm_bytes = (wb + 3) & ~3u;
+    a.cand = cand;
+    a.cap = cap;
+    a.counters = counters;
+    return a;
+}
+
+mpm::VerifyArgs verify_args(const mpm_handle* h, const uint8_t* dT, uint32_t n,
+                            const uint64_t* cand, uint32_t cand_cap, uint64_t* occ,
+                            uint32_t occ_cap, uint32_t* counters) {
+    mpm::VerifyArgs v{};
+    v.T = dT;
+    v.n = n;
+    v.m = (uint32_t)h->plan.m;
+    v.q = h->plan.p.q;
+    v.k = h->plan.p.k;
+    v.mprime = h->plan.info.mprime;
+    v.cand = cand;
+    v.cand_cap = cand_cap;
+    v.slots = h->d_slots;
+    v.slot_mask = (uint32_t)h->host.slots.size() - 1;
+    v.pat = h->d_pat;
+    v.pid = h->d_pid;
+    v.key_bytes = h->host.key_bytes;
+    v.occ = occ;
+    v.occ_cap = occ_cap;
+    v.counters = counters;
+    return v;
+}
+
+// True when mpm_search runs the specialised scan that verifies by itself.
+bool fused_search(const mpm_handle* h) { return h->jit && !h->plan.p.smag; }
+
+// Enqueues, without synchronising: the counter reset, the scan and the
+// verification of text dT (device).  Occurrence keys go to occ, candidate
+// records (generic and SMAG paths only) to cand.
+int enqueue_filter(mpm_handle* h, const uint8_t* dT, uint32_t n, uint64_t* cand,
+                   uint32_t cand_cap, uint64_t* occ, uint32_t occ_cap, uint32_t* counters,
+                   int* launches) {
     cudaStream_t s = h->stream;
     const mpm::FilterDev f = filter_dev(h);
-    if (cudaMemsetAsync(h->d_counters, 0, mpm::kNumCounters * sizeof(uint32_t), s) != cudaSuccess)
+    if (cudaMemsetAsync(counters, 0, mpm::kNumCounters * sizeof(uint32_t), s) != cudaSuccess)
         return MPM_ECUDA;
+    const mpm::VerifyArgs v = verify_args(h, dT, n, cand, cand_cap, occ, occ_cap, counters);
+    if (h->timing) cudaEventRecord(h->ev[0], s);
     int l;
     if (h->plan.p.smag) {
         const size_t nq = n / (uint32_t)f.q;
@@ -156,54 +199,39 @@ int run_filter(mpm_handle* h, const uint8_t* dT, uint32_t n, int* launches) {
         l = mpm::launch_encode(dT, n, f, h->d_codes, s);
         if (l < 0) return MPM_ECUDA;
         *launches += l;
-        l = mpm::launch_scan_codes(h->d_codes, (uint32_t)nq, f, h->d_cand, (uint32_t)h->cand_cap,
-                                   h->d_counters, s);
+        l = mpm::launch_scan_codes(h->d_codes, (uint32_t)nq, f, cand, cand_cap, counters, s);
+    } else if (fused_search(h)) {
+        l = mpm::launch_scan_jit(scan_args(h, dT, n, cand, cand_cap, counters), &v, h->jit,
+                                 h->num_sms, h->plan.p.chunk, s);
+        if (l < 0) return MPM_ECUDA;
+        *launches += l;
+        if (h->timing) {
+            cudaEventRecord(h->ev[1], s);
+            cudaEventRecord(h->ev[2], s);
+        }
+        return MPM_OK;
     } else {
-        mpm::ScanArgs a{};
-        a.T = dT;
-        a.n = n;
-        a.f = f;
-        a.P = (uint32_t)(f.k * f.q);
-        const uint32_t wb = (uint32_t)(f.mprime - 1) * a.P;
-        a.warm_bytes = (wb + 3) & ~3u;
-        a.cand = h->d_cand;
-        a.cap = (uint32_t)h->cand_cap;
-        a.counters = h->d_counters;
-        if (h->timing) cudaEventRecord(h->ev[0], s);
-        l = scan_launch(h, a, s);
-        if (h->timing) cudaEventRecord(h->ev[1], s);
-        if (l == -2) return MPM_ENOTSUP;
+        l = mpm::launch_scan(scan_args(h, dT, n, cand, cand_cap, counters), h->num_sms,
+                             h->plan.p.chunk, s);
     }
     if (l < 0) return MPM_ECUDA;
     *launches += l;
-    mpm::VerifyArgs v{};
-    v.T = dT;
-    v.n = n;
-    v.m = (uint32_t)h->plan.m;
-    v.q = f.q;
-    v.k = f.k;
-    v.mprime = f.mprime;
-    v.cand = h->d_cand;
-    v.cand_cap = (uint32_t)h->cand_cap;
-    v.slots = h->d_slots;
-    v.slot_mask = (uint32_t)h->host.slots.size() - 1;
-    v.pat = h->d_pat;
-    v.pid = h->d_pid;
-    v.key_bytes = h->host.key_bytes;
-    v.occ = h->d_occ;
-    v.occ_cap = (uint32_t)h->occ_cap;
-    v.counters = h->d_counters;
-    if (n >= h->plan.m) {
-        if (mpm::launch_verify(v, h->num_sms, s) < 0) return MPM_ECUDA;
-        *launches += 1;
-    }
+    if (h->timing) cudaEventRecord(h->ev[1], s);
+    if (mpm::launch_verify(v, h->num_sms, s) < 0) return MPM_ECUDA;
+    *launches += 1;
     if (h->timing) cudaEventRecord(h->ev[2], s);
-    if (cudaMemcpyAsync(h->h_counters, h->d_counters, mpm::kNumCounters * sizeof(uint32_t),
+    return MPM_OK;
+}
+
+// The one synchronisation of a search: the counters come back to the host.
+int read_counters(mpm_handle* h, const uint32_t* counters) {
+    cudaStream_t s = h->stream;
+    if (cudaMemcpyAsync(h->h_counters, counters, mpm::kNumCounters * sizeof(uint32_t),
                         cudaMemcpyDeviceToHost, s) != cudaSuccess)
         return MPM_ECUDA;
     if (cudaStreamSynchronize(s) != cudaSuccess) return MPM_ECUDA;
     if (h->h_counters[mpm::kErrorFlag]) return (int)h->h_counters[mpm::kErrorFlag];
-    if (h->timing && !h->plan.p.smag) {
+    if (h->timing) {
         float a = 0.f, b = 0.f;
         cudaEventElapsedTime(&a, h->ev[0], h->ev[1]);
         cudaEventElapsedTime(&b, h->ev[1], h->ev[2]);
@@ -304,7 +332,7 @@ mpm_handle* mpm_build(const uint8_t* P, size_t r, size_t m, int sigma, const mpm
     if (!h->plan.p.smag && h->plan.p.kernel != MPM_KERNEL_GENERIC) {
         int err = MPM_OK;
         std::string log;
-        h->jit = mpm::jit_scan_kernel(filter_dev(h), h->device, &err, &log);
+        h->jit = mpm::jit_scan_kernel(filter_dev(h), true, h->device, &err, &log);
         if (!h->jit && h->plan.p.kernel == MPM_KERNEL_SPECIALISED) {
             if (!log.empty()) std::fprintf(stderr, "mpm: specialised scan failed:\n%s\n", log.c_str());
             release(h);
@@ -359,7 +387,7 @@ int mpm_search(mpm_handle* h, const uint8_t* T, size_t n, uint32_t* out_pos, uin
     const size_t out_capacity = *z;
     h->stats = mpm_stats{};
     h->stats.n = n;
-    h->stats.specialised = h->jit && !h->plan.p.smag ? 1u : 0u;
+    h->stats.specialised = fused_search(h) ? 1u : 0u;
     const uint32_t q = (uint32_t)h->plan.p.q, k = (uint32_t)h->plan.p.k;
     h->stats.sampled = (n / q) / k;
     int launches = 0;
@@ -367,29 +395,52 @@ int mpm_search(mpm_handle* h, const uint8_t* T, size_t n, uint32_t* out_pos, uin
         *z = 0;
         return set_error(MPM_OK);
     }
+    cudaStream_t s = h->stream;
     // the text on the device
     const uint8_t* dT = T;
     if (!is_device_ptr(T)) {
         if (grow(&h->d_text, &h->text_cap, n)) return set_error(MPM_ENOMEM);
-        if (cudaMemcpyAsync(h->d_text, T, n, cudaMemcpyHostToDevice, h->stream) != cudaSuccess)
+        if (cudaMemcpyAsync(h->d_text, T, n, cudaMemcpyHostToDevice, s) != cudaSuccess)
             return set_error(MPM_ECUDA);
         dT = h->d_text;
     }
-    // first-call capacities: a candidate rate of 1/64 per byte, 64K occurrences
-    if (grow(&h->d_cand, &h->cand_cap, std::max<size_t>(1 << 16, n / 64 + 1024)))
+    // first-call capacities: a candidate rate of 1/64 per byte (unused by the
+    // specialised scan, which verifies its candidates itself), 64K occurrences
+    if (!fused_search(h) &&
+        grow(&h->d_cand, &h->cand_cap, std::max<size_t>(1 << 16, n / 64 + 1024)))
         return set_error(MPM_ENOMEM);
     if (!h->d_occ || h->occ_cap < (1u << 16)) {
         size_t c = 0;
         if (grow(&h->d_occ, &h->occ_cap, 1 << 16) || grow(&h->d_occ_tmp, &c, 1 << 16))
             return set_error(MPM_ENOMEM);
     }
+    // where the rank sort writes: the caller's device outputs, or staging
+    const bool dev_out =
+        out_capacity == 0 || (is_device_ptr(out_pos) && is_device_ptr(out_pid));
+    const uint32_t rank_cap = (uint32_t)std::min<size_t>(out_capacity, mpm::kRankSortMax);
+    uint32_t* op = out_pos;
+    uint32_t* oi = out_pid;
+    if (!dev_out) {
+        if (grow(&h->d_out, &h->out_cap, 2 * (size_t)rank_cap)) return set_error(MPM_ENOMEM);
+        op = h->d_out;
+        oi = h->d_out + rank_cap;
+    }
     for (int attempt = 0;; attempt++) {
-        rc = run_filter(h, dT, (uint32_t)n, &launches);
+        rc = enqueue_filter(h, dT, (uint32_t)n, h->d_cand, (uint32_t)h->cand_cap, h->d_occ,
+                            (uint32_t)h->occ_cap, h->d_counters, &launches);
+        if (rc) return set_error(rc);
+        if (rank_cap > 0) {
+            if (mpm::launch_rank_sort(h->d_occ, h->d_counters + mpm::kOccCount, rank_cap, op, oi,
+                                      s) < 0)
+                return set_error(MPM_ECUDA);
+            launches++;
+        }
+        rc = read_counters(h, h->d_counters);
         if (rc) return set_error(rc);
         const uint32_t nc = h->h_counters[mpm::kCandCount];
         const uint32_t nz = h->h_counters[mpm::kOccCount];
         bool again = false;
-        if (nc > h->cand_cap) {
+        if (!fused_search(h) && nc > h->cand_cap) {
             if (grow(&h->d_cand, &h->cand_cap, (size_t)nc + nc / 4 + 1024))
                 return set_error(MPM_ENOMEM);
             again = true;
@@ -414,30 +465,26 @@ int mpm_search(mpm_handle* h, const uint8_t* T, size_t n, uint32_t* out_pos, uin
         h->stats.launches = launches;
         return set_error(MPM_ECAPACITY);
     }
-    if (zz > 0) {
-        if (grow(&h->d_hist, &h->hist_cap, mpm::sort_hist_entries(zz))) return set_error(MPM_ENOMEM);
-        const bool dev_out = is_device_ptr(out_pos) && is_device_ptr(out_pid);
-        uint32_t* op = out_pos;
-        uint32_t* oi = out_pid;
+    if (zz > mpm::kRankSortMax) {
+        // too many for the rank sort: sort now that the count is known
         if (!dev_out) {
             if (grow(&h->d_out, &h->out_cap, 2 * (size_t)zz)) return set_error(MPM_ENOMEM);
             op = h->d_out;
             oi = h->d_out + zz;
         }
+        if (grow(&h->d_hist, &h->hist_cap, mpm::sort_hist_entries(zz))) return set_error(MPM_ENOMEM);
         const uint32_t key_bits =
             ((uint32_t)bits_for(n) << 16) | (uint32_t)bits_for(h->plan.r > 1 ? h->plan.r - 1 : 1);
         int l = mpm::launch_sort_output(h->d_occ, h->d_occ_tmp, h->d_hist, h->hist_cap, zz,
-                                        key_bits, op, oi, h->stream);
+                                        key_bits, op, oi, s);
         if (l < 0) return set_error(MPM_ECUDA);
         launches += l;
-        if (!dev_out) {
-            if (cudaMemcpyAsync(out_pos, op, (size_t)zz * 4, cudaMemcpyDeviceToHost, h->stream) !=
-                    cudaSuccess ||
-                cudaMemcpyAsync(out_pid, oi, (size_t)zz * 4, cudaMemcpyDeviceToHost, h->stream) !=
-                    cudaSuccess ||
-                cudaStreamSynchronize(h->stream) != cudaSuccess)
-                return set_error(MPM_ECUDA);
-        }
+    }
+    if (!dev_out && zz > 0) {
+        if (cudaMemcpyAsync(out_pos, op, (size_t)zz * 4, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+            cudaMemcpyAsync(out_pid, oi, (size_t)zz * 4, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+            cudaStreamSynchronize(s) != cudaSuccess)
+            return set_error(MPM_ECUDA);
     }
     h->stats.launches = launches;
     return set_error(MPM_OK);
@@ -459,8 +506,10 @@ int mpm_jit_compile(const uint8_t* P, size_t r, size_t m, int sigma, const mpm_p
     f.shift = plan.p.map_shift;
     f.mprime = plan.info.mprime;
     f.positions = plan.info.positions;
+    // both variants: the one mpm_search runs and the candidate one of mpm_scan
     std::string text;
-    rc = mpm::jit_compile_only(f, &text);
+    rc = mpm::jit_compile_only(f, true, &text);
+    if (rc == MPM_OK) rc = mpm::jit_compile_only(f, false, &text);
     if (log && log_bytes) {
         const size_t c = std::min(log_bytes - 1, text.size());
         std::memcpy(log, text.data(), c);
@@ -487,6 +536,14 @@ int mpm_scan(mpm_handle* h, const uint8_t* T, size_t n, uint64_t* cand, size_t* 
     if (rc) return set_error(rc);
     cudaStream_t s = h->stream;
     const mpm::FilterDev f = filter_dev(h);
+    if (!h->plan.p.smag && !h->jit_cand_tried && h->plan.p.kernel != MPM_KERNEL_GENERIC) {
+        h->jit_cand_tried = true;
+        int err = MPM_OK;
+        std::string log;
+        h->jit_cand = mpm::jit_scan_kernel(f, false, h->device, &err, &log);
+        if (!h->jit_cand && h->plan.p.kernel == MPM_KERNEL_SPECIALISED)
+            return set_error(err ? err : MPM_ENOTSUP);
+    }
     if (cudaMemsetAsync(h->d_counters, 0, mpm::kNumCounters * 4, s) != cudaSuccess)
         return set_error(MPM_ECUDA);
     int l = 0;
@@ -497,18 +554,10 @@ int mpm_scan(mpm_handle* h, const uint8_t* T, size_t n, uint64_t* cand, size_t* 
         l = mpm::launch_scan_codes(h->d_codes, (uint32_t)nq, f, cand, (uint32_t)*count,
                                    h->d_counters, s);
     } else {
-        mpm::ScanArgs a{};
-        a.T = T;
-        a.n = (uint32_t)n;
-        a.f = f;
-        a.P = (uint32_t)(f.k * f.q);
-        const uint32_t wb = (uint32_t)(f.mprime - 1) * a.P;
-        a.warm_bytes = (wb + 3) & ~3u;
-        a.cand = cand;
-        a.cap = (uint32_t)*count;
-        a.counters = h->d_counters;
-        l = scan_launch(h, a, s);
-        if (l == -2) return set_error(MPM_ENOTSUP);
+        const mpm::ScanArgs a = scan_args(h, T, (uint32_t)n, cand, (uint32_t)*count, h->d_counters);
+        l = h->jit_cand ? mpm::launch_scan_jit(a, nullptr, h->jit_cand, h->num_sms,
+                                               h->plan.p.chunk, s)
+                        : mpm::launch_scan(a, h->num_sms, h->plan.p.chunk, s);
     }
     if (l < 0) return set_error(MPM_ECUDA);
     if (cudaMemcpyAsync(h->h_counters, h->d_counters, mpm::kNumCounters * 4,
@@ -521,7 +570,7 @@ int mpm_scan(mpm_handle* h, const uint8_t* T, size_t n, uint64_t* cand, size_t* 
     h->stats = mpm_stats{};
     h->stats.n = n;
     h->stats.candidates = *count;
-    h->stats.specialised = h->jit && !h->plan.p.smag ? 1u : 0u;
+    h->stats.specialised = h->jit_cand && !h->plan.p.smag ? 1u : 0u;
     return set_error(*count > cap ? MPM_ECAPACITY : MPM_OK);
 }
 
@@ -590,57 +639,32 @@ extern "C" int mpm_search_noalloc(mpm_handle* h, const uint8_t* T, size_t n, uin
     h->stats = mpm_stats{};
     h->stats.n = n;
     h->stats.sampled = (n / (uint32_t)h->plan.p.q) / (uint32_t)h->plan.p.k;
-    h->stats.specialised = h->jit ? 1u : 0u;
+    h->stats.specialised = fused_search(h) ? 1u : 0u;
     if (n < h->plan.m) {
         *z = 0;
         return set_error(MPM_OK);
     }
     cudaStream_t s = h->stream;
-    const mpm::FilterDev f = filter_dev(h);
+    int launches = 0;
+    // the counters block is wider than the counters the kernels use; clear it
     if (cudaMemsetAsync(counters, 0, kNaCounterBytes, s) != cudaSuccess)
         return set_error(MPM_ECUDA);
-    mpm::ScanArgs a{};
-    a.T = T;
-    a.n = (uint32_t)n;
-    a.f = f;
-    a.P = (uint32_t)(f.k * f.q);
-    const uint32_t wb = (uint32_t)(f.mprime - 1) * a.P;
-    a.warm_bytes = (wb + 3) & ~3u;
-    a.cand = cand;
-    a.cap = (uint32_t)kNaMaxCand;
-    a.counters = counters;
-    int launches = scan_launch(h, a, s);
-    if (launches == -2) return set_error(MPM_ENOTSUP);
-    if (launches < 0) return set_error(MPM_ECUDA);
-    mpm::VerifyArgs v{};
-    v.T = T;
-    v.n = (uint32_t)n;
-    v.m = (uint32_t)h->plan.m;
-    v.q = f.q;
-    v.k = f.k;
-    v.mprime = f.mprime;
-    v.cand = cand;
-    v.cand_cap = (uint32_t)kNaMaxCand;
-    v.slots = h->d_slots;
-    v.slot_mask = (uint32_t)h->host.slots.size() - 1;
-    v.pat = h->d_pat;
-    v.pid = h->d_pid;
-    v.key_bytes = h->host.key_bytes;
-    v.occ = occ;
-    v.occ_cap = (uint32_t)kNaMaxOcc;
-    v.counters = counters;
-    if (mpm::launch_verify(v, h->num_sms, s) < 0) return set_error(MPM_ECUDA);
-    launches++;
-    if (cudaMemcpyAsync(h->h_counters, counters, mpm::kNumCounters * sizeof(uint32_t),
-                        cudaMemcpyDeviceToHost, s) != cudaSuccess ||
-        cudaStreamSynchronize(s) != cudaSuccess)
-        return set_error(MPM_ECUDA);
-    if (h->h_counters[mpm::kErrorFlag]) return set_error((int)h->h_counters[mpm::kErrorFlag]);
+    rc = enqueue_filter(h, T, (uint32_t)n, cand, (uint32_t)kNaMaxCand, occ, (uint32_t)kNaMaxOcc,
+                        counters, &launches);
+    if (rc) return set_error(rc);
+    const uint32_t rank_cap = (uint32_t)std::min<size_t>(out_capacity, mpm::kRankSortMax);
+    if (rank_cap > 0) {
+        if (mpm::launch_rank_sort(occ, counters + mpm::kOccCount, rank_cap, out_pos, out_pid, s) < 0)
+            return set_error(MPM_ECUDA);
+        launches++;
+    }
+    rc = read_counters(h, counters);
+    if (rc) return set_error(rc);
     const uint32_t nc = h->h_counters[mpm::kCandCount];
     const uint32_t zz = h->h_counters[mpm::kOccCount];
     h->stats.candidates = nc;
     h->stats.launches = (uint32_t)launches;
-    if (nc > kNaMaxCand) {
+    if (!fused_search(h) && nc > kNaMaxCand) {
         *z = 0;
         return set_error(MPM_ESCRATCH);
     }
@@ -648,7 +672,7 @@ extern "C" int mpm_search_noalloc(mpm_handle* h, const uint8_t* T, size_t n, uin
     h->stats.z = zz;
     if (zz > kNaMaxOcc) return set_error(MPM_ESCRATCH);
     if (zz > out_capacity) return set_error(MPM_ECAPACITY);
-    if (zz > 0) {
+    if (zz > mpm::kRankSortMax) {
         const uint32_t key_bits =
             ((uint32_t)bits_for(n) << 16) | (uint32_t)bits_for(h->plan.r > 1 ? h->plan.r - 1 : 1);
         // at most kNaMaxOcc keys: the one-block sort, no temporary buffers

@@ -125,16 +125,17 @@ constexpr size_t kSmemLimit = 227 * 1024;
 
 // Compile-time constants of one specialisation and its launch geometry.
 struct JitSpec {
-    int q, k, mp, ell, shift, mode, eb, smem, table_bytes, C, S, warps;
+    int q, k, mp, ell, shift, mode, eb, smem, table_bytes, C, S, warps, verify, ecap;
     size_t smem_bytes;
 
     std::string defines() const {
-        char buf[512];
+        char buf[640];
         std::snprintf(buf, sizeof(buf),
                       "-DMPM_Q=%d -DMPM_K=%d -DMPM_MP=%d -DMPM_ELL=%d -DMPM_SHIFT=%d "
                       "-DMPM_MODE=%d -DMPM_EB=%d -DMPM_SMEM=%d -DMPM_TABLE_BYTES=%du "
-                      "-DMPM_C=%d -DMPM_S=%d -DMPM_WARPS=%d",
-                      q, k, mp, ell, shift, mode, eb, smem, table_bytes, C, S, warps);
+                      "-DMPM_C=%d -DMPM_S=%d -DMPM_WARPS=%d -DMPM_VERIFY=%d -DMPM_EMIT_CAP=%d",
+                      q, k, mp, ell, shift, mode, eb, smem, table_bytes, C, S, warps, verify,
+                      ecap);
         return buf;
     }
 };
@@ -147,8 +148,10 @@ struct JitKernel {
 
 // The specialisation for a filter, or false when the filter is outside what
 // the specialised kernel handles (then the generic kernel runs).
-bool jit_spec(const FilterDev& f, JitSpec* out) {
+bool jit_spec(const FilterDev& f, bool verify, JitSpec* out) {
     JitSpec s{};
+    s.verify = verify ? 1 : 0;
+    s.ecap = 96;
     s.q = f.q;
     s.k = f.k;
     s.mp = f.mprime;
@@ -167,8 +170,9 @@ bool jit_spec(const FilterDev& f, JitSpec* out) {
     if ((C / P) * (uint32_t)f.k > 64) return false;
     s.C = (int)C;
     s.warps = C <= 48 ? 32 : 16;
-    const size_t fixed = (size_t)s.table_bytes + 256 + 8 * 32 * 4 + 128;
     for (;;) {
+        const size_t fixed =
+            (size_t)s.table_bytes + 256 + 8 * s.warps * 4 + 8 * s.warps * s.ecap + 128;
         const size_t per_stage = (size_t)s.warps * 32 * C;
         const size_t budget = kSmemLimit > fixed ? kSmemLimit - fixed : 0;
         s.S = (int)std::min<size_t>(4, budget / per_stage);
@@ -176,7 +180,8 @@ bool jit_spec(const FilterDev& f, JitSpec* out) {
         if (s.warps <= 4) return false;
         s.warps /= 2;
     }
-    const size_t stage_off = ((size_t)s.table_bytes + 256 + 8 * s.warps * s.S + 127) / 128 * 128;
+    const size_t emit_off = (size_t)s.table_bytes + 256 + 8 * s.warps * s.S;
+    const size_t stage_off = (emit_off + 8 * s.warps * s.ecap + 127) / 128 * 128;
     s.smem_bytes = stage_off + (size_t)s.warps * s.S * 32 * C;
     *out = s;
     return true;
@@ -225,9 +230,9 @@ static int compile_spec(const JitSpec& s, std::string* cubin, std::string* log) 
     return ret;
 }
 
-int jit_compile_only(const FilterDev& f, std::string* log) {
+int jit_compile_only(const FilterDev& f, bool verify, std::string* log) {
     JitSpec s;
-    if (!jit_spec(f, &s)) {
+    if (!jit_spec(f, verify, &s)) {
         if (log) *log = "filter outside the specialised kernel";
         return MPM_ENOTSUP;
     }
@@ -235,12 +240,13 @@ int jit_compile_only(const FilterDev& f, std::string* log) {
     return compile_spec(s, &cubin, log);
 }
 
-const JitKernel* jit_scan_kernel(const FilterDev& f, int device, int* err, std::string* log) {
+const JitKernel* jit_scan_kernel(const FilterDev& f, bool verify, int device, int* err,
+                                std::string* log) {
     static std::mutex mu;
     static std::map<std::string, std::unique_ptr<JitKernel>> cache;
     *err = MPM_OK;
     JitSpec s;
-    if (!jit_spec(f, &s)) {
+    if (!jit_spec(f, verify, &s)) {
         *err = MPM_ENOTSUP;
         return nullptr;
     }
@@ -280,8 +286,10 @@ const JitKernel* jit_scan_kernel(const FilterDev& f, int device, int* err, std::
     return out;
 }
 
-int launch_scan_jit(const ScanArgs& A, const JitKernel* K, int num_sms, int chunk,
-                    cudaStream_t stream) {
+bool jit_verifies(const JitKernel* k) { return k && k->spec.verify; }
+
+int launch_scan_jit(const ScanArgs& A, const VerifyArgs* V, const JitKernel* K, int num_sms,
+                    int chunk, cudaStream_t stream) {
     if (A.n == 0) return 0;
     const DriverApi& drv = driver();
     const JitSpec& s = K->spec;
@@ -317,6 +325,17 @@ int launch_scan_jit(const ScanArgs& A, const JitKernel* K, int num_sms, int chun
     Ls = std::max<uint32_t>((Ls + P - 1) / P * P, 4 * P);
     J.Ls = Ls;
     J.nstreams = rest ? (rest + Ls - 1) / Ls : 0;
+    if (s.verify) {
+        if (!V) return -1;
+        J.m = V->m;
+        J.slots = V->slots;
+        J.pat = V->pat;
+        J.pid = V->pid;
+        J.occ = reinterpret_cast<unsigned long long*>(V->occ);
+        J.slot_mask = V->slot_mask;
+        J.key_bytes = (uint32_t)V->key_bytes;
+        J.occ_cap = V->occ_cap;
+    }
 
     alignas(64) CUtensorMap tmap;
     std::memset(&tmap, 0, sizeof(tmap));

@@ -82,10 +82,24 @@ struct JitKernel;
 // Compiles (NVRTC) and loads the specialised scan for this filter on the
 // current device, cached per process; nullptr with *err = MPM_ENOTSUP when
 // the filter is outside the specialised kernel or NVRTC is missing.
-const JitKernel* jit_scan_kernel(const FilterDev& f, int device, int* err, std::string* log);
+// verify: the variant that verifies candidates itself and appends
+// occurrences (mpm_search); otherwise it appends candidate records.
+const JitKernel* jit_scan_kernel(const FilterDev& f, bool verify, int device, int* err,
+                                std::string* log);
 // Host-only: compiles the specialisation without loading it.
-int jit_compile_only(const FilterDev& f, std::string* log);
-int launch_scan_jit(const ScanArgs& a, const JitKernel* k, int num_sms, int chunk, cudaStream_t s);
+int jit_compile_only(const FilterDev& f, bool verify, std::string* log);
+bool jit_verifies(const JitKernel* k);
+// v: where the verifying variant finds the patterns and puts occurrences.
+int launch_scan_jit(const ScanArgs& a, const VerifyArgs* v, const JitKernel* k, int num_sms,
+                    int chunk, cudaStream_t s);
+
+// Sorts the device-counted occurrence keys (*count, in keys) into
+// out_pos/out_pid without the host knowing the count: one grid-wide rank
+// sort, valid while the count is at most kRankSortMax and at most out_cap;
+// otherwise it writes nothing and leaves the outputs to launch_sort_output.
+constexpr uint32_t kRankSortMax = 4096;
+int launch_rank_sort(const uint64_t* keys, const uint32_t* count, uint32_t out_cap,
+                     uint32_t* out_pos, uint32_t* out_pid, cudaStream_t s);
 
 // Sorts z keys (in d_keys, device count unknown to the kernels: z is passed)
 // and writes out_pos/out_pid.  tmp must hold z keys; returns launches or -1.

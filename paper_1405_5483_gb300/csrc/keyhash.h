@@ -1,0 +1,29 @@
+// Verification key of a window or pattern: its first min(m, 16) bytes, zero
+// padded, as two little-endian 64-bit words, hashed to a slot of the
+// open-addressing table of pattern groups.  Shared by the host builder and
+// every kernel that verifies (including the one compiled at run time), so it
+// has no includes.
+#pragma once
+
+namespace mpm {
+
+#if defined(__CUDACC__) || defined(__CUDACC_RTC__)
+__host__ __device__
+#endif
+inline unsigned long long key_hash(unsigned long long lo, unsigned long long hi) {
+    unsigned long long h = lo * 0x9E3779B97F4A7C15ull;
+    h ^= hi * 0xC2B2AE3D27D4EB4Full;
+    h ^= (lo ^ hi) >> 29;
+    h *= 0x165667B19E3779F9ull;
+    h ^= h >> 32;
+    return h;
+}
+
+// One slot: the patterns whose key is (lo, hi) occupy rows
+// [first, first + count) of the sorted pattern array; count == 0 is empty.
+struct Slot {
+    unsigned long long lo, hi;
+    unsigned int first, count;
+};
+
+}  // namespace mpm

@@ -5,6 +5,7 @@
 #include <cstdint>
 #include <vector>
 
+#include "keyhash.h"
 #include "mpm.h"
 
 #if defined(__CUDACC__)
@@ -22,24 +23,6 @@ int set_error(int code);
 constexpr int kMaxK = 32;
 constexpr int kMaxPositions = 64;
 
-// Verification key of a window or pattern: its first min(m, 16) bytes,
-// zero padded, as two little-endian 64-bit words, hashed to a slot.
-MPM_HD uint64_t key_hash(uint64_t lo, uint64_t hi) {
-    uint64_t h = lo * 0x9E3779B97F4A7C15ull;
-    h ^= hi * 0xC2B2AE3D27D4EB4Full;
-    h ^= (lo ^ hi) >> 29;
-    h *= 0x165667B19E3779F9ull;
-    h ^= h >> 32;
-    return h;
-}
-
-// One slot of the open-addressing table of pattern groups: all patterns
-// whose key is (lo, hi) occupy rows [first, first + count) of the sorted
-// pattern array.  count == 0 marks an empty slot.
-struct Slot {
-    uint64_t lo, hi;
-    uint32_t first, count;
-};
 static_assert(sizeof(Slot) == 24, "slot layout");
 
 // Parameters after automatic choices, plus what follows from them.

@@ -13,6 +13,9 @@
 //   MPM_TABLE_BYTES   mask-table bytes (padded to 16)
 //   MPM_C             bytes of a row per stage: a multiple of 16 and of k*q
 //   MPM_S, MPM_WARPS  stages per warp, warps per block
+//   MPM_VERIFY        1: verify the candidates in the kernel and append
+//                     occurrences; 0: append the candidate records
+//   MPM_EMIT_CAP      records a warp buffers in shared memory
 //
 // Layout and flow.  Rows of Lst bytes (a multiple of C, starting on a
 // multiple of k*q) are owned by threads; a warp streams its 32 rows through
@@ -23,9 +26,13 @@
 // is therefore straight-line code with constant offsets: cut the q-gram
 // code, one table lookup, D <- (D << k) | B[code], and the k report bits of
 // D go into a per-stage bit mask.  Only after the stage, if some lane of the
-// warp has a bit set, are records (fired << 32) | h appended, one atomicAdd
-// per warp and round.  The bytes after the last full row are scanned by the
-// last lanes of the grid with plain loads while the other warps stream rows.
+// warp has a bit set, are records (fired << 32) | h appended to the warp's
+// buffer in shared memory.  A full buffer is flushed: either copied out with
+// one atomicAdd, or (MPM_VERIFY) verified by the warp on the spot -- every
+// window the records stand for is looked up in the pattern-group table and
+// compared byte by byte (Section 3.2), while the text is still in L2.  The
+// bytes after the last full row are scanned by the last lanes of the grid
+// with plain loads while the other warps stream rows.
 
 typedef unsigned char u8;
 typedef unsigned short u16;
@@ -71,6 +78,8 @@ typedef Cond<(MPM_EB == 8), u64, u32>::T DT;
 typedef Cond<(NS * K > 32), u64, u32>::T FT;
 
 enum { kCandCountJ = 0, kOccCountJ = 1, kErrorFlagJ = 2 };
+constexpr u32 ECAP = MPM_EMIT_CAP;
+static_assert(ECAP >= 64, "emit buffer");
 
 static_assert(C % 16 == 0 && C % P == 0, "stage bytes");
 static_assert(NS * K <= 64, "fired mask");
@@ -136,30 +145,97 @@ __device__ __forceinline__ void run_stage(const u32* w, DT& D, FT& fm, const ET*
     }
 }
 
-// Appends the records of one stage: for every lane, every sample u with
-// report bits, ((bits) << 32) | (h0 + u*k + k-1).
-__device__ __forceinline__ void emit_stage(FT fm, u32 h0, u64* cand, u32 cap, u32* counters) {
+// Exact check of the window starting at text byte i against the patterns
+// whose first min(m, 16) bytes equal its own (Section 3.2: verification in
+// the original alphabet).  Every equal pattern is appended as (i << 32) | pid.
+__device__ __noinline__ void check_window(const JitScanArgs& A, u32 i) {
+    const u8* w = A.T + i;
+    u64 lo = 0, hi = 0;
+    for (u32 u = 0; u < A.key_bytes; u++) {
+        const u64 b = __ldg(w + u);
+        if (u < 8)
+            lo |= b << (8 * u);
+        else
+            hi |= b << (8 * (u - 8));
+    }
+    const Slot* slots = reinterpret_cast<const Slot*>(A.slots);
+    u32 slot = (u32)key_hash(lo, hi) & A.slot_mask;
+    for (u32 probes = 0; probes <= A.slot_mask; probes++) {
+        const Slot sl = slots[slot];
+        if (sl.count == 0) return;
+        if (sl.lo == lo && sl.hi == hi) {
+            for (u32 row = sl.first; row < sl.first + sl.count; row++) {
+                const u8* p = A.pat + (u64)row * A.m;
+                u32 u = A.key_bytes;
+                while (u < A.m && __ldg(w + u) == __ldg(p + u)) u++;
+                if (u == A.m) {
+                    const u32 idx = atomicAdd(&A.counters[kOccCountJ], 1u);
+                    if (idx < A.occ_cap) A.occ[idx] = ((u64)i << 32) | A.pid[row];
+                }
+            }
+            return;
+        }
+        slot = (slot + 1) & A.slot_mask;
+    }
+}
+
+// The windows of one record (sampled q-gram h, report bits `fired`) at
+// shift s: window h0 = h - (m'-1)k - j stands for the text start h0*q - s.
+__device__ __forceinline__ void verify_record(const JitScanArgs& A, u32 h, u32 fired, int s) {
+    while (fired) {
+        const int j = __ffs((int)fired) - 1;
+        fired &= fired - 1;
+        const i64 i = ((i64)h - RSH - j) * Q - s;
+        if (i < 0 || i + (i64)A.m > (i64)A.n) continue;
+        check_window(A, (u32)i);
+    }
+}
+
+// A warp's buffer of candidate records in shared memory (count warp-uniform).
+struct Emitter {
+    u64* buf;
+    u32 n;
+};
+
+__device__ __forceinline__ void flush(Emitter& E, const JitScanArgs& A) {
+    if (E.n == 0) return;
+    __syncwarp();
     const int lane = threadIdx.x & 31;
+#if MPM_VERIFY
+    if (lane == 0) atomicAdd(&A.counters[kCandCountJ], E.n);
+    const u32 items = E.n * (u32)Q;
+    for (u32 t = lane; t < items; t += 32) {
+        const u64 rec = E.buf[t / Q];
+        verify_record(A, (u32)rec, (u32)(rec >> 32), (int)(t % Q));
+    }
+#else
+    u32 base = 0;
+    if (lane == 0) base = atomicAdd(&A.counters[kCandCountJ], E.n);
+    base = __shfl_sync(0xFFFFFFFFu, base, 0);
+    for (u32 i = lane; i < E.n; i += 32)
+        if (base + i < A.cap) A.cand[base + i] = E.buf[i];
+#endif
+    __syncwarp();
+    E.n = 0;
+}
+
+// Buffers the records of one stage: for every lane, every sample u with
+// report bits, ((bits) << 32) | (h0 + u*k + k-1).
+__device__ __forceinline__ void emit_stage(FT fm, u32 h0, Emitter& E, const JitScanArgs& A) {
     while (true) {
         const bool has = fm != 0;
         const u32 bal = __ballot_sync(0xFFFFFFFFu, has);
         if (bal == 0) break;
-        u32 h = 0, fired = 0;
+        if (E.n + 32 > ECAP) flush(E, A);
         if (has) {
             const int bit = (sizeof(FT) == 8) ? (__ffsll((long long)fm) - 1) : (__ffs((int)fm) - 1);
             const int u = bit / K;
-            fired = (u32)(fm >> (u * K)) & KMASK;
+            const u32 fired = (u32)(fm >> (u * K)) & KMASK;
             fm &= ~((FT)KMASK << (u * K));
-            h = h0 + (u32)(u * K + (K - 1));
+            const u32 h = h0 + (u32)(u * K + (K - 1));
+            E.buf[E.n + __popc(bal & lanemask_lt())] = ((u64)fired << 32) | h;
         }
-        const int leader = __ffs(bal) - 1;
-        u32 base = 0;
-        if (lane == leader) base = atomicAdd(&counters[kCandCountJ], (u32)__popc(bal));
-        base = __shfl_sync(0xFFFFFFFFu, base, leader);
-        if (has) {
-            const u32 idx = base + __popc(bal & lanemask_lt());
-            if (idx < cap) cand[idx] = ((u64)fired << 32) | h;
-        }
+        E.n += __popc(bal);
     }
 }
 
@@ -182,9 +258,11 @@ struct __align__(64) TmapParam {
 extern "C" __global__ void __launch_bounds__(MPM_WARPS * 32, 1)
     mpm_scan_jit(const JitScanArgs A, const __grid_constant__ TmapParam tmap) {
     extern __shared__ __align__(128) u8 smem[];
-    // shared layout: [mask table?][mu, 256][mbarriers][stages, 128-aligned]
+    // shared layout: [mask table?][mu, 256][mbarriers][emit buffers]
+    //                [stages, 128-aligned]
     constexpr u32 TAB = MPM_SMEM ? MPM_TABLE_BYTES : 0u;
-    constexpr u32 STAGE_OFF = (TAB + 256u + 8u * WARPS * S + 127u) / 128u * 128u;
+    constexpr u32 EMIT_OFF = TAB + 256u + 8u * WARPS * S;
+    constexpr u32 STAGE_OFF = (EMIT_OFF + 8u * WARPS * ECAP + 127u) / 128u * 128u;
     u8* s_tab = smem;
     u8* s_mu = smem + TAB;
     u64* s_bar = reinterpret_cast<u64*>(s_mu + 256);
@@ -198,6 +276,9 @@ extern "C" __global__ void __launch_bounds__(MPM_WARPS * 32, 1)
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     u64* bars = s_bar + warp * S;
     u8* stage = s_stage + (u64)warp * S * SLOT;
+    Emitter E;
+    E.buf = reinterpret_cast<u64*>(smem + EMIT_OFF) + warp * ECAP;
+    E.n = 0;
     if (lane == 0) {
         for (int i = 0; i < S; i++) mbar_init(smem_addr(&bars[i]), 1);
         mbar_fence_init();
@@ -284,10 +365,10 @@ extern "C" __global__ void __launch_bounds__(MPM_WARPS * 32, 1)
                                 (int)((gw + (j / nst) * RW) * 32), bar);
                 }
                 if (!valid) fm = 0;
-                if (__any_sync(0xFFFFFFFFu, fm != 0))
-                    emit_stage(fm, h_row + st * (u32)(C / Q), A.cand, A.cap, A.counters);
+                if (__any_sync(0xFFFFFFFFu, fm != 0)) emit_stage(fm, h_row + st * (u32)(C / Q), E, A);
             }
         }
+        flush(E, A);
     }
 
     // ------------------------------------- bytes after the rows, plain loads
@@ -308,17 +389,15 @@ extern "C" __global__ void __launch_bounds__(MPM_WARPS * 32, 1)
             const u32 st = e - Q;
             D = (D << K) | (DT)tab[code_bytes(A.T, st, s_mu)];
             const u32 fired = (u32)(~D >> RSH) & KMASK;
-            const u32 act = __activemask();
-            const u32 bal = __ballot_sync(act, fired != 0);
-            if (bal) {
-                const int leader = __ffs(bal) - 1;
-                u32 base = 0;
-                if (lane == leader) base = atomicAdd(&A.counters[kCandCountJ], (u32)__popc(bal));
-                base = __shfl_sync(act, base, leader);
-                if (fired) {
-                    const u32 idx = base + __popc(bal & lanemask_lt());
-                    if (idx < A.cap) A.cand[idx] = ((u64)fired << 32) | (st / (u32)Q);
-                }
+            if (fired) {
+                // rare: handled by the lane alone
+                const u32 idx = atomicAdd(&A.counters[kCandCountJ], 1u);
+#if MPM_VERIFY
+                (void)idx;
+                for (int sh = 0; sh < Q; sh++) verify_record(A, st / (u32)Q, fired, sh);
+#else
+                if (idx < A.cap) A.cand[idx] = ((u64)fired << 32) | (st / (u32)Q);
+#endif
             }
         }
     }

@@ -9,7 +9,7 @@ struct JitScanArgs {
     const unsigned char* T;       // text (device)
     const void* table;            // mask table (device)
     const unsigned char* mu;      // byte -> reduced symbol (device, 256)
-    unsigned long long* cand;     // candidate records
+    unsigned long long* cand;     // candidate records (candidate variant)
     unsigned int* counters;       // kCandCount, kOccCount, kErrorFlag
     unsigned int n;               // text bytes
     unsigned int cap;             // capacity of cand
@@ -20,6 +20,15 @@ struct JitScanArgs {
     unsigned int pa;              // bytes [pa, n) are read with plain loads
     unsigned int Ls;              // ... in sub-streams of Ls bytes
     unsigned int nstreams;        // number of sub-streams
+    unsigned int m;               // pattern length
+    // verification (the fused variant): pattern groups and outputs
+    const void* slots;            // open-addressing table of pattern groups
+    const unsigned char* pat;     // patterns sorted by bytes, r * m
+    const unsigned int* pid;      // pattern id of each sorted row
+    unsigned long long* occ;      // occurrences (pos << 32) | pid
+    unsigned int slot_mask;
+    unsigned int key_bytes;       // min(m, 16)
+    unsigned int occ_cap;
     unsigned int pad;
 };
 

@@ -2,7 +2,11 @@
 // order; verification appends occurrences through atomics in an order that
 // varies from run to run, so the keys (pos << 32) | pid are sorted.
 //
-// Up to 8192 keys: one block, bitonic sort in shared memory.
+// Up to 4096 keys counted on the device: a grid-wide rank sort -- the keys
+// are unique, so each one goes to the slot given by the number of smaller
+// keys -- which needs no host read-back of the count.
+// Up to 8192 keys with the count known on the host: one block, bitonic sort
+// in shared memory.
 // More: least-significant-digit radix sort, 8-bit digits, only over the
 // digit positions that can be non-zero (pid bits and position bits).  Each
 // pass is a per-block digit histogram, one exclusive scan over
@@ -145,6 +149,36 @@ __global__ void __launch_bounds__(kRadixThreads)
     }
 }
 
+constexpr int kRankThreads = 256;
+constexpr int kRankTile = 2048;
+
+__global__ void __launch_bounds__(kRankThreads)
+    rank_sort_kernel(const uint64_t* keys, const uint32_t* count, uint32_t out_cap,
+                     uint32_t* out_pos, uint32_t* out_pid) {
+    __shared__ uint64_t tile[kRankTile];
+    const uint32_t z = *count;
+    if (z > kRankSortMax || z > out_cap) return;
+    if (blockIdx.x * blockDim.x >= z) return;
+    const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    const bool mine = i < z;
+    const uint64_t key = mine ? keys[i] : 0;
+    uint32_t rank = 0;
+    for (uint32_t t0 = 0; t0 < z; t0 += kRankTile) {
+        const uint32_t len = min((uint32_t)kRankTile, z - t0);
+        __syncthreads();
+        for (uint32_t j = threadIdx.x; j < len; j += blockDim.x) tile[j] = keys[t0 + j];
+        __syncthreads();
+        if (mine) {
+#pragma unroll 8
+            for (uint32_t j = 0; j < len; j++) rank += tile[j] < key ? 1u : 0u;
+        }
+    }
+    if (mine) {
+        out_pos[rank] = (uint32_t)(key >> 32);
+        out_pid[rank] = (uint32_t)key;
+    }
+}
+
 __global__ void split_kernel(const uint64_t* keys, uint32_t z, uint32_t* out_pos,
                              uint32_t* out_pid) {
     for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < z; i += gridDim.x * blockDim.x) {
@@ -155,6 +189,13 @@ __global__ void split_kernel(const uint64_t* keys, uint32_t z, uint32_t* out_pos
 }
 
 }  // namespace
+
+int launch_rank_sort(const uint64_t* keys, const uint32_t* count, uint32_t out_cap,
+                     uint32_t* out_pos, uint32_t* out_pid, cudaStream_t s) {
+    const uint32_t blocks = (kRankSortMax + kRankThreads - 1) / kRankThreads;
+    rank_sort_kernel<<<blocks, kRankThreads, 0, s>>>(keys, count, out_cap, out_pos, out_pid);
+    return cudaPeekAtLastError() == cudaSuccess ? 1 : -1;
+}
 
 size_t sort_hist_entries(uint32_t z) {
     const size_t nblocks = (z + kRadixTile - 1) / kRadixTile;
