@@ -193,6 +193,9 @@ def main():
     ap.add_argument("--cpu-sample-mib", type=int, default=256)
     ap.add_argument("--ref-sample-mib", type=int, default=64)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-tune", action="store_true")
+    ap.add_argument("--tune-sample-mib", type=int, default=32)
+    ap.add_argument("--tune-sets", type=int, default=48)
     args = ap.parse_args()
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -214,7 +217,16 @@ def main():
 
     case, sigma, desc = make_case(args.workload)
     T = torch.from_numpy(case.T).to(dev)
-    m = mpm.Matcher(case.P, sigma=sigma)
+    tuning = None
+    params = {}
+    if not args.no_tune:
+        # exhaustive autotuner on a sample of the text; not timed, like the build
+        sample = T[: min(case.n, args.tune_sample_mib << 20)]
+        t0 = time.perf_counter()
+        params, sets = mpm.autotune(case.P, sigma, sample, kernels=3, max_sets=args.tune_sets)
+        tuning = {"sample_bytes": int(sample.numel()), "sets_timed": len(sets),
+                  "seconds": round(time.perf_counter() - t0, 2)}
+    m = mpm.Matcher(case.P, sigma=sigma, **params)
     m.set_timing(True)
     cap = max(1 << 16, 8 * case.r)
     out_pos = torch.empty(cap, dtype=torch.int32, device=dev)
@@ -295,7 +307,7 @@ def main():
             "ms_per_step": elapsed_ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "u8", "data": "synthetic",
             "config": {"workload": args.workload, "description": desc, "n": case.n,
-                       "r": case.r, "m": case.m, "params": m.params,
+                       "r": case.r, "m": case.m, "params": m.params, "tuning": tuning,
                        "l2": "inputs larger than L2 (no flush)",
                        "parallelism": "replicas" if world > 1 else "single GPU"},
             "hbm_frac_of_%s_peak" % peak_kind: value / peak,

@@ -75,7 +75,8 @@ extern "C" {
  */
 #define MPM_KERNEL_AUTO        0
 #define MPM_KERNEL_GENERIC     1
-#define MPM_KERNEL_SPECIALISED 2
+#define MPM_KERNEL_SPECIALISED 2  /* specialised scan that verifies its candidates  */
+#define MPM_KERNEL_SPLIT       3  /* specialised scan, then the verification kernel */
 
 typedef struct {
     int q;
@@ -233,6 +234,45 @@ int mpm_encode(mpm_handle *h, const uint8_t *T, size_t n, uint32_t *codes);
  */
 int mpm_scan(mpm_handle *h, const uint8_t *T, size_t n, uint64_t *cand,
              size_t *count);
+
+/* --------------------------------------------------------- autotuning */
+
+typedef struct {
+    int max_q;           /* largest q tried; 0 = 8                                  */
+    int max_k;           /* largest k tried; 0 = 8                                  */
+    int reps;            /* timed searches per parameter set (median); 0 = 3       */
+    int kernels;         /* bit 0 specialised, bit 1 split, bit 2 generic; 0 = 1   */
+    int max_sets;        /* at most this many sets are timed, lowest estimated
+                            candidate rate first; 0 = 64                            */
+    double max_rate;     /* sets whose estimated candidate records per sampled
+                            q-gram exceed this are not timed; 0 = 0.05              */
+} mpm_tune_opts;
+
+typedef struct {
+    mpm_params params;   /* resolved parameters of the set                         */
+    mpm_table_info info;
+    double ms;           /* median wall time of one mpm_search of the sample       */
+    uint64_t candidates; /* candidate records of that search                        */
+    uint64_t z;          /* occurrences                                             */
+    int status;          /* MPM_OK, or why the set could not be built or run       */
+} mpm_tune_entry;
+
+/*
+ * Exhaustive autotuner (not in the paper, which fixes q from log_sigma(rm)
+ * and k by a closed form, Section 3.2): every feasible combination of
+ * sigma' (powers of two up to the pattern alphabet), mapping (equal-weight
+ * greedy bins, and low-order bits where they keep the pattern symbols
+ * distinct), q <= max_q and k <= max_k is planned; sets whose estimated
+ * candidate rate exceeds max_rate are dropped, the rest (at most max_sets)
+ * are built and timed on the sample T[0..n) (device or host memory) with
+ * each kernel selected in opts->kernels.  *best receives the fastest set;
+ * entries (may be NULL) receive up to cap timed sets in the order they were
+ * timed and *count the number of sets timed.  opts may be NULL.  Returns
+ * MPM_EINVAL for bad arguments or when no set can be run.
+ */
+int mpm_autotune(const uint8_t *P, size_t r, size_t m, int sigma, const uint8_t *T, size_t n,
+                 const mpm_tune_opts *opts, mpm_params *best, mpm_tune_entry *entries,
+                 size_t cap, size_t *count);
 
 /* ------------------------------------------- search that allocates nothing */
 

@@ -17,7 +17,8 @@ from ._native import (KERNEL_AUTO, KERNEL_GENERIC, KERNEL_SPECIALISED,  # noqa: 
                       MPM_ENOTSUP, MPM_OK, TABLE_AUTO, TABLE_GLOBAL, TABLE_SMEM, MpmError,
                       Params, Stats, TableInfo, declared_functions, lib)
 
-__all__ = ["Matcher", "plan", "host_tables", "MpmError", "lib", "declared_functions"]
+__all__ = ["Matcher", "plan", "host_tables", "autotune", "jit_compile", "MpmError", "lib",
+           "declared_functions"]
 
 
 def _torch():
@@ -74,6 +75,30 @@ def host_tables(P, sigma, **kw):
     if rc:
         raise MpmError(rc, "mpm_host_tables")
     return mu, table, dict(info, **params)
+
+
+def autotune(P, sigma, T, max_q=0, max_k=0, reps=0, kernels=0, max_sets=0, max_rate=0.0):
+    """Exhaustive parameter search timed on the sample text T (CUDA tensor or
+    numpy).  Returns (best params dict, list of timed sets)."""
+    from ._native import TuneEntry, TuneOpts
+    P = _patterns(P)
+    opts = TuneOpts(max_q, max_k, reps, kernels, max_sets, max_rate)
+    cap = 4096
+    entries = (TuneEntry * cap)()
+    best = Params()
+    count = ctypes.c_size_t(0)
+    if hasattr(T, "is_cuda") and T.is_cuda:
+        tp, tn = T.data_ptr(), T.numel()
+    else:
+        T = np.ascontiguousarray(np.asarray(T, dtype=np.uint8))
+        tp, tn = T.ctypes.data, T.size
+    rc = lib().mpm_autotune(P.ctypes.data, P.shape[0], P.shape[1], sigma, tp, tn,
+                            ctypes.byref(opts), ctypes.byref(best), entries, cap,
+                            ctypes.byref(count))
+    if rc:
+        raise MpmError(rc, "mpm_autotune")
+    out = [entries[i].as_dict() for i in range(min(count.value, cap))]
+    return best.as_dict(), out
 
 
 def _ptr(x):

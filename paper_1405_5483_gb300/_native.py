@@ -17,7 +17,7 @@ NOALLOC_MAX_CANDIDATES = 1 << 21
 NOALLOC_MAX_OCCURRENCES = 8192
 MAP_AUTO, MAP_RANK, MAP_GREEDY, MAP_LOWBITS = range(4)
 TABLE_AUTO, TABLE_SMEM, TABLE_GLOBAL = range(3)
-KERNEL_AUTO, KERNEL_GENERIC, KERNEL_SPECIALISED = range(3)
+KERNEL_AUTO, KERNEL_GENERIC, KERNEL_SPECIALISED, KERNEL_SPLIT = range(4)
 
 
 class Params(ctypes.Structure):
@@ -48,6 +48,22 @@ class Stats(ctypes.Structure):
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+class TuneOpts(ctypes.Structure):
+    _fields_ = [("max_q", ctypes.c_int), ("max_k", ctypes.c_int), ("reps", ctypes.c_int),
+                ("kernels", ctypes.c_int), ("max_sets", ctypes.c_int),
+                ("max_rate", ctypes.c_double)]
+
+
+class TuneEntry(ctypes.Structure):
+    _fields_ = [("params", Params), ("info", TableInfo), ("ms", ctypes.c_double),
+                ("candidates", ctypes.c_uint64), ("z", ctypes.c_uint64),
+                ("status", ctypes.c_int)]
+
+    def as_dict(self):
+        return {"params": self.params.as_dict(), "info": self.info.as_dict(), "ms": self.ms,
+                "candidates": self.candidates, "z": self.z, "status": self.status}
 
 
 class MpmError(RuntimeError):
@@ -94,6 +110,9 @@ def lib():
         "mpm_scan": (ctypes.c_int, [vp, u8p, sz, vp, szp]),
         "mpm_search_noalloc": (ctypes.c_int, [vp, u8p, sz, vp, vp, szp]),
         "mpm_jit_compile": (ctypes.c_int, [u8p, sz, sz, ctypes.c_int, Pp, ctypes.c_char_p, sz]),
+        "mpm_autotune": (ctypes.c_int, [u8p, sz, sz, ctypes.c_int, u8p, sz,
+                                        ctypes.POINTER(TuneOpts), Pp, ctypes.POINTER(TuneEntry),
+                                        sz, szp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(L, name)

@@ -18,10 +18,12 @@ INCLUDE = os.path.join(ROOT, "include")
 OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "libmpm.so")
 
-SOURCES = ["host_build.cpp", "capi.cu", "scan.cu", "encode.cu", "verify.cu", "sort.cu", "jit.cpp"]
+SOURCES = ["host_build.cpp", "capi.cu", "scan.cu", "encode.cu", "verify.cu", "sort.cu", "jit.cpp",
+           "tune.cpp"]
 # files concatenated, in this order, into the source of the scan kernel that
 # is compiled at run time
-JIT_PARTS = ["keyhash.h", "scan_jit_args.h", "ptx_common.cuh", "scan_jit.cuh"]
+JIT_PARTS = ["keyhash.h", "scan_jit_args.h", "ptx_common.cuh", "window_check.cuh",
+             "scan_jit.cuh"]
 GEN = os.path.join(OUT, "gen")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 

@@ -210,6 +210,10 @@ int enqueue_filter(mpm_handle* h, const uint8_t* dT, uint32_t n, uint64_t* cand,
             cudaEventRecord(h->ev[2], s);
         }
         return MPM_OK;
+    } else if (h->jit_cand) {
+        // split: the specialised scan writes candidates, verification follows
+        l = mpm::launch_scan_jit(scan_args(h, dT, n, cand, cand_cap, counters), nullptr,
+                                 h->jit_cand, h->num_sms, h->plan.p.chunk, s);
     } else {
         l = mpm::launch_scan(scan_args(h, dT, n, cand, cand_cap, counters), h->num_sms,
                              h->plan.p.chunk, s);
@@ -332,8 +336,14 @@ mpm_handle* mpm_build(const uint8_t* P, size_t r, size_t m, int sigma, const mpm
     if (!h->plan.p.smag && h->plan.p.kernel != MPM_KERNEL_GENERIC) {
         int err = MPM_OK;
         std::string log;
-        h->jit = mpm::jit_scan_kernel(filter_dev(h), true, h->device, &err, &log);
-        if (!h->jit && h->plan.p.kernel == MPM_KERNEL_SPECIALISED) {
+        const bool split = h->plan.p.kernel == MPM_KERNEL_SPLIT;
+        if (split) {
+            h->jit_cand = mpm::jit_scan_kernel(filter_dev(h), false, h->device, &err, &log);
+            h->jit_cand_tried = true;
+        } else {
+            h->jit = mpm::jit_scan_kernel(filter_dev(h), true, h->device, &err, &log);
+        }
+        if (!h->jit && !h->jit_cand && (h->plan.p.kernel == MPM_KERNEL_SPECIALISED || split)) {
             if (!log.empty()) std::fprintf(stderr, "mpm: specialised scan failed:\n%s\n", log.c_str());
             release(h);
             set_error(err ? err : MPM_ENOTSUP);
@@ -387,7 +397,7 @@ int mpm_search(mpm_handle* h, const uint8_t* T, size_t n, uint32_t* out_pos, uin
     const size_t out_capacity = *z;
     h->stats = mpm_stats{};
     h->stats.n = n;
-    h->stats.specialised = fused_search(h) ? 1u : 0u;
+    h->stats.specialised = (h->jit || h->jit_cand) && !h->plan.p.smag ? 1u : 0u;
     const uint32_t q = (uint32_t)h->plan.p.q, k = (uint32_t)h->plan.p.k;
     h->stats.sampled = (n / q) / k;
     int launches = 0;

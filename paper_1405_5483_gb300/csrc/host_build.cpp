@@ -215,7 +215,7 @@ int make_plan(const uint8_t* P, size_t r, size_t m, int sigma, const mpm_params*
     if (req.map_shift > 7) return MPM_EINVAL;
     if (req.table_place < 0 || req.table_place > MPM_TABLE_GLOBAL) return MPM_EINVAL;
     if (req.smag < 0 || req.smag > 1 || req.chunk < 0) return MPM_EINVAL;
-    if (req.kernel < MPM_KERNEL_AUTO || req.kernel > MPM_KERNEL_SPECIALISED) return MPM_EINVAL;
+    if (req.kernel < MPM_KERNEL_AUTO || req.kernel > MPM_KERNEL_SPLIT) return MPM_EINVAL;
 
     uint64_t h[256];
     histogram(P, r, m, h);

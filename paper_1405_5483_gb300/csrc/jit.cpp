@@ -15,6 +15,7 @@
 #include <memory>
 #include <mutex>
 #include <string>
+#include <thread>
 #include <vector>
 
 #include <cudaTypedefs.h>
@@ -151,7 +152,7 @@ struct JitKernel {
 bool jit_spec(const FilterDev& f, bool verify, JitSpec* out) {
     JitSpec s{};
     s.verify = verify ? 1 : 0;
-    s.ecap = 96;
+    s.ecap = 64;
     s.q = f.q;
     s.k = f.k;
     s.mp = f.mprime;
@@ -240,10 +241,54 @@ int jit_compile_only(const FilterDev& f, bool verify, std::string* log) {
     return compile_spec(s, &cubin, log);
 }
 
+namespace {
+std::mutex g_cache_mu;
+std::map<std::string, std::unique_ptr<JitKernel>> g_cache;  // loaded kernels
+std::map<std::string, std::string> g_cubins;               // compiled, not yet loaded
+}  // namespace
+
+void jit_precompile(const std::vector<FilterDev>& fs, bool verify, int threads) {
+    std::vector<JitSpec> todo;
+    {
+        std::lock_guard<std::mutex> lock(g_cache_mu);
+        std::map<std::string, bool> seen;
+        for (const auto& f : fs) {
+            JitSpec s;
+            if (!jit_spec(f, verify, &s)) continue;
+            const std::string d = s.defines();
+            if (g_cubins.count(d) || seen.count(d)) continue;
+            seen[d] = true;
+            todo.push_back(s);
+        }
+    }
+    if (todo.empty() || !nvrtc().ok) return;
+    std::vector<std::string> out(todo.size());
+    std::vector<int> rc(todo.size(), MPM_ECUDA);
+    size_t next = 0;
+    std::mutex next_mu;
+    auto work = [&] {
+        for (;;) {
+            size_t i;
+            {
+                std::lock_guard<std::mutex> lock(next_mu);
+                if (next >= todo.size()) return;
+                i = next++;
+            }
+            rc[i] = compile_spec(todo[i], &out[i], nullptr);
+        }
+    };
+    std::vector<std::thread> pool;
+    for (int t = 0; t < std::max(1, threads); t++) pool.emplace_back(work);
+    for (auto& t : pool) t.join();
+    std::lock_guard<std::mutex> lock(g_cache_mu);
+    for (size_t i = 0; i < todo.size(); i++)
+        if (rc[i] == MPM_OK) g_cubins[todo[i].defines()] = std::move(out[i]);
+}
+
 const JitKernel* jit_scan_kernel(const FilterDev& f, bool verify, int device, int* err,
-                                std::string* log) {
-    static std::mutex mu;
-    static std::map<std::string, std::unique_ptr<JitKernel>> cache;
+                                 std::string* log) {
+    auto& mu = g_cache_mu;
+    auto& cache = g_cache;
     *err = MPM_OK;
     JitSpec s;
     if (!jit_spec(f, verify, &s)) {
@@ -260,10 +305,16 @@ const JitKernel* jit_scan_kernel(const FilterDev& f, bool verify, int device, in
     auto it = cache.find(key);
     if (it != cache.end()) return it->second.get();
     std::string cubin;
-    int rc = compile_spec(s, &cubin, log);
-    if (rc) {
-        *err = rc;
-        return nullptr;
+    auto pre = g_cubins.find(s.defines());
+    if (pre != g_cubins.end()) {
+        cubin = pre->second;
+    } else {
+        int rc = compile_spec(s, &cubin, log);
+        if (rc) {
+            *err = rc;
+            return nullptr;
+        }
+        g_cubins[s.defines()] = cubin;
     }
     CUmodule mod;
     CUfunction fn;

@@ -3,6 +3,7 @@
 
 #include <cstdint>
 #include <string>
+#include <vector>
 #include <cuda.h>
 #include <cuda_runtime.h>
 
@@ -86,6 +87,9 @@ struct JitKernel;
 // occurrences (mpm_search); otherwise it appends candidate records.
 const JitKernel* jit_scan_kernel(const FilterDev& f, bool verify, int device, int* err,
                                 std::string* log);
+// Compiles the specialisations of these filters that are not compiled yet,
+// on `threads` host threads, and keeps the cubins for jit_scan_kernel.
+void jit_precompile(const std::vector<FilterDev>& fs, bool verify, int threads);
 // Host-only: compiles the specialisation without loading it.
 int jit_compile_only(const FilterDev& f, bool verify, std::string* log);
 bool jit_verifies(const JitKernel* k);

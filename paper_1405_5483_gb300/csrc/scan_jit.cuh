@@ -145,49 +145,32 @@ __device__ __forceinline__ void run_stage(const u32* w, DT& D, FT& fm, const ET*
     }
 }
 
-// Exact check of the window starting at text byte i against the patterns
-// whose first min(m, 16) bytes equal its own (Section 3.2: verification in
-// the original alphabet).  Every equal pattern is appended as (i << 32) | pid.
-__device__ __noinline__ void check_window(const JitScanArgs& A, u32 i) {
-    const u8* w = A.T + i;
-    u64 lo = 0, hi = 0;
-    for (u32 u = 0; u < A.key_bytes; u++) {
-        const u64 b = __ldg(w + u);
-        if (u < 8)
-            lo |= b << (8 * u);
-        else
-            hi |= b << (8 * (u - 8));
-    }
-    const Slot* slots = reinterpret_cast<const Slot*>(A.slots);
-    u32 slot = (u32)key_hash(lo, hi) & A.slot_mask;
-    for (u32 probes = 0; probes <= A.slot_mask; probes++) {
-        const Slot sl = slots[slot];
-        if (sl.count == 0) return;
-        if (sl.lo == lo && sl.hi == hi) {
-            for (u32 row = sl.first; row < sl.first + sl.count; row++) {
-                const u8* p = A.pat + (u64)row * A.m;
-                u32 u = A.key_bytes;
-                while (u < A.m && __ldg(w + u) == __ldg(p + u)) u++;
-                if (u == A.m) {
-                    const u32 idx = atomicAdd(&A.counters[kOccCountJ], 1u);
-                    if (idx < A.occ_cap) A.occ[idx] = ((u64)i << 32) | A.pid[row];
-                }
-            }
-            return;
-        }
-        slot = (slot + 1) & A.slot_mask;
-    }
-}
-
 // The windows of one record (sampled q-gram h, report bits `fired`) at
 // shift s: window h0 = h - (m'-1)k - j stands for the text start h0*q - s.
+__device__ __forceinline__ WindowCtx window_ctx(const JitScanArgs& A) {
+    WindowCtx c;
+    c.T = A.T;
+    c.n = A.n;
+    c.m = A.m;
+    c.key_bytes = A.key_bytes;
+    c.slot_mask = A.slot_mask;
+    c.occ_cap = A.occ_cap;
+    c.slots = reinterpret_cast<const Slot*>(A.slots);
+    c.pat = A.pat;
+    c.pid = A.pid;
+    c.occ = A.occ;
+    c.occ_count = &A.counters[kOccCountJ];
+    return c;
+}
+
 __device__ __forceinline__ void verify_record(const JitScanArgs& A, u32 h, u32 fired, int s) {
+    const WindowCtx c = window_ctx(A);
     while (fired) {
         const int j = __ffs((int)fired) - 1;
         fired &= fired - 1;
         const i64 i = ((i64)h - RSH - j) * Q - s;
         if (i < 0 || i + (i64)A.m > (i64)A.n) continue;
-        check_window(A, (u32)i);
+        check_window(c, (u32)i);
     }
 }
 

@@ -1,0 +1,209 @@
+// Exhaustive autotuner over the filter parameters (sigma', mapping, q, k)
+// and the scan kernel variant: plan every feasible set on the host, drop the
+// sets whose estimated candidate rate is hopeless, compile the remaining
+// specialisations in parallel, then build and time each set on a sample
+// text and keep the fastest.  The paper chooses q from log_sigma(rm) and k
+// by a closed form (Section 3.2); here the choice is measured.
+#include <algorithm>
+#include <chrono>
+#include <cstring>
+#include <thread>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "kernels.h"
+
+namespace {
+
+using mpm::set_error;
+
+mpm::FilterDev filter_of(const mpm::Plan& plan) {
+    mpm::FilterDev f{};
+    f.table_bytes = (uint32_t)((plan.info.table_bytes + 15) & ~uint64_t(15));
+    f.entry_bytes = plan.info.entry_bytes;
+    f.smem_table = plan.p.table_place == MPM_TABLE_SMEM;
+    f.map_kind = plan.p.map_kind;
+    f.q = plan.p.q;
+    f.k = plan.p.k;
+    f.ell = plan.ell;
+    f.shift = plan.p.map_shift;
+    f.mprime = plan.info.mprime;
+    f.positions = plan.info.positions;
+    return f;
+}
+
+bool on_device(const void* p) {
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+struct Candidate {
+    mpm_params p;
+    mpm::Plan plan;
+    double key;  // estimated candidate records per text byte
+};
+
+constexpr uint64_t kTuneMaxTable = 16ull << 20;
+
+}  // namespace
+
+extern "C" int mpm_autotune(const uint8_t* P, size_t r, size_t m, int sigma, const uint8_t* T,
+                            size_t n, const mpm_tune_opts* opts, mpm_params* best,
+                            mpm_tune_entry* entries, size_t cap, size_t* count) {
+    if (!P || !best || !count || r == 0 || m == 0 || (n > 0 && !T) || n >= (1ull << 32))
+        return set_error(MPM_EINVAL);
+    mpm_tune_opts o{};
+    if (opts) o = *opts;
+    const int max_q = o.max_q > 0 ? std::min(o.max_q, 16) : 8;
+    const int max_k = o.max_k > 0 ? std::min(o.max_k, mpm::kMaxK) : 8;
+    const int reps = o.reps > 0 ? o.reps : 3;
+    const int kernels = o.kernels > 0 ? o.kernels : 1;
+    const size_t max_sets = o.max_sets > 0 ? (size_t)o.max_sets : 64;
+    const double max_rate = o.max_rate > 0 ? o.max_rate : 0.05;
+
+    // the pattern alphabet bounds sigma'
+    bool seen[256] = {false};
+    int distinct = 0;
+    for (size_t i = 0; i < r * m; i++)
+        if (!seen[P[i]]) {
+            seen[P[i]] = true;
+            distinct++;
+        }
+    const int sigma_eff = std::min(256, std::max(sigma, distinct));
+    int top = 2;
+    while (top < distinct && top < 256) top <<= 1;
+
+    std::vector<Candidate> cands;
+    for (int sr = 2; sr <= top; sr <<= 1) {
+        // low-order bits only where they keep the pattern symbols apart
+        std::vector<int> kinds = {MPM_MAP_GREEDY};
+        {
+            mpm_params a{};
+            a.sigma_r = sr;
+            a.map_shift = -1;
+            mpm::Plan pa;
+            if (mpm::make_plan(P, r, m, sigma_eff, &a, &pa) == MPM_OK &&
+                pa.p.map_kind == MPM_MAP_LOWBITS)
+                kinds.push_back(MPM_MAP_LOWBITS);
+        }
+        for (int kind : kinds)
+            for (int q = 1; q <= max_q; q++)
+                for (int k = 1; k <= max_k; k++) {
+                    mpm_params p{};
+                    p.q = q;
+                    p.sigma_r = sr;
+                    p.k = k;
+                    p.map_kind = kind;
+                    p.map_shift = -1;
+                    Candidate c;
+                    if (mpm::make_plan(P, r, m, sigma_eff, &p, &c.plan) != MPM_OK) continue;
+                    if (c.plan.info.table_bytes > kTuneMaxTable) continue;
+                    if (c.plan.info.est_candidate_rate > max_rate) continue;
+                    c.p = c.plan.p;
+                    c.key = c.plan.info.est_candidate_rate / (double)(q * k);
+                    cands.push_back(c);
+                }
+    }
+    std::stable_sort(cands.begin(), cands.end(),
+                     [](const Candidate& a, const Candidate& b) { return a.key < b.key; });
+    if (cands.size() > max_sets) cands.resize(max_sets);
+    if (cands.empty()) return set_error(MPM_EINVAL);
+
+    // compile every specialisation up front, in parallel
+    const int threads = (int)std::max(1u, std::thread::hardware_concurrency());
+    std::vector<mpm::FilterDev> fs;
+    for (const auto& c : cands) fs.push_back(filter_of(c.plan));
+    if (kernels & 1) mpm::jit_precompile(fs, true, threads);
+    if (kernels & 2) mpm::jit_precompile(fs, false, threads);
+
+    // the sample on the device, and output buffers
+    const uint8_t* dT = T;
+    uint8_t* own_text = nullptr;
+    if (n > 0 && !on_device(T)) {
+        if (cudaMalloc(&own_text, n) != cudaSuccess ||
+            cudaMemcpy(own_text, T, n, cudaMemcpyHostToDevice) != cudaSuccess) {
+            cudaGetLastError();
+            cudaFree(own_text);
+            return set_error(MPM_ENOMEM);
+        }
+        dT = own_text;
+    }
+    size_t out_cap = 1 << 16;
+    uint32_t* d_out = nullptr;
+    if (cudaMalloc(&d_out, 2 * out_cap * sizeof(uint32_t)) != cudaSuccess) {
+        cudaGetLastError();
+        cudaFree(own_text);
+        return set_error(MPM_ENOMEM);
+    }
+
+    size_t timed = 0;
+    bool have_best = false;
+    double best_ms = 0.0;
+    const int modes[3] = {MPM_KERNEL_SPECIALISED, MPM_KERNEL_SPLIT, MPM_KERNEL_GENERIC};
+    for (const auto& c : cands) {
+        for (int bit = 0; bit < 3; bit++) {
+            if (!(kernels & (1 << bit))) continue;
+            mpm_tune_entry e{};
+            e.params = c.p;
+            e.params.kernel = modes[bit];
+            e.info = c.plan.info;
+            mpm_handle* h = mpm_build(P, r, m, sigma_eff, &e.params);
+            if (!h) {
+                e.status = mpm_last_error();
+            } else {
+                std::vector<double> ms;
+                for (int it = 0; it <= reps && e.status == MPM_OK; it++) {
+                    size_t z = out_cap;
+                    const auto t0 = std::chrono::steady_clock::now();
+                    int rc = mpm_search(h, dT, n, d_out, d_out + out_cap, &z);
+                    const auto t1 = std::chrono::steady_clock::now();
+                    if (rc == MPM_ECAPACITY) {
+                        cudaFree(d_out);
+                        out_cap = z + 1024;
+                        if (cudaMalloc(&d_out, 2 * out_cap * sizeof(uint32_t)) != cudaSuccess) {
+                            cudaGetLastError();
+                            d_out = nullptr;
+                            e.status = MPM_ENOMEM;
+                            break;
+                        }
+                        it--;
+                        continue;
+                    }
+                    if (rc) {
+                        e.status = rc;
+                        break;
+                    }
+                    if (it > 0)  // the first search warms up
+                        ms.push_back(std::chrono::duration<double, std::milli>(t1 - t0).count());
+                }
+                if (e.status == MPM_OK && !ms.empty()) {
+                    std::sort(ms.begin(), ms.end());
+                    e.ms = ms[ms.size() / 2];
+                    mpm_stats st;
+                    mpm_get_stats(h, &st);
+                    e.candidates = st.candidates;
+                    e.z = st.z;
+                    if (!have_best || e.ms < best_ms) {
+                        have_best = true;
+                        best_ms = e.ms;
+                        *best = e.params;
+                    }
+                }
+                mpm_free(h);
+            }
+            if (entries && timed < cap) entries[timed] = e;
+            timed++;
+            if (!d_out) break;
+        }
+        if (!d_out) break;
+    }
+    cudaFree(d_out);
+    cudaFree(own_text);
+    *count = timed;
+    return set_error(have_best ? MPM_OK : MPM_EINVAL);
+}

@@ -11,48 +11,29 @@
 // the key and every equal pattern id is appended as (i << 32) | pid.
 #include "device_common.cuh"
 #include "kernels.h"
+#include "window_check.cuh"
 
 namespace mpm {
 
 namespace {
-
-__device__ __forceinline__ void emit_occ(const VerifyArgs& A, uint32_t i, uint32_t pid) {
-    const uint32_t idx = atomicAdd(&A.counters[kOccCount], 1u);
-    if (idx < A.occ_cap) A.occ[idx] = ((uint64_t)i << 32) | pid;
-}
-
-__device__ void check_window(const VerifyArgs& A, uint32_t i) {
-    const uint8_t* w = A.T + i;
-    uint64_t lo = 0, hi = 0;
-    for (int u = 0; u < A.key_bytes; u++) {
-        const uint64_t b = w[u];
-        if (u < 8)
-            lo |= b << (8 * u);
-        else
-            hi |= b << (8 * (u - 8));
-    }
-    uint32_t slot = (uint32_t)key_hash(lo, hi) & A.slot_mask;
-    for (uint32_t probes = 0; probes <= A.slot_mask; probes++) {
-        const Slot sl = A.slots[slot];
-        if (sl.count == 0) return;
-        if (sl.lo == lo && sl.hi == hi) {
-            for (uint32_t row = sl.first; row < sl.first + sl.count; row++) {
-                const uint8_t* p = A.pat + (size_t)row * A.m;
-                uint32_t u = (uint32_t)A.key_bytes;
-                while (u < A.m && w[u] == p[u]) u++;
-                if (u == A.m) emit_occ(A, i, A.pid[row]);
-            }
-            return;
-        }
-        slot = (slot + 1) & A.slot_mask;
-    }
-}
 
 __global__ void __launch_bounds__(256) verify_kernel(const VerifyArgs A) {
     const uint32_t count = min(A.counters[kCandCount], A.cand_cap);
     const uint64_t total = (uint64_t)count * A.q;
     const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
     const int64_t lead = (int64_t)(A.mprime - 1) * A.k;
+    WindowCtx wc;
+    wc.T = A.T;
+    wc.n = A.n;
+    wc.m = A.m;
+    wc.key_bytes = (unsigned int)A.key_bytes;
+    wc.slot_mask = A.slot_mask;
+    wc.occ_cap = A.occ_cap;
+    wc.slots = A.slots;
+    wc.pat = A.pat;
+    wc.pid = A.pid;
+    wc.occ = reinterpret_cast<unsigned long long*>(A.occ);
+    wc.occ_count = &A.counters[kOccCount];
     for (uint64_t idx = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
          idx += stride) {
         const uint32_t c = (uint32_t)(idx / A.q);
@@ -66,7 +47,7 @@ __global__ void __launch_bounds__(256) verify_kernel(const VerifyArgs A) {
             const int64_t h0 = h - lead - j;
             const int64_t i = h0 * A.q - s;
             if (i < 0 || i + (int64_t)A.m > (int64_t)A.n) continue;
-            check_window(A, (uint32_t)i);
+            check_window(wc, (uint32_t)i);
         }
     }
 }

@@ -138,7 +138,7 @@ SCAN_CASES = [
     ("english", 32, dict(q=2, sigma_r=16, k=2, map_kind=3, map_shift=6)),
     ("protein", 32, dict(q=5, sigma_r=16, k=1, map_kind=2, table_place=2)),  # 1 MB table in L2
 ]
-KERNELS = [1, 2]  # generic, specialised
+KERNELS = [1, 2, 3]  # generic, specialised (verifies itself), specialised + verify kernel
 
 
 @pytest.mark.parametrize("kernel", KERNELS)
@@ -150,7 +150,7 @@ def test_scan_candidates_match_oracle(mpm, kind, mlen, kw, kernel):
     rec = m.scan(dev(c.T))
     torch.cuda.synchronize()
     if not kw.get("smag"):
-        assert m.stats["specialised"] == (1 if kernel == 2 else 0)
+        assert m.stats["specialised"] == (0 if kernel == 1 else 1)
     got = windows_of(rec, p, info)
     assert np.unique(got).size == got.size, "a window was reported twice"
     want = np.array(oracle_windows(c.T, c.P, p), dtype=np.int64)
@@ -282,3 +282,15 @@ def test_full_size_dna_large_sets(mpm, native, r, mlen):
     # every planted pattern occurs at its planting offset
     pos_set = z
     assert pos_set >= r // 10
+
+
+def test_autotune_picks_a_set_that_is_exact(mpm, native):
+    c = W.protein_case(4 << 20, 300, 32, 150)
+    best, sets = mpm.autotune(c.P, 20, dev(c.T), kernels=7, max_sets=12, reps=2)
+    ok = [e for e in sets if e["status"] == 0]
+    assert ok, sets
+    fastest = min(ok, key=lambda e: e["ms"])
+    assert fastest["params"] == best
+    # every timed set found the same occurrences
+    assert len({e["z"] for e in ok}) == 1
+    check_search(mpm, native, c.T, c.P, 20, **best)
