@@ -194,7 +194,8 @@ def main():
     ap.add_argument("--ref-sample-mib", type=int, default=64)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-tune", action="store_true")
-    ap.add_argument("--tune-sample-mib", type=int, default=32)
+    ap.add_argument("--tune-sample-mib", type=int, default=256)
+    ap.add_argument("--params", default="", help="JSON filter parameters; skips tuning")
     ap.add_argument("--tune-sets", type=int, default=48)
     args = ap.parse_args()
 
@@ -219,7 +220,9 @@ def main():
     T = torch.from_numpy(case.T).to(dev)
     tuning = None
     params = {}
-    if not args.no_tune:
+    if args.params:
+        params = json.loads(args.params)
+    elif not args.no_tune:
         # exhaustive autotuner on a sample of the text; not timed, like the build
         sample = T[: min(case.n, args.tune_sample_mib << 20)]
         t0 = time.perf_counter()
@@ -289,13 +292,7 @@ def main():
     scan_avg = statistics.mean(scan_ms)
     algo_bytes = case.n + 8 * st["candidates"]
     achieved = algo_bytes / (scan_avg * 1e-3) / 1e9
-    traffic = None
-    tpath = os.path.join(ROOT, "profiles", "scan_traffic.json")
-    if os.path.exists(tpath):
-        with open(tpath) as f:
-            tj = json.load(f)
-        if tj.get("workload") == args.workload and tj.get("kernel_rev") == kernel_rev():
-            traffic = tj.get("traffic_bytes_per_launch")
+    traffic = recorded_traffic(args.workload, m.params)
 
     if rank == 0:
         cpu = None
@@ -331,13 +328,40 @@ def main():
 
 
 def kernel_rev():
-    """A hash of the scan kernel's source, to tie stored counters to it."""
+    """A hash of the specialised scan kernel's source and launch geometry, to
+    tie DRAM counters recorded under profiles/ to the code that made them."""
     import hashlib
     h = hashlib.sha1()
-    for f in ("scan.cu", "device_common.cuh", "kernels.h"):
+    for f in ("keyhash.h", "scan_jit_args.h", "ptx_common.cuh", "window_check.cuh",
+              "scan_jit.cuh", "jit.cpp"):
         with open(os.path.join(ROOT, "paper_1405_5483_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:12]
+
+
+def recorded_traffic(workload, params):
+    """DRAM bytes per launch of the scan kernel from the ncu summary of this
+    workload, when it was taken on the current kernel with these parameters."""
+    path = os.path.join(ROOT, "profiles", "mpm_scan_jit_%s.md" % workload)
+    if not os.path.exists(path):
+        return None
+    vals = {}
+    for line in open(path):
+        if ":" in line and line.startswith("- `"):
+            k, v = line[3:].split("`", 1)
+            vals[k.strip()] = v.split(":", 1)[1].strip().strip("`")
+    if vals.get("kernel_rev") != kernel_rev():
+        return None
+    try:
+        rec = json.loads(vals.get("params", "{}"))
+    except ValueError:
+        return None
+    if any(params.get(k) != v for k, v in rec.items()):
+        return None
+    try:
+        return int(vals["traffic_bytes_per_launch"])
+    except (KeyError, ValueError):
+        return None
 
 
 if __name__ == "__main__":
