@@ -48,6 +48,8 @@ extern "C" {
 #define MPM_MAP_RANK     1  /* frequency-rank bins (Section 3.3)                 */
 #define MPM_MAP_GREEDY   2  /* equal-weight bins, greedy (Section 3.3)           */
 #define MPM_MAP_LOWBITS  3  /* low-order bits after a right shift (Section 3.3)  */
+#define MPM_MAP_QHASH    4  /* whole q-grams hashed to sigma_r bins (Section 3.3,
+                               "alphabet mapping on the q-grams")               */
 
 #define MPM_TABLE_AUTO   0
 #define MPM_TABLE_SMEM   1  /* mask table copied to shared memory per block  */
@@ -57,9 +59,14 @@ extern "C" {
  * Filter parameters (Sections 3.2, 3.3).  Zero in q, sigma_r, k, map_kind,
  * table_place or chunk means "choose automatically"; map_shift < 0 means
  * "choose automatically" (0 is a valid shift).
- *   q        q-gram length, 1..16, with q*log2(sigma_r) <= 30 and
+ *   q        q-gram length, 1..16 (1..8 with MPM_MAP_QHASH), with
+ *            q*log2(sigma_r) <= 30 (symbol maps) and
  *            L' = floor((m - q + 1) / q) >= 1.
- *   sigma_r  reduced alphabet size sigma', a power of two in 2..256.
+ *   sigma_r  reduced alphabet size sigma', a power of two in 2..256; with
+ *            MPM_MAP_QHASH the number of q-gram bins, a power of two in
+ *            2..2^24, a q-gram's bin being the top log2(sigma_r) bits of
+ *            raw * 0x9E3779B1 mod 2^32 (q <= 4) or raw * 0x9E3779B97F4A7C15
+ *            mod 2^64 (q <= 8), raw = its q bytes read little-endian.
  *   k        AOSO sampling step: every k-th text q-gram is read; 1..32 and
  *            k <= min(L', 64).
  *   map_kind MPM_MAP_*.
@@ -189,9 +196,10 @@ int mpm_plan(const uint8_t *P, size_t r, size_t m, int sigma, const mpm_params *
 
 /*
  * Builds, on the host only, the tables mpm_build would upload: mu[256] (the
- * byte -> reduced symbol map, Section 3.3) and the Shift-Or mask table
- * (Sections 2, 3.2): entry c (q-gram code, first symbol most significant,
- * c = sum_t mu(S[t]) * sigma_r^(q-1-t)), entry_bytes little-endian bytes,
+ * byte -> reduced symbol map, Section 3.3; the identity with MPM_MAP_QHASH)
+ * and the Shift-Or mask table (Sections 2, 3.2): entry c (q-gram code, first
+ * symbol most significant, c = sum_t mu(S[t]) * sigma_r^(q-1-t); with
+ * MPM_MAP_QHASH the q-gram's bin), entry_bytes little-endian bytes,
  * bit p (p < positions) is 0 iff some pattern, at some shift s < q, has code
  * c as its p-th non-overlapping q-gram; bits >= positions are 1.  table
  * (host memory) must hold table_bytes bytes (mpm_plan); mu or table may be
@@ -260,9 +268,10 @@ typedef struct {
 /*
  * Exhaustive autotuner (not in the paper, which fixes q from log_sigma(rm)
  * and k by a closed form, Section 3.2): every feasible combination of
- * sigma' (powers of two up to the pattern alphabet), mapping (equal-weight
- * greedy bins, and low-order bits where they keep the pattern symbols
- * distinct), q <= max_q and k <= max_k is planned; sets whose estimated
+ * mapping and sigma' (equal-weight greedy bins and, where they keep the
+ * pattern symbols distinct, low-order bits, for sigma' up to the pattern
+ * alphabet; q-gram hashing into 2^10 .. 2^16 bins), q <= max_q and
+ * k <= max_k is planned; sets whose estimated
  * candidate rate exceeds max_rate are dropped, the rest (at most max_sets)
  * are built and timed on the sample T[0..n) (device or host memory) with
  * each kernel selected in opts->kernels.  *best receives the fastest set;

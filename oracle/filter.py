@@ -13,6 +13,9 @@ Steps and where they come from
                                       and q-gram generation": the l low-order
                                       bits of each symbol, and the DNA
                                       multiply trick for a 4-gram.
+  qgram_hash                          Section 3.3, "Alphabet mapping on the
+                                      q-grams": whole q-grams mapped to sigma'
+                                      bins, the mapping given by hashing.
   qgram_code                          Section 3.2 "Implementation": the
                                       numeric value of a q-gram by Horner's
                                       rule.
@@ -112,6 +115,22 @@ def multiply_trick(x):
     return ((((x >> 1) & 0x03030303) * 0x40100401) & 0xFFFFFFFF) >> 24
 
 
+def qgram_hash(raw, bits):
+    """Mapping of a whole q-gram to one of 2^bits bins (Section 3.3, "Alphabet
+    mapping on the q-grams": the q-grams are mapped to 0..sigma'-1 and the
+    mapping is stored by hashing).  Here the bin is the multiplicative
+    (Fibonacci) hash of the q raw bytes read as a little-endian integer:
+    the top `bits` bits of raw * 0x9E3779B1 mod 2^32 for q <= 4, of
+    raw * 0x9E3779B97F4A7C15 mod 2^64 for 5 <= q <= 8."""
+    raw = bytes(raw)
+    q = len(raw)
+    assert 1 <= q <= 8 and 1 <= bits <= 32
+    x = int.from_bytes(raw, "little")
+    if q <= 4:
+        return ((x * 0x9E3779B1) & 0xFFFFFFFF) >> (32 - bits)
+    return ((x * 0x9E3779B97F4A7C15) & 0xFFFFFFFFFFFFFFFF) >> (64 - bits)
+
+
 # ----------------------------------------------------------------- Section 3.2
 
 def qgram_code(symbols, sigma_r, order="lsd"):
@@ -167,11 +186,16 @@ def superimpose(qpatterns):
 # ------------------------------------------------------- the filter's tables
 
 class FilterParams:
-    """q, sigma' (power of two), k and the mapping of one filter instance."""
+    """q, sigma' (power of two), k and the mapping of one filter instance.
 
-    def __init__(self, q, sigma_r, k, mu, order="msd"):
+    With mu, sigma' is the reduced symbol alphabet and a q-gram code has q
+    digits; with qhash=True, sigma' is the number of q-gram bins and a
+    q-gram's code is qgram_hash of its raw bytes."""
+
+    def __init__(self, q, sigma_r, k, mu=None, order="msd", qhash=False):
         self.q, self.sigma_r, self.k = int(q), int(sigma_r), int(k)
-        self.mu = np.asarray(mu, dtype=np.uint8)
+        self.qhash = bool(qhash)
+        self.mu = None if mu is None else np.asarray(mu, dtype=np.uint8)
         self.order = order
 
     def lengths(self, m):
@@ -190,6 +214,11 @@ def pattern_classes(P, fp):
     m = P.shape[1]
     Lc, mp, mpp = fp.lengths(m)
     assert mp >= 1, "infeasible: need floor(min(L',64)/k) >= 1"
+    if fp.qhash:
+        qp = nonoverlapping_qgram_patterns([list(row) for row in P], fp.q, shifts=True, length=Lc)
+        classes = superimpose(qp)[:mpp]
+        bits = log2i(fp.sigma_r)
+        return [set(qgram_hash(g, bits) for g in cls) for cls in classes]
     reduced = [[int(fp.mu[c]) for c in row] for row in P]
     qp = nonoverlapping_qgram_patterns(reduced, fp.q, shifts=True, length=Lc)
     classes = superimpose(qp)[:mpp]
@@ -199,7 +228,7 @@ def pattern_classes(P, fp):
 def mask_table(classes, fp):
     """Shift-Or table over the q-gram alphabet: bit p of B[c] is 0 iff c is
     in Cls[p]; bits >= len(classes) are 0 (they are never tested)."""
-    size = fp.sigma_r ** fp.q
+    size = fp.sigma_r if fp.qhash else fp.sigma_r ** fp.q
     full = (1 << len(classes)) - 1
     B = [full] * size
     for p, cls in enumerate(classes):
@@ -213,6 +242,10 @@ def text_codes(T, fp):
     q-grams (the text factored like the patterns, Section 2)."""
     T = np.asarray(T, dtype=np.uint8)
     nq = T.size // fp.q
+    if fp.qhash:
+        bits = log2i(fp.sigma_r)
+        raw = T[: nq * fp.q].reshape(nq, fp.q)
+        return np.array([qgram_hash(g.tobytes(), bits) for g in raw], dtype=np.int64)
     red = fp.mu[T[: nq * fp.q]].reshape(nq, fp.q).astype(np.int64)
     code = np.zeros(nq, dtype=np.int64)
     cols = range(fp.q) if fp.order == "msd" else range(fp.q - 1, -1, -1)
@@ -288,7 +321,10 @@ def verify(T, P, windows, q):
 
 
 def make_params(P, q, sigma_r, k, map_kind, shift=0, order="msd"):
-    """Convenience: the mapping of `map_kind` ("rank", "greedy", "lowbits")."""
+    """Convenience: the mapping of `map_kind` ("rank", "greedy", "lowbits",
+    "qhash")."""
+    if map_kind == "qhash":
+        return FilterParams(q, sigma_r, k, None, order, qhash=True)
     if map_kind == "rank":
         mu = map_rank(P, sigma_r)
     elif map_kind == "greedy":

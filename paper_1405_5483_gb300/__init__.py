@@ -13,7 +13,7 @@ import ctypes
 import numpy as np
 
 from ._native import (KERNEL_AUTO, KERNEL_GENERIC, KERNEL_SPECIALISED,  # noqa: F401
-                      MAP_AUTO, MAP_GREEDY, MAP_LOWBITS, MAP_RANK, MPM_ECAPACITY, MPM_EINVAL,
+                      MAP_AUTO, MAP_GREEDY, MAP_LOWBITS, MAP_QHASH, MAP_RANK, MPM_ECAPACITY, MPM_EINVAL,
                       MPM_ENOTSUP, MPM_OK, TABLE_AUTO, TABLE_GLOBAL, TABLE_SMEM, MpmError,
                       Params, Stats, TableInfo, declared_functions, lib)
 

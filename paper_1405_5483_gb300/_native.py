@@ -15,7 +15,7 @@ HEADER = os.path.join(os.path.dirname(HERE), "include", "mpm.h")
  MPM_ESCRATCH) = range(8)
 NOALLOC_MAX_CANDIDATES = 1 << 21
 NOALLOC_MAX_OCCURRENCES = 8192
-MAP_AUTO, MAP_RANK, MAP_GREEDY, MAP_LOWBITS = range(4)
+MAP_AUTO, MAP_RANK, MAP_GREEDY, MAP_LOWBITS, MAP_QHASH = range(5)
 TABLE_AUTO, TABLE_SMEM, TABLE_GLOBAL = range(3)
 KERNEL_AUTO, KERNEL_GENERIC, KERNEL_SPECIALISED, KERNEL_SPLIT = range(4)
 

@@ -1,7 +1,7 @@
 // K1: SMAG's separate encoding pass (Section 3.2): the code of every
 // non-overlapping text q-gram, h = 0 .. floor(n/q) - 1, with the byte map mu
 // of Section 3.3 applied to each symbol and the first symbol most
-// significant.  A block stages 1024 q-grams' worth of text (1024 * q bytes)
+// significant (or, with the q-gram hashing map, the bin of its raw bytes).  A block stages 1024 q-grams' worth of text (1024 * q bytes)
 // in shared memory with 16-byte vector loads, then each thread encodes four
 // q-grams and the codes are written coalesced.
 #include "device_common.cuh"
@@ -43,7 +43,13 @@ __global__ void __launch_bounds__(kEncThreads)
         if (h >= nq) break;
         const uint8_t* g = s_txt + (size_t)local * q;
         uint32_t c = 0;
-        for (int t = 0; t < q; t++) c = (c << ell) | s_mu[g[t]];
+        if (f.map_kind == MPM_MAP_QHASH) {
+            uint64_t raw = 0;
+            for (int t = 0; t < q; t++) raw |= (uint64_t)g[t] << (8 * t);
+            c = qgram_bin(raw, q, ell);
+        } else {
+            for (int t = 0; t < q; t++) c = (c << ell) | s_mu[g[t]];
+        }
         codes[h] = c;
     }
 }

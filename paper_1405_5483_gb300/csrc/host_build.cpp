@@ -137,6 +137,63 @@ std::vector<double> class_probabilities(const uint8_t* P, size_t r, size_t m, in
     return pt;
 }
 
+uint64_t raw_qgram(const uint8_t* g, int q) {
+    uint64_t x = 0;
+    for (int u = 0; u < q; u++) x |= (uint64_t)g[u] << (8 * u);
+    return x;
+}
+
+// The same probability for the q-gram hashing map: a text q-gram falls in
+// class t when it is one of the pattern q-grams there, or when it is another
+// q-gram that shares a bin with one of them.  GramStats holds what does not
+// depend on the number of bins.
+struct GramStats {
+    std::vector<std::vector<uint64_t>> grams;  // distinct raw q-grams per position
+    std::vector<double> ptrue;                 // their total probability
+};
+
+GramStats gram_stats(const uint8_t* P, size_t r, size_t m, int q, const uint64_t h[256],
+                     int npos) {
+    double pb[256];
+    const double tot = (double)(r * m);
+    for (int c = 0; c < 256; c++) pb[c] = (double)h[c] / tot;
+    GramStats g;
+    g.grams.resize(npos);
+    g.ptrue.assign(npos, 0.0);
+    for (auto& v : g.grams) v.reserve(r * q);
+    for (size_t i = 0; i < r; i++)
+        for (int s = 0; s < q; s++)
+            for (int t = 0; t < npos; t++) g.grams[t].push_back(raw_qgram(P + i * m + s + t * q, q));
+    for (int t = 0; t < npos; t++) {
+        auto& v = g.grams[t];
+        std::sort(v.begin(), v.end());
+        v.erase(std::unique(v.begin(), v.end()), v.end());
+        double acc = 0.0;
+        for (uint64_t x : v) {
+            double pr = 1.0;
+            for (int u = 0; u < q; u++) pr *= pb[(x >> (8 * u)) & 0xFF];
+            acc += pr;
+        }
+        g.ptrue[t] = std::min(1.0, acc);
+    }
+    return g;
+}
+
+std::vector<double> qhash_class_probabilities(const GramStats& g, int q, int bits) {
+    const int npos = (int)g.grams.size();
+    std::vector<double> pt(npos, 0.0);
+    std::vector<uint32_t> bins;
+    for (int t = 0; t < npos; t++) {
+        bins.clear();
+        for (uint64_t x : g.grams[t]) bins.push_back(qgram_bin(x, q, bits));
+        std::sort(bins.begin(), bins.end());
+        bins.erase(std::unique(bins.begin(), bins.end()), bins.end());
+        const double pcoll = (double)bins.size() / (double)(1ull << bits);
+        pt[t] = std::min(1.0, g.ptrue[t] + pcoll * (1.0 - g.ptrue[t]));
+    }
+    return pt;
+}
+
 // Expected candidate records per sampled q-gram for step k: subpattern j
 // fires when all its m' q-grams fall in their classes.
 double candidate_rate(const std::vector<double>& pt, int k, int mprime) {
@@ -155,9 +212,10 @@ constexpr uint64_t kAutoTableBytes = 64ull << 20;
 
 // Relative cost per text byte of one parameter choice (a planning
 // heuristic; the autotuner replaces it with measurements).
-double plan_cost(bool lowbits, int q, int k, double rate, uint64_t table_bytes) {
+double plan_cost(int kind, int q, int k, double rate, uint64_t table_bytes) {
     const double P = (double)q * k;
-    double alu = (lowbits ? 1.5 : 3.5) + 10.0 / P;
+    const double per_byte = kind == MPM_MAP_QHASH ? 0.5 : (kind == MPM_MAP_LOWBITS ? 1.5 : 3.5);
+    double alu = per_byte + 10.0 / P;
     double scan = std::max(1.0, alu / 4.0);
     double verify = rate / P * q * 48.0;
     double table = table_bytes <= kSmemTableBudget ? 0.0
@@ -173,6 +231,10 @@ void make_mu(const uint8_t* P, size_t r, size_t m, int kind, int sigma_r, int sh
     histogram(P, r, m, h);
     if (kind == MPM_MAP_LOWBITS) {
         for (int c = 0; c < 256; c++) mu[c] = (uint8_t)((c >> shift) & (sigma_r - 1));
+        return;
+    }
+    if (kind == MPM_MAP_QHASH) {  // whole q-grams are hashed; bytes pass as they are
+        for (int c = 0; c < 256; c++) mu[c] = (uint8_t)c;
         return;
     }
     std::fill(mu, mu + 256, (uint8_t)(sigma_r - 1));
@@ -205,13 +267,17 @@ int make_plan(const uint8_t* P, size_t r, size_t m, int sigma, const mpm_params*
         std::memset(&req, 0, sizeof(req));
         req.map_shift = -1;
     }
-    if (req.q < 0 || req.q > 16) return MPM_EINVAL;
-    if (req.sigma_r != 0 &&
+    if (req.map_kind < 0 || req.map_kind > MPM_MAP_QHASH) return MPM_EINVAL;
+    const bool want_qhash = req.map_kind == MPM_MAP_QHASH;
+    if (req.q < 0 || req.q > (want_qhash ? 8 : 16)) return MPM_EINVAL;
+    if (req.sigma_r != 0 && want_qhash &&
+        (!is_pow2(req.sigma_r) || req.sigma_r < 2 || req.sigma_r > (1 << 24)))
+        return MPM_EINVAL;
+    if (req.sigma_r != 0 && !want_qhash &&
         (!is_pow2(req.sigma_r) || req.sigma_r < 2 || req.sigma_r > 256 ||
          req.sigma_r > std::max(2, pow2_ceil(sigma))))
         return MPM_EINVAL;
     if (req.k < 0 || req.k > kMaxK) return MPM_EINVAL;
-    if (req.map_kind < 0 || req.map_kind > MPM_MAP_LOWBITS) return MPM_EINVAL;
     if (req.map_shift > 7) return MPM_EINVAL;
     if (req.table_place < 0 || req.table_place > MPM_TABLE_GLOBAL) return MPM_EINVAL;
     if (req.smag < 0 || req.smag > 1 || req.chunk < 0) return MPM_EINVAL;
@@ -234,6 +300,71 @@ int make_plan(const uint8_t* P, size_t r, size_t m, int sigma, const mpm_params*
     double best_cost = 0.0;
     Plan best;
     std::memset(&best, 0, sizeof(best));
+    // scores every k for one (mapping, sigma', q) given the per-position
+    // class probabilities pt
+    auto consider = [&](int kind, int sr, int ell, int shift, int q, uint64_t entries,
+                        const std::vector<double>& pt, const Lengths& L1) {
+        std::vector<int> ks;
+        if (req.k) {
+            ks.push_back(req.k);
+        } else {
+            for (int k = 1; k <= std::min(L1.Lf, kMaxK); k++) ks.push_back(k);
+        }
+        for (int k : ks) {
+            Lengths Lk = lengths(m, q, k);
+            if (Lk.mprime < 1) continue;
+            const int eb = entry_bytes_for(Lk.positions);
+            const uint64_t tb = entries * (uint64_t)eb;
+            if (tb > kMaxTableBytes) continue;
+            if (!(req.q && req.sigma_r && req.k) && tb > kAutoTableBytes) continue;
+            double rate = candidate_rate(pt, k, Lk.mprime);
+            double cost = plan_cost(kind, q, k, rate, tb);
+            if (!found || cost < best_cost) {
+                found = true;
+                best_cost = cost;
+                best.p = req;
+                best.p.q = q;
+                best.p.sigma_r = sr;
+                best.p.k = k;
+                best.p.map_kind = kind;
+                best.p.map_shift = kind == MPM_MAP_LOWBITS ? shift : 0;
+                best.ell = ell;
+                best.info.L = Lk.L;
+                best.info.mprime = Lk.mprime;
+                best.info.positions = Lk.positions;
+                best.info.entry_bytes = eb;
+                best.info.entries = entries;
+                best.info.table_bytes = tb;
+                best.info.est_candidate_rate = rate;
+            }
+        }
+    };
+    // q-gram hashing: whole q-grams into sigma' bins
+    if (want_qhash || req.map_kind == MPM_MAP_AUTO) {
+        std::vector<int> bins;
+        if (req.sigma_r && want_qhash) {
+            bins.push_back(req.sigma_r);
+        } else if (!req.sigma_r) {
+            for (int b = 10; b <= 16; b++) bins.push_back(1 << b);
+        }
+        std::vector<int> qs;
+        if (req.q) {
+            if (req.q <= 8) qs.push_back(req.q);
+        } else {
+            for (int q = 2; q <= 8; q++) qs.push_back(q);
+        }
+        for (int q : qs) {
+            Lengths L1 = lengths(m, q, 1);
+            if (L1.L < 1) continue;
+            const GramStats g = gram_stats(P, r, m, q, h, L1.Lf);
+            for (int sr : bins) {
+                const int bits = log2_exact(sr);
+                std::vector<double> pt = qhash_class_probabilities(g, q, bits);
+                consider(MPM_MAP_QHASH, sr, bits, 0, q, (uint64_t)sr, pt, L1);
+            }
+        }
+    }
+    if (want_qhash) sigmas.clear();
     for (int sr : sigmas) {
         const int ell = log2_exact(sr);
         // the mapping for this sigma'
@@ -266,40 +397,7 @@ int make_plan(const uint8_t* P, size_t r, size_t m, int sigma, const mpm_params*
             if (!req.q && entries * 8 > kAutoTableBytes * 8 && q * ell > 26) continue;
             std::vector<double> pt =
                 class_probabilities(P, r, m, q, ell, mu, h, L1.Lf);
-            std::vector<int> ks;
-            if (req.k) {
-                ks.push_back(req.k);
-            } else {
-                for (int k = 1; k <= std::min(L1.Lf, kMaxK); k++) ks.push_back(k);
-            }
-            for (int k : ks) {
-                Lengths Lk = lengths(m, q, k);
-                if (Lk.mprime < 1) continue;
-                const int eb = entry_bytes_for(Lk.positions);
-                const uint64_t tb = entries * (uint64_t)eb;
-                if (tb > kMaxTableBytes) continue;
-                if (!(req.q && req.sigma_r && req.k) && tb > kAutoTableBytes) continue;
-                double rate = candidate_rate(pt, k, Lk.mprime);
-                double cost = plan_cost(kind == MPM_MAP_LOWBITS, q, k, rate, tb);
-                if (!found || cost < best_cost) {
-                    found = true;
-                    best_cost = cost;
-                    best.p = req;
-                    best.p.q = q;
-                    best.p.sigma_r = sr;
-                    best.p.k = k;
-                    best.p.map_kind = kind;
-                    best.p.map_shift = kind == MPM_MAP_LOWBITS ? shift : 0;
-                    best.ell = ell;
-                    best.info.L = Lk.L;
-                    best.info.mprime = Lk.mprime;
-                    best.info.positions = Lk.positions;
-                    best.info.entry_bytes = eb;
-                    best.info.entries = entries;
-                    best.info.table_bytes = tb;
-                    best.info.est_candidate_rate = rate;
-                }
-            }
+            consider(kind, sr, ell, shift, q, entries, pt, L1);
         }
     }
     if (!found) return MPM_EINVAL;
@@ -321,6 +419,16 @@ int make_mask_table(const uint8_t* P, const Plan& plan, const uint8_t mu[256],
     const int npos = plan.info.positions;
     const size_t r = plan.r, m = plan.m;
     std::memset(table, 0xFF, plan.info.table_bytes);
+    if (plan.p.map_kind == MPM_MAP_QHASH) {
+        for (size_t i = 0; i < r; i++)
+            for (int s = 0; s < q; s++)
+                for (int t = 0; t < npos; t++) {
+                    const uint32_t c = qgram_bin(raw_qgram(P + i * m + s + t * q, q), q, ell);
+                    uint8_t* e = table + (size_t)c * eb;
+                    e[t >> 3] &= (uint8_t)~(1u << (t & 7));
+                }
+        return MPM_OK;
+    }
     std::vector<uint8_t> red(m);
     for (size_t i = 0; i < r; i++) {
         for (size_t j = 0; j < m; j++) red[j] = mu[P[i * m + j]];

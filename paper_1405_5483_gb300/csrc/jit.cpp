@@ -158,7 +158,7 @@ bool jit_spec(const FilterDev& f, bool verify, JitSpec* out) {
     s.mp = f.mprime;
     s.ell = f.ell;
     s.shift = f.map_kind == MPM_MAP_LOWBITS ? f.shift : 0;
-    s.mode = f.map_kind == MPM_MAP_LOWBITS ? 0 : 1;
+    s.mode = f.map_kind == MPM_MAP_LOWBITS ? 0 : (f.map_kind == MPM_MAP_QHASH ? 2 : 1);
     s.eb = f.entry_bytes;
     s.smem = f.smem_table ? 1 : 0;
     s.table_bytes = f.smem_table ? (int)f.table_bytes : 0;

@@ -19,6 +19,19 @@ inline unsigned long long key_hash(unsigned long long lo, unsigned long long hi)
     return h;
 }
 
+// Bin of a whole q-gram for the q-gram hashing map (MPM_MAP_QHASH): raw is
+// its q (<= 8) bytes read little-endian; the bin is the top `bits` bits of a
+// multiplicative hash, 32-bit for q <= 4 and 64-bit above.
+#if defined(__CUDACC__) || defined(__CUDACC_RTC__)
+__host__ __device__ __forceinline__
+#else
+inline
+#endif
+unsigned int qgram_bin(unsigned long long raw, int q, int bits) {
+    if (q <= 4) return ((unsigned int)raw * 0x9E3779B1u) >> (32 - bits);
+    return (unsigned int)((raw * 0x9E3779B97F4A7C15ull) >> (64 - bits));
+}
+
 // One slot: the patterns whose key is (lo, hi) occupy rows
 // [first, first + count) of the sorted pattern array; count == 0 is empty.
 struct Slot {

@@ -38,7 +38,8 @@ enum ScanMode : int {
     kLow2 = 0,    // low-bit map with 2 bits: the multiply trick of Section 3.3
     kLowG = 1,    // low-bit map, any width
     kLutRed = 2,  // byte map mu on every byte, reduced-symbol window
-    kLutRaw = 3   // raw-byte window, mu on the q bytes of sampled q-grams (q <= 5)
+    kLutRaw = 3,  // raw-byte window, mu on the q bytes of sampled q-grams (q <= 5)
+    kQHash = 4    // raw-byte window, whole q-gram hashed to a bin (q <= 5)
 };
 
 template <int MODE, typename ET>
@@ -65,14 +66,18 @@ struct Stepper {
                          ((uint32_t)smu[(x >> 8) & 0xFFu] << (2 * ell)) |
                          ((uint32_t)smu[(x >> 16) & 0xFFu] << ell) | (uint32_t)smu[x >> 24];
             W = (W << (4 * ell)) | v;
-        } else {
+        } else {  // kLutRaw, kQHash: raw bytes, the newest word on top
             W = (W >> 32) | ((uint64_t)x << 32);
         }
     }
 
     // Code of the q-gram that ends e bytes before the end of the last word.
     __device__ __forceinline__ uint32_t code(int e) const {
-        if (MODE == kLutRaw) {
+        if (MODE == kQHash) {
+            uint64_t raw = W >> (raw_base - 8 * e);
+            if (q < 8) raw &= (1ull << (8 * q)) - 1;
+            return qgram_bin(raw, q, ell);
+        } else if (MODE == kLutRaw) {
             uint64_t raw = W >> (raw_base - 8 * e);
             uint32_t c = 0;
 #pragma unroll
@@ -379,6 +384,7 @@ uint32_t gcd_u(uint32_t a, uint32_t b) {
 uint32_t lcm_u(uint32_t a, uint32_t b) { return a / gcd_u(a, b) * b; }
 
 int scan_mode(const FilterDev& f) {
+    if (f.map_kind == MPM_MAP_QHASH) return kQHash;
     if (f.map_kind == MPM_MAP_LOWBITS) return f.ell == 2 ? kLow2 : kLowG;
     return f.q <= 5 ? kLutRaw : kLutRed;
 }
@@ -463,7 +469,10 @@ int launch_mode(const ScanArgs& A, int num_sms, int chunk, cudaStream_t s) {
 
 int launch_scan(const ScanArgs& A, int num_sms, int chunk, cudaStream_t s) {
     if (A.n == 0) return 0;
+    // the generic kernel's raw window holds q-grams of at most 5 bytes
+    if (A.f.map_kind == MPM_MAP_QHASH && A.f.q > 5) return -2;
     switch (scan_mode(A.f)) {
+        case kQHash: return launch_mode<kQHash>(A, num_sms, chunk, s);
         case kLow2: return launch_mode<kLow2>(A, num_sms, chunk, s);
         case kLowG: return launch_mode<kLowG>(A, num_sms, chunk, s);
         case kLutRed: return launch_mode<kLutRed>(A, num_sms, chunk, s);

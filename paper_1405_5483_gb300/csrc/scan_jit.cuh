@@ -7,7 +7,9 @@
 //   MPM_ELL, MPM_SHIFT reduced symbol width log2(sigma') and, for the
 //                     low-bit map, the right shift applied to each byte
 //   MPM_MODE          0: low-bit map (Section 3.3, combined mapping and
-//                     q-gram generation), 1: byte map mu through a table
+//                     q-gram generation), 1: byte map mu through a table,
+//                     2: whole q-grams hashed to 2^MPM_ELL bins (Section 3.3,
+//                     alphabet mapping on the q-grams)
 //   MPM_EB            bytes per mask-table entry (1, 2, 4, 8)
 //   MPM_SMEM          1: mask table copied to shared memory
 //   MPM_TABLE_BYTES   mask-table bytes (padded to 16)
@@ -108,7 +110,16 @@ __device__ __forceinline__ u32 pack_word(u32 x) {
 // Code of the q-gram at byte offset o of the stage (o constant after
 // unrolling), first symbol most significant.
 __device__ __forceinline__ u32 code_at(const u32* w, const u32* rw, const u8* smu, int o) {
-    if (MPM_MODE == 0) {
+    if (MPM_MODE == 2) {
+        // the q raw bytes at o, little-endian, from at most three words
+        const int first = o >> 2, last = (o + Q - 1) >> 2, sh = 8 * (o & 3);
+        u64 a = w[first];
+        if (first + 1 <= last) a |= (u64)w[first + 1] << 32;
+        u64 raw = a >> sh;
+        if (first + 2 <= last) raw |= (u64)w[first + 2] << (64 - sh);
+        if (Q < 8) raw &= (1ull << (8 * Q)) - 1;
+        return qgram_bin(raw, Q, ELL);
+    } else if (MPM_MODE == 0) {
         const int first = o >> 2, last = (o + Q - 1) >> 2;
         u64 acc = 0;
 #pragma unroll
@@ -224,6 +235,12 @@ __device__ __forceinline__ void emit_stage(FT fm, u32 h0, Emitter& E, const JitS
 
 // The q-gram code of text bytes [st, st + q) read with byte loads.
 __device__ __forceinline__ u32 code_bytes(const u8* T, u32 st, const u8* smu) {
+    if (MPM_MODE == 2) {
+        u64 raw = 0;
+#pragma unroll
+        for (int t = 0; t < Q; t++) raw |= (u64)__ldg(T + st + t) << (8 * t);
+        return qgram_bin(raw, Q, ELL);
+    }
     u32 c = 0;
 #pragma unroll
     for (int t = 0; t < Q; t++) {

@@ -1,4 +1,5 @@
-// Exhaustive autotuner over the filter parameters (sigma', mapping, q, k)
+// Exhaustive autotuner over the filter parameters (sigma', mapping, q, k;
+// the mappings are equal-weight bins, low-order bits and q-gram hashing)
 // and the scan kernel variant: plan every feasible set on the host, drop the
 // sets whose estimated candidate rate is hopeless, compile the remaining
 // specialisations in parallel, then build and time each set on a sample
@@ -109,6 +110,23 @@ extern "C" int mpm_autotune(const uint8_t* P, size_t r, size_t m, int sigma, con
                     cands.push_back(c);
                 }
     }
+    // q-gram hashing: whole q-grams into 2^10 .. 2^16 bins
+    for (int bits = 10; bits <= 16; bits++)
+        for (int q = 1; q <= std::min(max_q, 8); q++)
+            for (int k = 1; k <= max_k; k++) {
+                mpm_params p{};
+                p.q = q;
+                p.sigma_r = 1 << bits;
+                p.k = k;
+                p.map_kind = MPM_MAP_QHASH;
+                Candidate c;
+                if (mpm::make_plan(P, r, m, sigma_eff, &p, &c.plan) != MPM_OK) continue;
+                if (c.plan.info.table_bytes > kTuneMaxTable) continue;
+                if (c.plan.info.est_candidate_rate > max_rate) continue;
+                c.p = c.plan.p;
+                c.key = c.plan.info.est_candidate_rate / (double)(q * k);
+                cands.push_back(c);
+            }
     std::stable_sort(cands.begin(), cands.end(),
                      [](const Candidate& a, const Candidate& b) { return a.key < b.key; });
     if (cands.size() > max_sets) cands.resize(max_sets);

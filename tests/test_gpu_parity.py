@@ -20,7 +20,7 @@ torch = pytest.importorskip("torch")
 from oracle import filter as F  # noqa: E402
 from paper_1405_5483_gb300 import workloads as W  # noqa: E402
 
-KIND = {1: "rank", 2: "greedy", 3: "lowbits"}
+KIND = {1: "rank", 2: "greedy", 3: "lowbits", 4: "qhash"}
 
 
 @pytest.fixture(scope="module")
@@ -98,6 +98,8 @@ ENCODE_CASES = [
     ("protein", dict(q=4, sigma_r=8, k=1, map_kind=1)),
     ("english", dict(q=2, sigma_r=32, k=3, map_kind=2)),
     ("english", dict(q=3, sigma_r=16, k=1, map_kind=3, map_shift=0)),
+    ("protein", dict(q=5, sigma_r=1 << 16, k=1, map_kind=4)),
+    ("english", dict(q=3, sigma_r=1 << 12, k=2, map_kind=4)),
 ]
 
 
@@ -137,8 +139,16 @@ SCAN_CASES = [
     ("english", 16, dict(q=3, sigma_r=4, k=1, map_kind=3, map_shift=7)),     # shift+ell > 8
     ("english", 32, dict(q=2, sigma_r=16, k=2, map_kind=3, map_shift=6)),
     ("protein", 32, dict(q=5, sigma_r=16, k=1, map_kind=2, table_place=2)),  # 1 MB table in L2
+    ("protein", 32, dict(q=4, sigma_r=1 << 16, k=1, map_kind=4)),            # q-gram hashing
+    ("protein", 32, dict(q=5, sigma_r=1 << 12, k=2, map_kind=4)),
+    ("english", 64, dict(q=7, sigma_r=1 << 14, k=3, map_kind=4)),
+    ("dna", 16, dict(q=3, sigma_r=1 << 10, k=1, map_kind=4)),
 ]
 KERNELS = [1, 2, 3]  # generic, specialised (verifies itself), specialised + verify kernel
+
+
+def _generic_unsupported(kw, kernel):
+    return kernel == 1 and kw.get("map_kind") == 4 and kw.get("q", 0) > 5
 
 
 @pytest.mark.parametrize("kernel", KERNELS)
@@ -146,6 +156,11 @@ KERNELS = [1, 2, 3]  # generic, specialised (verifies itself), specialised + ver
 def test_scan_candidates_match_oracle(mpm, kind, mlen, kw, kernel):
     c = _case(kind, 300_007, 60, mlen, 30)
     m = mpm.Matcher(c.P, sigma=c.sigma, kernel=kernel, **kw)
+    if _generic_unsupported(kw, kernel):
+        with pytest.raises(mpm.MpmError) as e:
+            m.scan(dev(c.T))
+        assert e.value.code == mpm.MPM_ENOTSUP
+        return
     p, info = m.params, m.info
     rec = m.scan(dev(c.T))
     torch.cuda.synchronize()
@@ -183,6 +198,12 @@ def test_search_config1_matches_oracle(mpm, native):
 @pytest.mark.parametrize("kind,mlen,kw", SCAN_CASES)
 def test_search_parameter_grid_matches_oracle(mpm, native, kind, mlen, kw, kernel):
     c = _case(kind, 500_003, 80, mlen, 40)
+    if _generic_unsupported(kw, kernel):
+        m = mpm.Matcher(c.P, sigma=c.sigma, kernel=kernel, **kw)
+        with pytest.raises(mpm.MpmError) as e:
+            m.search(dev(c.T))
+        assert e.value.code == mpm.MPM_ENOTSUP
+        return
     check_search(mpm, native, c.T, c.P, c.sigma, kernel=kernel, **kw)
 
 

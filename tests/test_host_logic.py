@@ -55,14 +55,19 @@ def test_auto_plan_dna_uses_low_bits_with_shift_one(mpm):
 
 
 def _oracle_tables(P, p):
-    fp = F.FilterParams(p["q"], p["sigma_r"], p["k"], _oracle_mu(P, p), "msd")
+    fp = _oracle_fp(P, p)
     cls = F.pattern_classes(P, fp)
-    return fp.mu, F.mask_table(cls, fp), len(cls)
+    return _oracle_mu(P, p), F.mask_table(cls, fp), len(cls)
+
+
+def _oracle_fp(P, p):
+    kind = {1: "rank", 2: "greedy", 3: "lowbits", 4: "qhash"}[p["map_kind"]]
+    return F.make_params(P, p["q"], p["sigma_r"], p["k"], kind, shift=p["map_shift"])
 
 
 def _oracle_mu(P, p):
-    kind = {1: "rank", 2: "greedy", 3: "lowbits"}[p["map_kind"]]
-    return F.make_params(P, p["q"], p["sigma_r"], p["k"], kind, shift=p["map_shift"]).mu
+    fp = _oracle_fp(P, p)
+    return fp.mu if fp.mu is not None else np.arange(256, dtype=np.uint8)
 
 
 def _table_positions(table, entry_bytes, positions):
@@ -100,6 +105,27 @@ def test_host_tables_equal_oracle(mpm, seed):
     assert np.array_equal(got, otab.astype(np.uint64)), "mask table differs from the oracle"
 
 
+@pytest.mark.parametrize("seed", range(12))
+def test_host_tables_qgram_hashing_equal_oracle(mpm, seed):
+    rng = np.random.default_rng(300 + seed)
+    sigma = int(rng.choice([4, 20, 95]))
+    r = int(rng.integers(1, 200))
+    m = int(rng.choice([8, 16, 32, 64]))
+    q = int(rng.integers(1, 9))
+    while (m - q + 1) // q < 1:
+        q -= 1
+    Lc = (m - q + 1) // q
+    k = int(rng.integers(1, min(Lc, 32) + 1))
+    bins = int(rng.choice([16, 1024, 4096, 1 << 16]))
+    P = (rng.integers(0, sigma, size=(r, m)) + 33).astype(np.uint8)
+    mu, table, info = mpm.host_tables(P, sigma, q=q, sigma_r=bins, k=k, map_kind=4)
+    p = dict(q=q, sigma_r=bins, k=k, map_kind=4, map_shift=0)
+    omu, otab, npos = _oracle_tables(P, p)
+    assert np.array_equal(mu, omu)
+    got = _table_positions(table, info["entry_bytes"], npos)
+    assert np.array_equal(got, otab.astype(np.uint64))
+
+
 def test_host_tables_auto_params_equal_oracle(mpm):
     from paper_1405_5483_gb300 import workloads as W
     for case in (W.dna_case(1 << 14, 50, 16, 25), W.protein_case(1 << 14, 100, 32, 50),
@@ -123,6 +149,9 @@ JIT_GRID = [
     ("protein", 32, dict(q=5, sigma_r=16, k=1, map_kind=2, table_place=2)),
     ("english", 64, dict(q=7, sigma_r=8, k=2, map_kind=2)),
     ("english", 16, dict(q=3, sigma_r=4, k=1, map_kind=3, map_shift=7)),
+    ("protein", 32, dict(q=4, sigma_r=1 << 16, k=1, map_kind=4)),
+    ("protein", 32, dict(q=6, sigma_r=1 << 14, k=2, map_kind=4)),
+    ("english", 64, dict(q=8, sigma_r=1 << 12, k=3, map_kind=4)),
 ]
 
 

@@ -330,3 +330,58 @@ def test_aho_corasick_threaded_matches_single_thread_on_planted_text(oracle_nati
     pos, pid = oracle_native.naive(T[:20000], P)
     c = ac.search(T[:20000])
     assert np.array_equal(pos, c[0]) and np.array_equal(pid, c[1])
+
+
+# --------------------------------------- Section 3.3, mapping whole q-grams
+
+def test_qgram_hash_bins_are_an_invertible_map_at_full_width():
+    # with as many bins as raw values the multiplicative map must lose
+    # nothing: multiplication by an odd constant is invertible mod 2^32 and
+    # mod 2^64, so every raw q-gram gets its own bin and the raw bytes come
+    # back by multiplying with the inverse
+    rng = random.Random(12)
+    inv32 = pow(0x9E3779B1, -1, 1 << 32)
+    inv64 = pow(0x9E3779B97F4A7C15, -1, 1 << 64)
+    for q in (1, 2, 3, 4):
+        for _ in range(200):
+            raw = bytes(rng.randrange(256) for _ in range(q))
+            h = F.qgram_hash(raw, 32)
+            assert (h * inv32) % (1 << 32) == int.from_bytes(raw, "little")
+    for q in (5, 8):
+        for _ in range(200):
+            raw = bytes(rng.randrange(256) for _ in range(q))
+            h = F.qgram_hash(raw, 32)  # top 32 of 64 bits: check the full product instead
+            full = (int.from_bytes(raw, "little") * 0x9E3779B97F4A7C15) % (1 << 64)
+            assert full >> 32 == h and (full * inv64) % (1 << 64) == int.from_bytes(raw, "little")
+
+
+def test_qgram_hash_spreads_bins_uniformly():
+    # 20 000 distinct 4-grams over a 20-letter alphabet into 2^10 bins: the
+    # bin counts must look uniform (chi-square within 5 sigma of its mean)
+    rng = np.random.default_rng(3)
+    letters = np.frombuffer(b"ACDEFGHIKLMNPQRSTVWY", np.uint8)
+    grams = {bytes(letters[rng.integers(0, 20, 4)]) for _ in range(40000)}
+    grams = list(grams)[:20000]
+    counts = np.bincount([F.qgram_hash(g, 10) for g in grams], minlength=1024)
+    e = len(grams) / 1024
+    chi2 = ((counts - e) ** 2 / e).sum()
+    assert abs(chi2 - 1023) < 5 * np.sqrt(2 * 1023)
+
+
+def test_qhash_filter_equals_definition_and_search_is_exact():
+    rng = np.random.default_rng(13)
+    for _ in range(150):
+        m = int(rng.integers(2, 20))
+        q = int(rng.integers(1, 9))
+        if (m - q + 1) // q < 1:
+            continue
+        Lc = (m - q + 1) // q
+        k = int(rng.integers(1, min(Lc, 4) + 1))
+        T, P = _rand_case(rng, int(rng.integers(1, 5)), int(rng.integers(0, 200)),
+                          int(rng.integers(1, 6)), m, 2)
+        fp = F.make_params(P, q, int(rng.choice([2, 16, 256, 4096])), k, "qhash")
+        cls = F.pattern_classes(P, fp)
+        codes = F.text_codes(T, fp)
+        wins = F.aoso_scan(codes, F.mask_table(cls, fp), fp, len(cls))
+        assert wins == F.candidate_windows_by_definition(codes, cls, fp)
+        assert F.search(T, P, fp) == brute.occurrences(T.tobytes(), [p.tobytes() for p in P])
