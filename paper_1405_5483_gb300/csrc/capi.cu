@@ -218,6 +218,7 @@ int enqueue_filter(mpm_handle* h, const uint8_t* dT, uint32_t n, uint64_t* cand,
         l = mpm::launch_scan(scan_args(h, dT, n, cand, cand_cap, counters), h->num_sms,
                              h->plan.p.chunk, s);
     }
+    if (l == -2) return MPM_ENOTSUP;
     if (l < 0) return MPM_ECUDA;
     *launches += l;
     if (h->timing) cudaEventRecord(h->ev[1], s);
@@ -569,6 +570,7 @@ int mpm_scan(mpm_handle* h, const uint8_t* T, size_t n, uint64_t* cand, size_t* 
                                                h->plan.p.chunk, s)
                         : mpm::launch_scan(a, h->num_sms, h->plan.p.chunk, s);
     }
+    if (l == -2) return set_error(MPM_ENOTSUP);
     if (l < 0) return set_error(MPM_ECUDA);
     if (cudaMemcpyAsync(h->h_counters, h->d_counters, mpm::kNumCounters * 4,
                         cudaMemcpyDeviceToHost, s) != cudaSuccess ||
