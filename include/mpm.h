@@ -78,7 +78,11 @@ extern "C" {
  *   chunk    text bytes one scan thread handles before it moves on, or 0.
  *   kernel   MPM_KERNEL_*: the scan kernel compiled at build time for
  *            these parameters (NVRTC, sm_103a), or the precompiled generic
- *            one; AUTO takes the specialised kernel when it compiles.
+ *            one; AUTO takes the specialised kernel when it compiles.  The
+ *            specialised kernel needs lcm(k*q, 16) <= 256 (an explicit
+ *            request outside that fails with MPM_ENOTSUP); the generic one
+ *            hashes q-grams of at most 5 bytes (MPM_ENOTSUP from the search
+ *            otherwise).
  */
 #define MPM_KERNEL_AUTO        0
 #define MPM_KERNEL_GENERIC     1

@@ -141,7 +141,7 @@ SCAN_CASES = [
     ("protein", 32, dict(q=5, sigma_r=16, k=1, map_kind=2, table_place=2)),  # 1 MB table in L2
     ("protein", 32, dict(q=4, sigma_r=1 << 16, k=1, map_kind=4)),            # q-gram hashing
     ("protein", 32, dict(q=5, sigma_r=1 << 12, k=2, map_kind=4)),
-    ("english", 64, dict(q=7, sigma_r=1 << 14, k=3, map_kind=4)),
+    ("english", 64, dict(q=7, sigma_r=1 << 14, k=2, map_kind=4)),
     ("dna", 16, dict(q=3, sigma_r=1 << 10, k=1, map_kind=4)),
 ]
 KERNELS = [1, 2, 3]  # generic, specialised (verifies itself), specialised + verify kernel
@@ -315,3 +315,17 @@ def test_autotune_picks_a_set_that_is_exact(mpm, native):
     # every timed set found the same occurrences
     assert len({e["z"] for e in ok}) == 1
     check_search(mpm, native, c.T, c.P, 20, **best)
+
+
+def test_specialised_kernel_refuses_periods_it_cannot_stage(mpm):
+    # k*q = 21: a stage holding whole periods would be lcm(21, 16) = 336 bytes
+    c = W.english_case(1 << 14, 40, 64, 20)
+    with pytest.raises(mpm.MpmError) as e:
+        mpm.Matcher(c.P, sigma=95, q=7, sigma_r=1 << 14, k=3, map_kind=4, kernel=2)
+    assert e.value.code == mpm.MPM_ENOTSUP
+    # the automatic kernel choice falls back to the generic kernel, which
+    # cannot hash 7-byte q-grams either: the search reports it
+    m = mpm.Matcher(c.P, sigma=95, q=7, sigma_r=1 << 14, k=3, map_kind=4)
+    with pytest.raises(mpm.MpmError) as e:
+        m.search(dev(c.T))
+    assert e.value.code == mpm.MPM_ENOTSUP
