@@ -165,12 +165,24 @@ bool jit_spec(const FilterDev& f, bool verify, JitSpec* out) {
     const uint32_t P = (uint32_t)(f.k * f.q);
     const uint32_t base = lcm_u(P, 16);
     if (base > 256) return false;
+    // stage rows of at least 80 bytes (48-byte rows measured up to 3x slower
+    // on GB300); odd multiples of base keep C/16 odd, which keeps the 16-byte
+    // shared loads of a quarter warp on distinct banks
     uint32_t C = base;
-    if ((base / 16) % 2 == 1)
-        while (C + 2 * base <= 48) C += 2 * base;  // odd multiples keep C/16 odd
+    while (C < 80 && C + 2 * base <= 256) C += ((base / 16) % 2 == 1) ? 2 * base : base;
+    s.warps = 16;
+    // overrides for tuning the geometry: MPM_JIT_C (stage bytes, a multiple
+    // of lcm(k q, 16) up to 256) and MPM_JIT_WARPS (4..32)
+    if (const char* e = std::getenv("MPM_JIT_C")) {
+        const uint32_t c = (uint32_t)std::atoi(e);
+        if (c >= base && c <= 256 && c % base == 0) C = c;
+    }
+    if (const char* e = std::getenv("MPM_JIT_WARPS")) {
+        const int w = std::atoi(e);
+        if (w >= 4 && w <= 32) s.warps = w;
+    }
     if ((C / P) * (uint32_t)f.k > 64) return false;
     s.C = (int)C;
-    s.warps = C <= 48 ? 32 : 16;
     for (;;) {
         const size_t fixed =
             (size_t)s.table_bytes + 256 + 8 * s.warps * 4 + 8 * s.warps * s.ecap + 128;
