@@ -168,8 +168,10 @@ bool jit_spec(const FilterDev& f, bool verify, JitSpec* out) {
     // stage rows of at least 80 bytes (48-byte rows measured up to 3x slower
     // on GB300); odd multiples of base keep C/16 odd, which keeps the 16-byte
     // shared loads of a quarter warp on distinct banks
+    // (and at most 64 report bits per stage: C / P * k <= 64)
     uint32_t C = base;
-    while (C < 80 && C + 2 * base <= 256) C += ((base / 16) % 2 == 1) ? 2 * base : base;
+    const uint32_t step = ((base / 16) % 2 == 1) ? 2 * base : base;
+    while (C < 80 && C + step <= 256 && (C + step) / P * (uint32_t)f.k <= 64) C += step;
     s.warps = 16;
     // overrides for tuning the geometry: MPM_JIT_C (stage bytes, a multiple
     // of lcm(k q, 16) up to 256) and MPM_JIT_WARPS (4..32)
