@@ -247,6 +247,59 @@ int mpm_encode(mpm_handle *h, const uint8_t *T, size_t n, uint32_t *codes);
 int mpm_scan(mpm_handle *h, const uint8_t *T, size_t n, uint64_t *cand,
              size_t *count);
 
+/* ----------------------------------------------------- batched search */
+
+/*
+ * Many texts, each searched against one of many built pattern sets, in one
+ * persistent kernel launch (not in the paper; its filter per set is the one
+ * of Sections 3.1 and 3.2 with that set's own q, k and mapping).  Texts are
+ * device memory, shorter than 2^24 bytes each, fewer than 2^20 of them;
+ * each set must have at most 32 filter positions, at most 2^20 patterns and,
+ * with MPM_MAP_QHASH, q <= 5 (MPM_ENOTSUP otherwise); all sets on one
+ * device.  The handles and texts must outlive the batch.  Occurrences are
+ * reported as (text index, position, pattern id), sorted in that order.
+ *
+ * mpm_batch_create cuts every text into tiles of up to 32 lanes x lane_bytes
+ * (each lane's share a multiple of its set's k*q), builds per-set device
+ * descriptors (mask tables widened to 32-bit entries) and, unless
+ * opts->no_graph, captures one run -- counter reset, the persistent scan
+ * with in-kernel verification, a radix sort driven by the device-side
+ * count, the split into three arrays and the 16-byte count read-back -- into
+ * a CUDA graph on its own stream.  mpm_batch_run replays it (growing its
+ * buffers and re-capturing when the occurrences outgrow them), waits, and
+ * copies the result into out_tid/out_pos/out_pid (device or host): *z is in:
+ * their capacity, out: the number of occurrences (MPM_ECAPACITY when it
+ * exceeds the capacity).  mpm_search_batch does create, run and free once.
+ */
+typedef struct mpm_batch mpm_batch;
+
+typedef struct {
+    int lane_bytes;  /* text bytes per lane of a tile; 0 = 1024 */
+    int no_graph;    /* 1: launch the kernels on every run instead of a graph */
+} mpm_batch_opts;
+
+typedef struct {
+    uint64_t bytes;       /* text bytes in the batch                        */
+    uint64_t candidates;  /* candidate records of the last run              */
+    uint64_t z;           /* occurrences of the last run                    */
+    uint32_t tiles;       /* tiles in the work list                         */
+    uint32_t launches;    /* kernels per run                                */
+    float ms;             /* device time of the last run (events on the
+                             batch stream around the graph launch)           */
+    float reserved;
+} mpm_batch_stats;
+
+mpm_batch *mpm_batch_create(mpm_handle *const *sets, int nsets, const uint8_t *const *texts,
+                            const size_t *lens, const uint32_t *set_of_text, int ntexts,
+                            const mpm_batch_opts *opts);
+int mpm_batch_run(mpm_batch *b, uint32_t *out_tid, uint32_t *out_pos, uint32_t *out_pid,
+                  size_t *z);
+int mpm_batch_get_stats(const mpm_batch *b, mpm_batch_stats *out);
+void mpm_batch_free(mpm_batch *b);
+int mpm_search_batch(mpm_handle *const *sets, int nsets, const uint8_t *const *texts,
+                     const size_t *lens, const uint32_t *set_of_text, int ntexts,
+                     uint32_t *out_tid, uint32_t *out_pos, uint32_t *out_pid, size_t *z);
+
 /* --------------------------------------------------------- autotuning */
 
 typedef struct {

@@ -233,3 +233,60 @@ class Matcher:
             self.close()
         except Exception:
             pass
+
+
+class Batch:
+    """Many texts (CUDA uint8 tensors), each against one of several Matchers,
+    in one persistent launch replayed from a CUDA graph (mpm_batch_*)."""
+
+    def __init__(self, matchers, texts, set_of_text, lane_bytes=0, graph=True):
+        from ._native import BatchOpts
+        self._keep = (list(matchers), list(texts))
+        n = len(texts)
+        hs = (ctypes.c_void_p * len(matchers))(*[m._h for m in matchers])
+        tp = (ctypes.c_void_p * n)(*[t.data_ptr() for t in texts])
+        ln = (ctypes.c_size_t * n)(*[t.numel() for t in texts])
+        st = (ctypes.c_uint32 * n)(*[int(s) for s in set_of_text])
+        opts = BatchOpts(lane_bytes, 0 if graph else 1)
+        self._b = lib().mpm_batch_create(hs, len(matchers), tp, ln, st, n, ctypes.byref(opts))
+        if not self._b:
+            raise MpmError(lib().mpm_last_error(), "mpm_batch_create")
+        self._cap = 1 << 16
+
+    def run(self):
+        """(text index, position, pattern id) as int32 CUDA tensors, sorted."""
+        torch = _torch()
+        dev = self._keep[1][0].device
+        while True:
+            out = torch.empty(3 * self._cap, dtype=torch.int32, device=dev)
+            z = ctypes.c_size_t(self._cap)
+            rc = lib().mpm_batch_run(self._b, out[: self._cap].data_ptr(),
+                                     out[self._cap: 2 * self._cap].data_ptr(),
+                                     out[2 * self._cap:].data_ptr(), ctypes.byref(z))
+            if rc == MPM_ECAPACITY:
+                self._cap = int(z.value) + 1024
+                continue
+            if rc:
+                raise MpmError(rc, "mpm_batch_run")
+            zz = z.value
+            return out[:zz], out[self._cap: self._cap + zz], out[2 * self._cap: 2 * self._cap + zz]
+
+    @property
+    def stats(self):
+        from ._native import BatchStats
+        s = BatchStats()
+        if lib().mpm_batch_get_stats(self._b, ctypes.byref(s)):
+            raise MpmError(lib().mpm_last_error(), "mpm_batch_get_stats")
+        return s.as_dict()
+
+    def close(self):
+        if getattr(self, "_b", None):
+            lib().mpm_batch_free(self._b)
+            self._b = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+

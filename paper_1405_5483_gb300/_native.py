@@ -66,6 +66,20 @@ class TuneEntry(ctypes.Structure):
                 "candidates": self.candidates, "z": self.z, "status": self.status}
 
 
+class BatchOpts(ctypes.Structure):
+    _fields_ = [("lane_bytes", ctypes.c_int), ("no_graph", ctypes.c_int)]
+
+
+class BatchStats(ctypes.Structure):
+    _fields_ = [("bytes", ctypes.c_uint64), ("candidates", ctypes.c_uint64),
+                ("z", ctypes.c_uint64), ("tiles", ctypes.c_uint32),
+                ("launches", ctypes.c_uint32), ("ms", ctypes.c_float),
+                ("reserved", ctypes.c_float)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
 class MpmError(RuntimeError):
     def __init__(self, code, what=""):
         self.code = code
@@ -109,6 +123,16 @@ def lib():
         "mpm_encode": (ctypes.c_int, [vp, u8p, sz, vp]),
         "mpm_scan": (ctypes.c_int, [vp, u8p, sz, vp, szp]),
         "mpm_search_noalloc": (ctypes.c_int, [vp, u8p, sz, vp, vp, szp]),
+        "mpm_batch_create": (vp, [ctypes.POINTER(vp), ctypes.c_int, ctypes.POINTER(vp),
+                                  ctypes.POINTER(ctypes.c_size_t), ctypes.POINTER(ctypes.c_uint32),
+                                  ctypes.c_int, ctypes.POINTER(BatchOpts)]),
+        "mpm_batch_run": (ctypes.c_int, [vp, vp, vp, vp, szp]),
+        "mpm_batch_get_stats": (ctypes.c_int, [vp, ctypes.POINTER(BatchStats)]),
+        "mpm_batch_free": (None, [vp]),
+        "mpm_search_batch": (ctypes.c_int, [ctypes.POINTER(vp), ctypes.c_int, ctypes.POINTER(vp),
+                                            ctypes.POINTER(ctypes.c_size_t),
+                                            ctypes.POINTER(ctypes.c_uint32), ctypes.c_int,
+                                            vp, vp, vp, szp]),
         "mpm_jit_compile": (ctypes.c_int, [u8p, sz, sz, ctypes.c_int, Pp, ctypes.c_char_p, sz]),
         "mpm_autotune": (ctypes.c_int, [u8p, sz, sz, ctypes.c_int, u8p, sz,
                                         ctypes.POINTER(TuneOpts), Pp, ctypes.POINTER(TuneEntry),

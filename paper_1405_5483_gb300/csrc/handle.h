@@ -1,0 +1,46 @@
+// The state behind an mpm_handle: the resolved plan, the host copies that
+// stay, the device tables, the scratch buffers and the compiled kernels.
+// Shared by the C ABI (capi.cu), the batched search (batch.cu) and the tuner.
+#pragma once
+
+#include "kernels.h"
+
+struct mpm_handle {
+    mpm::Plan plan;
+    mpm::HostTables host;
+    int device = 0;
+    int num_sms = 0;
+    cudaStream_t stream = nullptr;
+
+    uint8_t* d_mu = nullptr;
+    void* d_table = nullptr;
+    uint32_t table_bytes_padded = 0;
+    mpm::Slot* d_slots = nullptr;
+    uint8_t* d_pat = nullptr;
+    uint32_t* d_pid = nullptr;
+
+    // scratch, grown on demand
+    uint64_t* d_cand = nullptr;
+    size_t cand_cap = 0;
+    uint64_t* d_occ = nullptr;
+    uint64_t* d_occ_tmp = nullptr;
+    size_t occ_cap = 0;
+    uint32_t* d_hist = nullptr;
+    size_t hist_cap = 0;
+    uint32_t* d_counters = nullptr;
+    uint32_t* h_counters = nullptr;  // pinned
+    uint8_t* d_text = nullptr;       // staging for host text
+    size_t text_cap = 0;
+    uint32_t* d_codes = nullptr;     // SMAG codes
+    size_t codes_cap = 0;
+    uint32_t* d_out = nullptr;       // staging for host outputs (pos | pid)
+    size_t out_cap = 0;
+
+    mpm_stats stats{};
+    const mpm::JitKernel* jit = nullptr;       // specialised scan that verifies
+    const mpm::JitKernel* jit_cand = nullptr;  // specialised scan, candidates only
+    bool jit_cand_tried = false;
+    int timing = 0;
+    cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};
+};
+

@@ -102,6 +102,16 @@ int launch_scan_jit(const ScanArgs& a, const VerifyArgs* v, const JitKernel* k, 
 // sort, valid while the count is at most kRankSortMax and at most out_cap;
 // otherwise it writes nothing and leaves the outputs to launch_sort_output.
 constexpr uint32_t kRankSortMax = 4096;
+
+// LSD radix sort of keys[0 .. min(*count, cap)) over the 8-bit digits at
+// `shifts`, with the count read on the device and fixed grids, so that it
+// can be captured in a CUDA graph.  tmp holds cap keys, hist
+// sort_dev_hist_entries(cap) entries; *sorted receives keys or tmp,
+// whichever holds the result.
+size_t sort_dev_hist_entries(uint32_t cap);
+int launch_sort_dev(uint64_t* keys, uint64_t* tmp, uint32_t* hist, uint32_t cap,
+                    const uint32_t* count, const int* shifts, int nshifts, int num_sms,
+                    uint64_t** sorted, cudaStream_t s);
 int launch_rank_sort(const uint64_t* keys, const uint32_t* count, uint32_t out_cap,
                      uint32_t* out_pos, uint32_t* out_pid, cudaStream_t s);
 

@@ -171,6 +171,8 @@ __device__ __forceinline__ WindowCtx window_ctx(const JitScanArgs& A) {
     c.pid = A.pid;
     c.occ = A.occ;
     c.occ_count = &A.counters[kOccCountJ];
+    c.tag = 0;
+    c.pos_shift = 32;
     return c;
 }
 

@@ -12,6 +12,7 @@
 // pass is a per-block digit histogram, one exclusive scan over
 // (digit, block), and a stable scatter in which each warp ranks its keys
 // with __match_any_sync, warps and blocks in key order.
+#include <algorithm>
 #include <vector>
 
 #include "device_common.cuh"
@@ -188,7 +189,145 @@ __global__ void split_kernel(const uint64_t* keys, uint32_t z, uint32_t* out_pos
     }
 }
 
+// ---- radix sort with the count on the device (fixed grids: graph-capturable)
+
+constexpr int kDevTile = 4096;
+
+__device__ __forceinline__ uint32_t dev_tiles(const uint32_t* count, uint32_t cap) {
+    const uint32_t z = min(*count, cap);
+    return (z + kDevTile - 1) / kDevTile;
+}
+
+__global__ void __launch_bounds__(kRadixThreads)
+    dev_hist_kernel(const uint64_t* keys, const uint32_t* count, uint32_t cap, int shift,
+                    uint32_t* hist, uint32_t ntmax) {
+    __shared__ uint32_t h[256];
+    const uint32_t z = min(*count, cap);
+    const uint32_t nt = dev_tiles(count, cap);
+    for (uint32_t t = blockIdx.x; t < nt; t += gridDim.x) {
+        for (int i = threadIdx.x; i < 256; i += blockDim.x) h[i] = 0;
+        __syncthreads();
+        const uint32_t a = t * kDevTile, b = min(z, a + kDevTile);
+        for (uint32_t i = a + threadIdx.x; i < b; i += blockDim.x)
+            atomicAdd(&h[(keys[i] >> shift) & 0xFF], 1u);
+        __syncthreads();
+        for (int d = threadIdx.x; d < 256; d += blockDim.x) hist[(size_t)d * ntmax + t] = h[d];
+        __syncthreads();
+    }
+}
+
+// Exclusive prefix sum, in (digit, tile) order, over the tiles in use.
+__global__ void __launch_bounds__(1024)
+    dev_scan_kernel(uint32_t* hist, const uint32_t* count, uint32_t cap, uint32_t ntmax) {
+    __shared__ uint32_t warp_sums[32];
+    __shared__ uint32_t carry;
+    const uint32_t nt = dev_tiles(count, cap);
+    const uint32_t len = 256 * nt;
+    if (threadIdx.x == 0) carry = 0;
+    __syncthreads();
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (uint32_t base = 0; base < len; base += blockDim.x) {
+        const uint32_t f = base + threadIdx.x;
+        const size_t at = f < len ? (size_t)(f / nt) * ntmax + (f % nt) : 0;
+        const uint32_t v = f < len ? hist[at] : 0;
+        uint32_t x = v;
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, x, o);
+            if (lane >= o) x += y;
+        }
+        if (lane == 31) warp_sums[warp] = x;
+        __syncthreads();
+        if (warp == 0) {
+            const int nw = blockDim.x / 32;
+            uint32_t sum = lane < nw ? warp_sums[lane] : 0;
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, sum, o);
+                if (lane >= o) sum += y;
+            }
+            if (lane < nw) warp_sums[lane] = sum;
+        }
+        __syncthreads();
+        const uint32_t before = (warp > 0 ? warp_sums[warp - 1] : 0) + carry;
+        if (f < len) hist[at] = before + x - v;
+        __syncthreads();
+        if (threadIdx.x == blockDim.x - 1) carry = before + x;
+        __syncthreads();
+    }
+}
+
+__global__ void __launch_bounds__(kRadixThreads)
+    dev_scatter_kernel(const uint64_t* in, uint64_t* out, const uint32_t* count, uint32_t cap,
+                       int shift, const uint32_t* offs, uint32_t ntmax) {
+    __shared__ uint32_t cnt[kRadixWarps][256];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const uint32_t z = min(*count, cap);
+    const uint32_t nt = dev_tiles(count, cap);
+    constexpr uint32_t kWarpSpan = kDevTile / kRadixWarps;
+    for (uint32_t t = blockIdx.x; t < nt; t += gridDim.x) {
+        for (int i = threadIdx.x; i < kRadixWarps * 256; i += blockDim.x) (&cnt[0][0])[i] = 0;
+        __syncthreads();
+        const uint32_t a = t * kDevTile + warp * kWarpSpan;
+        const uint32_t b = min(z, a + kWarpSpan);
+        for (uint32_t c = a; c < b; c += 32) {
+            const uint32_t i = c + lane;
+            const bool live = i < b;
+            const uint32_t d = live ? (uint32_t)((in[i] >> shift) & 0xFF) : 256u + lane;
+            const uint32_t peers = __match_any_sync(0xFFFFFFFFu, d);
+            if (live && lane == __ffs(peers) - 1) cnt[warp][d] += __popc(peers);
+            __syncwarp();
+        }
+        __syncthreads();
+        for (int d = threadIdx.x; d < 256; d += blockDim.x) {
+            uint32_t run = offs[(size_t)d * ntmax + t];
+            for (int w = 0; w < kRadixWarps; w++) {
+                const uint32_t c = cnt[w][d];
+                cnt[w][d] = run;
+                run += c;
+            }
+        }
+        __syncthreads();
+        for (uint32_t c = a; c < b; c += 32) {
+            const uint32_t i = c + lane;
+            const bool live = i < b;
+            const uint64_t key = live ? in[i] : 0;
+            const uint32_t d = live ? (uint32_t)((key >> shift) & 0xFF) : 256u + lane;
+            const uint32_t peers = __match_any_sync(0xFFFFFFFFu, d);
+            if (live) out[cnt[warp][d] + __popc(peers & lanemask_lt())] = key;
+            __syncwarp();
+            if (live && lane == __ffs(peers) - 1) cnt[warp][d] += __popc(peers);
+            __syncwarp();
+        }
+        __syncthreads();
+    }
+}
+
 }  // namespace
+
+size_t sort_dev_hist_entries(uint32_t cap) {
+    return 256 * (size_t)((cap + kDevTile - 1) / kDevTile + 1);
+}
+
+int launch_sort_dev(uint64_t* keys, uint64_t* tmp, uint32_t* hist, uint32_t cap,
+                    const uint32_t* count, const int* shifts, int nshifts, int num_sms,
+                    uint64_t** sorted, cudaStream_t s) {
+    const uint32_t ntmax = (cap + kDevTile - 1) / kDevTile + 1;
+    const uint32_t grid = std::min<uint32_t>(ntmax, (uint32_t)num_sms * 4);
+    uint64_t* src = keys;
+    uint64_t* dst = tmp;
+    int launches = 0;
+    for (int p = 0; p < nshifts; p++) {
+        dev_hist_kernel<<<grid, kRadixThreads, 0, s>>>(src, count, cap, shifts[p], hist, ntmax);
+        dev_scan_kernel<<<1, 1024, 0, s>>>(hist, count, cap, ntmax);
+        dev_scatter_kernel<<<grid, kRadixThreads, 0, s>>>(src, dst, count, cap, shifts[p], hist,
+                                                          ntmax);
+        launches += 3;
+        uint64_t* t = src;
+        src = dst;
+        dst = t;
+    }
+    *sorted = src;
+    return cudaPeekAtLastError() == cudaSuccess ? launches : -1;
+}
 
 int launch_rank_sort(const uint64_t* keys, const uint32_t* count, uint32_t out_cap,
                      uint32_t* out_pos, uint32_t* out_pid, cudaStream_t s) {

@@ -34,6 +34,8 @@ __global__ void __launch_bounds__(256) verify_kernel(const VerifyArgs A) {
     wc.pid = A.pid;
     wc.occ = reinterpret_cast<unsigned long long*>(A.occ);
     wc.occ_count = &A.counters[kOccCount];
+    wc.tag = 0;
+    wc.pos_shift = 32;
     for (uint64_t idx = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
          idx += stride) {
         const uint32_t c = (uint32_t)(idx / A.q);

@@ -12,8 +12,10 @@ struct WindowCtx {
     const Slot* slots;
     const unsigned char* pat;     // patterns sorted by bytes, r * m
     const unsigned int* pid;      // pattern id of each sorted row
-    unsigned long long* occ;      // (pos << 32) | pid
+    unsigned long long* occ;      // tag | (pos << pos_shift) | pid
     unsigned int* occ_count;
+    unsigned long long tag;       // 0 for one text; the text id's bits in a batch
+    unsigned int pos_shift;       // 32 for one text; 20 in a batch
 };
 
 // The first key_bytes (<= 16) bytes of T[i..) as two little-endian words.
@@ -58,8 +60,8 @@ __device__ __forceinline__ void window_key(const WindowCtx& c, unsigned int i,
 }
 
 // Looks the window T[i..i+m) up among the pattern groups by its key and
-// appends (i << 32) | pid for every pattern equal to it.
-__device__ __noinline__ void check_window(const WindowCtx& c, unsigned int i) {
+// appends tag | (i << pos_shift) | pid for every pattern equal to it.
+static __device__ __noinline__ void check_window(const WindowCtx& c, unsigned int i) {
     unsigned long long lo, hi;
     window_key(c, i, &lo, &hi);
     unsigned int slot = (unsigned int)key_hash(lo, hi) & c.slot_mask;
@@ -74,7 +76,8 @@ __device__ __noinline__ void check_window(const WindowCtx& c, unsigned int i) {
                 while (u < c.m && __ldg(w + u) == __ldg(p + u)) u++;
                 if (u == c.m) {
                     const unsigned int idx = atomicAdd(c.occ_count, 1u);
-                    if (idx < c.occ_cap) c.occ[idx] = ((unsigned long long)i << 32) | c.pid[row];
+                    if (idx < c.occ_cap)
+                        c.occ[idx] = c.tag | ((unsigned long long)i << c.pos_shift) | c.pid[row];
                 }
             }
             return;
