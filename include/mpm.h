@@ -311,6 +311,9 @@ typedef struct {
                             candidate rate first; 0 = 64                            */
     double max_rate;     /* sets whose estimated candidate records per sampled
                             q-gram exceed this are not timed; 0 = 0.05              */
+    int max_positions;   /* only sets with at most this many filter positions
+                            (32 for mpm_batch); 0 = 64                              */
+    int reserved;
 } mpm_tune_opts;
 
 typedef struct {

@@ -77,12 +77,13 @@ def host_tables(P, sigma, **kw):
     return mu, table, dict(info, **params)
 
 
-def autotune(P, sigma, T, max_q=0, max_k=0, reps=0, kernels=0, max_sets=0, max_rate=0.0):
+def autotune(P, sigma, T, max_q=0, max_k=0, reps=0, kernels=0, max_sets=0, max_rate=0.0,
+             max_positions=0):
     """Exhaustive parameter search timed on the sample text T (CUDA tensor or
     numpy).  Returns (best params dict, list of timed sets)."""
     from ._native import TuneEntry, TuneOpts
     P = _patterns(P)
-    opts = TuneOpts(max_q, max_k, reps, kernels, max_sets, max_rate)
+    opts = TuneOpts(max_q, max_k, reps, kernels, max_sets, max_rate, max_positions, 0)
     cap = 4096
     entries = (TuneEntry * cap)()
     best = Params()

@@ -53,7 +53,8 @@ class Stats(ctypes.Structure):
 class TuneOpts(ctypes.Structure):
     _fields_ = [("max_q", ctypes.c_int), ("max_k", ctypes.c_int), ("reps", ctypes.c_int),
                 ("kernels", ctypes.c_int), ("max_sets", ctypes.c_int),
-                ("max_rate", ctypes.c_double)]
+                ("max_rate", ctypes.c_double), ("max_positions", ctypes.c_int),
+                ("reserved", ctypes.c_int)]
 
 
 class TuneEntry(ctypes.Structure):

@@ -66,6 +66,7 @@ extern "C" int mpm_autotune(const uint8_t* P, size_t r, size_t m, int sigma, con
     const int kernels = o.kernels > 0 ? o.kernels : 1;
     const size_t max_sets = o.max_sets > 0 ? (size_t)o.max_sets : 64;
     const double max_rate = o.max_rate > 0 ? o.max_rate : 0.05;
+    const int max_positions = o.max_positions > 0 ? o.max_positions : 64;
 
     // the pattern alphabet bounds sigma'
     bool seen[256] = {false};
@@ -104,6 +105,7 @@ extern "C" int mpm_autotune(const uint8_t* P, size_t r, size_t m, int sigma, con
                     Candidate c;
                     if (mpm::make_plan(P, r, m, sigma_eff, &p, &c.plan) != MPM_OK) continue;
                     if (c.plan.info.table_bytes > kTuneMaxTable) continue;
+                    if (c.plan.info.positions > max_positions) continue;
                     if (c.plan.info.est_candidate_rate > max_rate) continue;
                     c.p = c.plan.p;
                     c.key = c.plan.info.est_candidate_rate / (double)(q * k);
@@ -122,6 +124,7 @@ extern "C" int mpm_autotune(const uint8_t* P, size_t r, size_t m, int sigma, con
                 Candidate c;
                 if (mpm::make_plan(P, r, m, sigma_eff, &p, &c.plan) != MPM_OK) continue;
                 if (c.plan.info.table_bytes > kTuneMaxTable) continue;
+                if (c.plan.info.positions > max_positions) continue;
                 if (c.plan.info.est_candidate_rate > max_rate) continue;
                 c.p = c.plan.p;
                 c.key = c.plan.info.est_candidate_rate / (double)(q * k);
