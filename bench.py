@@ -222,7 +222,7 @@ def run_batch(args, rank):
         mine = [texts[t] for t in np.flatnonzero(b.set_of_text == sidx)]
         sample = torch.cat(mine)[: 16 << 20] if mine else texts[0]
         try:
-            best, _ = mpm.autotune(P, b.sigma, sample, kernels=4, max_positions=32,
+            best, _ = mpm.autotune(P, b.sigma, sample, kernels=8, max_positions=32,
                                    max_sets=24, reps=2)
         except mpm.MpmError:
             best = {}
@@ -244,11 +244,13 @@ def run_batch(args, rank):
         B.run()
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.nvtx.range_push("batch_timed")
     e0.record()
     for _ in range(args.steps):
         B.run()
     e1.record()
     torch.cuda.synchronize()
+    torch.cuda.nvtx.range_pop()
     batched_ms = e0.elapsed_time(e1) / args.steps
     plain_steps = max(1, min(3, args.steps))
     plain_pass()

@@ -260,8 +260,9 @@ int mpm_scan(mpm_handle *h, const uint8_t *T, size_t n, uint64_t *cand,
  * reported as (text index, position, pattern id), sorted in that order.
  *
  * mpm_batch_create cuts every text into tiles of up to 32 lanes x lane_bytes
- * (each lane's share a multiple of its set's k*q), builds per-set device
- * descriptors (mask tables widened to 32-bit entries) and, unless
+ * (each lane's share a multiple of lcm(k*q, 4) for its set), groups the
+ * tiles of each set into work units, builds per-set device descriptors
+ * (pointing at the handles' tables) and, unless
  * opts->no_graph, captures one run -- counter reset, the persistent scan
  * with in-kernel verification, a radix sort driven by the device-side
  * count, the split into three arrays and the 16-byte count read-back -- into
@@ -274,8 +275,10 @@ int mpm_scan(mpm_handle *h, const uint8_t *T, size_t n, uint64_t *cand,
 typedef struct mpm_batch mpm_batch;
 
 typedef struct {
-    int lane_bytes;  /* text bytes per lane of a tile; 0 = 1024 */
+    int lane_bytes;  /* text bytes per lane of a tile; 0 = 512 */
     int no_graph;    /* 1: launch the kernels on every run instead of a graph */
+    int unit_kib;    /* estimated cost of a work unit, in KiB of scanned text
+                        (verification counted as extra bytes); 0 = 512 */
 } mpm_batch_opts;
 
 typedef struct {
@@ -306,7 +309,10 @@ typedef struct {
     int max_q;           /* largest q tried; 0 = 8                                  */
     int max_k;           /* largest k tried; 0 = 8                                  */
     int reps;            /* timed searches per parameter set (median); 0 = 3       */
-    int kernels;         /* bit 0 specialised, bit 1 split, bit 2 generic; 0 = 1   */
+    int kernels;         /* bit 0 specialised, bit 1 split, bit 2 generic (timed
+                            through mpm_search), bit 3 the batched kernel (one
+                            mpm_batch over the sample, sets of <= 32 positions);
+                            0 = 1                                                  */
     int max_sets;        /* at most this many sets are timed, lowest estimated
                             candidate rate first; 0 = 64                            */
     double max_rate;     /* sets whose estimated candidate records per sampled
@@ -319,7 +325,7 @@ typedef struct {
 typedef struct {
     mpm_params params;   /* resolved parameters of the set                         */
     mpm_table_info info;
-    double ms;           /* median wall time of one mpm_search of the sample       */
+    double ms;           /* median wall time of one search of the sample          */
     uint64_t candidates; /* candidate records of that search                        */
     uint64_t z;          /* occurrences                                             */
     int status;          /* MPM_OK, or why the set could not be built or run       */

@@ -240,7 +240,7 @@ class Batch:
     """Many texts (CUDA uint8 tensors), each against one of several Matchers,
     in one persistent launch replayed from a CUDA graph (mpm_batch_*)."""
 
-    def __init__(self, matchers, texts, set_of_text, lane_bytes=0, graph=True):
+    def __init__(self, matchers, texts, set_of_text, lane_bytes=0, graph=True, unit_kib=0):
         from ._native import BatchOpts
         self._keep = (list(matchers), list(texts))
         n = len(texts)
@@ -248,7 +248,7 @@ class Batch:
         tp = (ctypes.c_void_p * n)(*[t.data_ptr() for t in texts])
         ln = (ctypes.c_size_t * n)(*[t.numel() for t in texts])
         st = (ctypes.c_uint32 * n)(*[int(s) for s in set_of_text])
-        opts = BatchOpts(lane_bytes, 0 if graph else 1)
+        opts = BatchOpts(lane_bytes, 0 if graph else 1, unit_kib)
         self._b = lib().mpm_batch_create(hs, len(matchers), tp, ln, st, n, ctypes.byref(opts))
         if not self._b:
             raise MpmError(lib().mpm_last_error(), "mpm_batch_create")

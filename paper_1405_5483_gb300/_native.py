@@ -68,7 +68,8 @@ class TuneEntry(ctypes.Structure):
 
 
 class BatchOpts(ctypes.Structure):
-    _fields_ = [("lane_bytes", ctypes.c_int), ("no_graph", ctypes.c_int)]
+    _fields_ = [("lane_bytes", ctypes.c_int), ("no_graph", ctypes.c_int),
+                ("unit_kib", ctypes.c_int)]
 
 
 class BatchStats(ctypes.Structure):

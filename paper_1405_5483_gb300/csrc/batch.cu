@@ -3,15 +3,20 @@
 // 3.2 with each set's own q, k and mapping as runtime values).
 //
 // Work list.  Every text is cut into tiles of at most 32 lanes x L bytes,
-// each lane's range a multiple of its set's sampling period k*q from the
-// text start; tiles are listed longest text first.  Warps of a persistent
-// grid pop tiles from a device counter; each lane runs the Shift-Or
-// recurrence over its range (after warming up on the m'-1 sampled q-grams
-// before it), verifies its candidates on the spot against its set's pattern
-// groups, and appends (text << 44) | (pos << 20) | pid.  A radix sort driven
-// by the device count orders the keys; the whole run -- counter reset, scan,
-// sort, split into (text, pos, pid) and the count read-back -- is captured
-// once into a CUDA graph and replayed by every run.
+// each lane's range a multiple of lcm(k*q, 32) from the text start (its
+// set's sampling period, and whole 32-byte sectors).  Consecutive tiles of one
+// pattern set form work units of about equal estimated cost (scan plus
+// verification), handed out most expensive first.
+// Persistent blocks of 32 warps pop units from a device counter; a block
+// loads the unit's mask table into shared memory (at its own entry width,
+// when it fits) and its warps pop the unit's tiles from a shared counter.
+// Each lane runs the Shift-Or recurrence over its range (after warming up
+// on the m'-1 sampled q-grams before it), reading 32 bytes at a time,
+// verifies its candidates on the spot against its set's pattern groups and
+// appends (text << 44) | (pos << 20) | pid.  A radix sort driven by the
+// device count orders the keys; the whole run -- counter reset, scan, sort,
+// split into (text, pos, pid) and the count read-back -- is captured once
+// into a CUDA graph and replayed by every run.
 #include <algorithm>
 #include <cstring>
 #include <new>
@@ -27,14 +32,43 @@ namespace mpm {
 namespace {
 
 struct BatchSet {
-    const uint32_t* table;  // mask table widened to 32-bit entries
+    const void* table;      // mask table (entry_bytes per entry), global memory
     const uint8_t* mu;
     const Slot* slots;
     const uint8_t* pat;
     const uint32_t* pid;
-    uint32_t slot_mask, key_bytes, m, pad;
-    int q, k, mprime, ell, shift, mode, map_kind, pad2;
+    const uint32_t* keys;   // bitmap of key hashes (key_bits bits), or null
+    uint32_t slot_mask, key_bytes, m, table_bytes;  // table_bytes padded to 16
+    int q, k, mprime, ell, shift, mode, map_kind, entry_bytes;
+    uint32_t key_bits, pad;
 };
+
+struct BatchUnit {
+    uint32_t set, tile_begin, tile_end, pad;
+};
+
+constexpr uint32_t kBatchThreads = 1024;
+constexpr uint32_t kBatchSmemTable = 128 * 1024;  // larger tables stay in L2
+constexpr uint32_t kBatchKeyBits = 1u << 19;      // key bitmap of a set, at most
+constexpr uint32_t kBatchSmem = 256 + kBatchSmemTable + kBatchKeyBits / 8;
+
+static __device__ __noinline__ void batch_probe(const WindowCtx& wc, uint32_t i,
+                                                unsigned long long lo, unsigned long long hi,
+                                                unsigned long long h) {
+    probe_window(wc, i, lo, hi, h);
+}
+
+// A window whose key hash misses the set's bitmap (shared memory) matches no
+// pattern; the others are looked up among the pattern groups.
+__device__ __forceinline__ void batch_check(const WindowCtx& wc, const uint32_t* keys,
+                                            uint32_t key_mask, uint32_t i) {
+    unsigned long long lo, hi;
+    window_key(wc, i, &lo, &hi);
+    const unsigned long long h = key_hash(lo, hi);
+    const uint32_t bit = (uint32_t)h & key_mask;
+    if (!((keys[bit >> 5] >> (bit & 31)) & 1u)) return;
+    batch_probe(wc, i, lo, hi, h);
+}
 
 struct BatchText {
     const uint8_t* T;
@@ -51,26 +85,19 @@ constexpr int kPosBits = 24;   // text positions < 2^24 in a batch
 constexpr int kPidBits = 20;   // pattern ids < 2^20 per set
 constexpr int kTextShift = kPosBits + kPidBits;  // 44
 
-__global__ void widen_kernel(const uint8_t* src, int eb, uint32_t entries, uint32_t* dst) {
-    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < entries;
-         i += gridDim.x * blockDim.x) {
-        uint32_t v = 0;
-        for (int b = 0; b < eb && b < 4; b++) v |= (uint32_t)src[(size_t)i * eb + b] << (8 * b);
-        dst[i] = v;
-    }
-}
-
-template <int MODE>
-__device__ void batch_lane(const BatchSet& S, const BatchText& tx, uint32_t a, uint32_t b,
-                           const WindowCtx& wc, uint32_t* counters) {
+template <int MODE, typename ET>
+__device__ void batch_lane(const BatchSet& S, const ET* tab, const uint8_t* smu,
+                           const uint32_t* keys, uint32_t key_mask, const BatchText& tx,
+                           uint32_t a, uint32_t b, const WindowCtx& wc, uint32_t& ncand) {
+    using DT = typename Stepper<MODE, ET>::DT;
     FilterDev f{};
     f.q = S.q;
     f.k = S.k;
     f.ell = S.ell;
     f.shift = S.shift;
     f.map_kind = S.map_kind;
-    Stepper<MODE, uint32_t> sp;
-    sp.init(f, S.table, S.mu);
+    Stepper<MODE, ET> sp;
+    sp.init(f, tab, smu);
     const uint32_t P = (uint32_t)(S.k * S.q);
     const uint32_t Wr = (((uint32_t)(S.mprime - 1) * P) + 3) & ~3u;
     warm_up(sp, tx.T, tx.n, a, Wr, P, true);
@@ -79,77 +106,149 @@ __device__ void batch_lane(const BatchSet& S, const BatchText& tx, uint32_t a, u
     uint32_t hq = a / (uint32_t)S.q + (uint32_t)(S.k - 1);
     int pos = 0, nxt = (int)P;
     const uint32_t words = (b - a + 3) / 4;
-    for (uint32_t w = 0; w < words; w++) {
-        const uint32_t at = a + 4 * w;
-        uint32_t x;
-        if (at + 4 <= tx.n) {
-            x = load_word(tx.T, at);
+    // a is a multiple of 32 from the text start: whole 32-byte sectors, read
+    // as two 16-byte loads that stay in L1 between them
+    const bool vec = (reinterpret_cast<uintptr_t>(tx.T) & 15) == 0;
+    bool done = false;
+    for (uint32_t w0 = 0; w0 < words && !done; w0 += 8) {
+        uint32_t x[8];
+        const uint32_t at0 = a + 4 * w0;
+        if (vec && at0 + 32 <= tx.n) {
+            const uint4 lo = __ldg(reinterpret_cast<const uint4*>(tx.T + at0));
+            const uint4 hi = __ldg(reinterpret_cast<const uint4*>(tx.T + at0 + 16));
+            x[0] = lo.x; x[1] = lo.y; x[2] = lo.z; x[3] = lo.w;
+            x[4] = hi.x; x[5] = hi.y; x[6] = hi.z; x[7] = hi.w;
         } else {
-            x = 0;
-            for (uint32_t u = 0; u < 4 && at + u < tx.n; u++) x |= (uint32_t)tx.T[at + u] << (8 * u);
-        }
-        sp.push(x);
-        pos += 4;
-        while (nxt <= pos && a + (uint32_t)nxt <= b) {
-            const uint32_t c = sp.code(pos - nxt);
-            sp.D = (sp.D << S.k) | sp.tab[c];
-            uint32_t fired = (uint32_t)(~sp.D >> rsh) & kmask;
-            if (fired) {
-                atomicAdd(&counters[kBCand], 1u);
-                while (fired) {
-                    const int j = __ffs((int)fired) - 1;
-                    fired &= fired - 1;
-                    for (int s = 0; s < S.q; s++) {
-                        const int64_t i = ((int64_t)hq - rsh - j) * S.q - s;
-                        if (i < 0 || i + (int64_t)S.m > (int64_t)tx.n) continue;
-                        check_window(wc, (uint32_t)i);
+#pragma unroll
+            for (int u = 0; u < 8; u++) {
+                const uint32_t at = at0 + 4 * u;
+                x[u] = 0;
+                if (w0 + u < words) {
+                    if (at + 4 <= tx.n) {
+                        x[u] = load_word(tx.T, at);
+                    } else {
+                        for (uint32_t v = 0; v < 4 && at + v < tx.n; v++)
+                            x[u] |= (uint32_t)tx.T[at + v] << (8 * v);
                     }
                 }
             }
-            nxt += (int)P;
-            hq += (uint32_t)S.k;
         }
-        if (nxt <= pos) break;
+#pragma unroll
+        for (int u = 0; u < 8; u++) {
+            if (w0 + u >= words || done) break;
+            sp.push(x[u]);
+            pos += 4;
+            while (nxt <= pos && a + (uint32_t)nxt <= b) {
+                const uint32_t c = sp.code(pos - nxt);
+                sp.D = (sp.D << S.k) | (DT)tab[c];
+                uint32_t fired = (uint32_t)(~sp.D >> rsh) & kmask;
+                if (fired) {
+                    ncand++;
+                    while (fired) {
+                        const int j = __ffs((int)fired) - 1;
+                        fired &= fired - 1;
+                        for (int sh = 0; sh < S.q; sh++) {
+                            const int64_t i = ((int64_t)hq - rsh - j) * S.q - sh;
+                            if (i < 0 || i + (int64_t)S.m > (int64_t)tx.n) continue;
+                            batch_check(wc, keys, key_mask, (uint32_t)i);
+                        }
+                    }
+                }
+                nxt += (int)P;
+                hq += (uint32_t)S.k;
+            }
+            if (nxt <= pos) done = true;
+        }
     }
 }
 
-__global__ void __launch_bounds__(256)
+template <int MODE>
+__device__ __forceinline__ void batch_lane_eb(const BatchSet& S, const void* tab,
+                                              const uint8_t* smu, const uint32_t* keys,
+                                              uint32_t key_mask, const BatchText& tx,
+                                              uint32_t a, uint32_t b, const WindowCtx& wc,
+                                              uint32_t& ncand) {
+    switch (S.entry_bytes) {
+        case 1:
+            batch_lane<MODE>(S, (const uint8_t*)tab, smu, keys, key_mask, tx, a, b, wc, ncand);
+            break;
+        case 2:
+            batch_lane<MODE>(S, (const uint16_t*)tab, smu, keys, key_mask, tx, a, b, wc, ncand);
+            break;
+        default:
+            batch_lane<MODE>(S, (const uint32_t*)tab, smu, keys, key_mask, tx, a, b, wc, ncand);
+            break;
+    }
+}
+
+__global__ void __launch_bounds__(kBatchThreads, 1)
     batch_scan_kernel(const BatchSet* sets, const BatchText* texts, const BatchTile* tiles,
-                      uint32_t ntiles, uint64_t* occ, uint32_t occ_cap, uint32_t* counters) {
+                      const BatchUnit* units, uint32_t nunits, uint64_t* occ, uint32_t occ_cap,
+                      uint32_t* counters) {
+    extern __shared__ __align__(16) uint8_t smem[];
+    uint8_t* s_mu = smem;
+    uint8_t* s_tab = smem + 256;
+    uint32_t* s_keys = reinterpret_cast<uint32_t*>(smem + 256 + kBatchSmemTable);
+    __shared__ uint32_t s_unit, s_next;
     const int lane = threadIdx.x & 31;
+    uint32_t ncand = 0;
     for (;;) {
-        uint32_t t = 0;
-        if (lane == 0) t = atomicAdd(&counters[kQueue], 1u);
-        t = __shfl_sync(0xFFFFFFFFu, t, 0);
-        if (t >= ntiles) break;
-        const BatchTile tl = tiles[t];
-        const BatchText tx = texts[tl.text];
-        const BatchSet S = sets[tx.set];
-        WindowCtx wc;
-        wc.T = tx.T;
-        wc.n = tx.n;
-        wc.m = S.m;
-        wc.key_bytes = S.key_bytes;
-        wc.slot_mask = S.slot_mask;
-        wc.occ_cap = occ_cap;
-        wc.slots = S.slots;
-        wc.pat = S.pat;
-        wc.pid = S.pid;
-        wc.occ = reinterpret_cast<unsigned long long*>(occ);
-        wc.occ_count = &counters[kBOcc];
-        wc.tag = (unsigned long long)tl.text << kTextShift;
-        wc.pos_shift = kPidBits;
-        const uint32_t a = tl.start + (uint32_t)lane * tl.sub;
-        const uint32_t b = min(tl.start + tl.len, a + tl.sub);
-        if (a >= b) continue;
-        switch (S.mode) {
-            case kLow2: batch_lane<kLow2>(S, tx, a, b, wc, counters); break;
-            case kLowG: batch_lane<kLowG>(S, tx, a, b, wc, counters); break;
-            case kLutRed: batch_lane<kLutRed>(S, tx, a, b, wc, counters); break;
-            case kLutRaw: batch_lane<kLutRaw>(S, tx, a, b, wc, counters); break;
-            default: batch_lane<kQHash>(S, tx, a, b, wc, counters); break;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            s_unit = atomicAdd(&counters[kQueue], 1u);
+            s_next = 0;
+        }
+        __syncthreads();
+        const uint32_t ui = s_unit;
+        if (ui >= nunits) break;
+        const BatchUnit U = units[ui];
+        const BatchSet S = sets[U.set];
+        const bool in_smem = S.table_bytes <= kBatchSmemTable;
+        for (uint32_t i = threadIdx.x; i < 256; i += blockDim.x) s_mu[i] = S.mu[i];
+        if (in_smem)
+            for (uint32_t i = threadIdx.x; i < S.table_bytes / 16; i += blockDim.x)
+                reinterpret_cast<uint4*>(s_tab)[i] = reinterpret_cast<const uint4*>(S.table)[i];
+        for (uint32_t i = threadIdx.x; i < S.key_bits / 128; i += blockDim.x)
+            reinterpret_cast<uint4*>(s_keys)[i] = reinterpret_cast<const uint4*>(S.keys)[i];
+        const uint32_t kmask = S.key_bits - 1;
+        __syncthreads();
+        const void* tab = in_smem ? (const void*)s_tab : S.table;
+        for (;;) {
+            uint32_t t = 0;
+            if (lane == 0) t = atomicAdd(&s_next, 1u);
+            t = __shfl_sync(0xFFFFFFFFu, t, 0) + U.tile_begin;
+            if (t >= U.tile_end) break;
+            const BatchTile tl = tiles[t];
+            const BatchText tx = texts[tl.text];
+            WindowCtx wc;
+            wc.T = tx.T;
+            wc.n = tx.n;
+            wc.m = S.m;
+            wc.key_bytes = S.key_bytes;
+            wc.slot_mask = S.slot_mask;
+            wc.occ_cap = occ_cap;
+            wc.slots = S.slots;
+            wc.pat = S.pat;
+            wc.pid = S.pid;
+            wc.occ = reinterpret_cast<unsigned long long*>(occ);
+            wc.occ_count = &counters[kBOcc];
+            wc.tag = (unsigned long long)tl.text << kTextShift;
+            wc.pos_shift = kPidBits;
+            const uint32_t a = tl.start + (uint32_t)lane * tl.sub;
+            const uint32_t b = min(tl.start + tl.len, a + tl.sub);
+            if (a >= b) continue;
+            switch (S.mode) {
+                case kLow2: batch_lane_eb<kLow2>(S, tab, s_mu, s_keys, kmask, tx, a, b, wc, ncand); break;
+                case kLowG: batch_lane_eb<kLowG>(S, tab, s_mu, s_keys, kmask, tx, a, b, wc, ncand); break;
+                case kLutRed: batch_lane_eb<kLutRed>(S, tab, s_mu, s_keys, kmask, tx, a, b, wc, ncand); break;
+                case kLutRaw: batch_lane_eb<kLutRaw>(S, tab, s_mu, s_keys, kmask, tx, a, b, wc, ncand); break;
+                default: batch_lane_eb<kQHash>(S, tab, s_mu, s_keys, kmask, tx, a, b, wc, ncand); break;
+            }
         }
     }
+    // one atomic per warp for the candidate count
+    for (int o = 16; o > 0; o >>= 1) ncand += __shfl_xor_sync(0xFFFFFFFFu, ncand, o);
+    if (lane == 0 && ncand) atomicAdd(&counters[kBCand], ncand);
 }
 
 __global__ void batch_split_kernel(const uint64_t* keys, const uint32_t* count, uint32_t cap,
@@ -189,8 +288,9 @@ struct mpm_batch {
     mpm::BatchSet* d_sets = nullptr;
     mpm::BatchText* d_texts = nullptr;
     mpm::BatchTile* d_tiles = nullptr;
-    uint32_t ntiles = 0, ntexts = 0;
-    std::vector<uint32_t*> tables;
+    mpm::BatchUnit* d_units = nullptr;
+    uint32_t* d_keys = nullptr;  // the sets' key bitmaps, one after another
+    uint32_t ntiles = 0, ntexts = 0, nunits = 0;
     uint64_t* d_occ = nullptr;
     uint64_t* d_tmp = nullptr;
     uint32_t* d_hist = nullptr;
@@ -238,7 +338,8 @@ void release_batch(mpm_batch* b) {
     cudaFree(b->d_sets);
     cudaFree(b->d_texts);
     cudaFree(b->d_tiles);
-    for (auto* t : b->tables) cudaFree(t);
+    cudaFree(b->d_units);
+    cudaFree(b->d_keys);
     cudaFree(b->d_counters);
     if (b->h_counters) cudaFreeHost(b->h_counters);
     for (auto& e : b->ev)
@@ -266,9 +367,9 @@ int alloc_buffers(mpm_batch* b, uint32_t cap) {
 int enqueue_batch(mpm_batch* b) {
     cudaStream_t s = b->stream;
     if (cudaMemsetAsync(b->d_counters, 0, 16, s) != cudaSuccess) return MPM_ECUDA;
-    mpm::batch_scan_kernel<<<b->num_sms * 8, 256, 0, s>>>(b->d_sets, b->d_texts, b->d_tiles,
-                                                          b->ntiles, b->d_occ, b->cap,
-                                                          b->d_counters);
+    mpm::batch_scan_kernel<<<b->num_sms, mpm::kBatchThreads, mpm::kBatchSmem, s>>>(
+        b->d_sets, b->d_texts, b->d_tiles, b->d_units, b->nunits, b->d_occ, b->cap,
+        b->d_counters);
     int l = mpm::launch_sort_dev(b->d_occ, b->d_tmp, b->d_hist, b->cap, b->d_counters + mpm::kBOcc,
                                  b->shifts, b->nshifts, b->num_sms, &b->sorted, s);
     if (l < 0) return MPM_ECUDA;
@@ -369,25 +470,26 @@ mpm_batch* mpm_batch_create(mpm_handle* const* sets, int nsets, const uint8_t* c
               cudaEventCreate(&b->ev[0]) == cudaSuccess && cudaEventCreate(&b->ev[1]) == cudaSuccess &&
               cudaMalloc(&b->d_counters, 16) == cudaSuccess &&
               cudaMallocHost(&b->h_counters, 16) == cudaSuccess;
-    // per-set descriptors with tables widened to 32-bit entries
+    // per-set descriptors pointing at the handles' device tables
     std::vector<mpm::BatchSet> hs(nsets);
     for (int i = 0; ok && i < nsets; i++) {
         const mpm_handle* h = sets[i];
-        const uint32_t entries = (uint32_t)h->plan.info.entries;
-        uint32_t* wide = nullptr;
-        ok = cudaMalloc(&wide, (size_t)entries * 4) == cudaSuccess;
-        if (!ok) break;
-        b->tables.push_back(wide);
-        mpm::widen_kernel<<<std::min<uint32_t>((entries + 255) / 256, 4096), 256, 0, b->stream>>>(
-            static_cast<const uint8_t*>(h->d_table), h->plan.info.entry_bytes, entries, wide);
         mpm::BatchSet S{};
-        S.table = wide;
+        S.table = h->d_table;
+        S.table_bytes = h->table_bytes_padded;
+        S.entry_bytes = h->plan.info.entry_bytes;
         S.mu = h->d_mu;
         S.slots = h->d_slots;
         S.pat = h->d_pat;
         S.pid = h->d_pid;
         S.slot_mask = (uint32_t)h->host.slots.size() - 1;
         S.key_bytes = (uint32_t)h->host.key_bytes;
+        // key bitmap: 64 bits per pattern group, 2^10 .. 2^19 bits
+        uint32_t groups = 0;
+        for (const auto& sl : h->host.slots) groups += sl.count ? 1 : 0;
+        uint32_t bits = 1u << 10;
+        while (bits < mpm::kBatchKeyBits && bits < 64ull * groups) bits <<= 1;
+        S.key_bits = bits;
         S.m = (uint32_t)h->plan.m;
         S.q = h->plan.p.q;
         S.k = h->plan.p.k;
@@ -398,44 +500,109 @@ mpm_batch* mpm_batch_create(mpm_handle* const* sets, int nsets, const uint8_t* c
         S.mode = mpm::mode_of(h);
         hs[i] = S;
     }
-    // texts and tiles: per lane a multiple of the set's period, longest first
+    // the key bitmaps, one after another (each a multiple of 16 bytes)
+    if (ok) {
+        size_t words = 0;
+        for (const auto& S : hs) words += S.key_bits / 32;
+        std::vector<uint32_t> bm(words, 0u);
+        size_t at = 0;
+        for (int i = 0; i < nsets; i++) {
+            const uint32_t mask = hs[i].key_bits - 1;
+            for (const auto& sl : sets[i]->host.slots) {
+                if (!sl.count) continue;
+                const uint32_t bit = (uint32_t)mpm::key_hash(sl.lo, sl.hi) & mask;
+                bm[at + bit / 32] |= 1u << (bit % 32);
+            }
+            at += hs[i].key_bits / 32;
+        }
+        ok = cudaMalloc(&b->d_keys, words * 4) == cudaSuccess &&
+             cudaMemcpy(b->d_keys, bm.data(), words * 4, cudaMemcpyHostToDevice) == cudaSuccess;
+        at = 0;
+        for (auto& S : hs) {
+            S.keys = b->d_keys + at;
+            at += S.key_bits / 32;
+        }
+    }
+    // texts and tiles, grouped by set: per lane a multiple of lcm(period, 32)
     std::vector<mpm::BatchText> ht(ntexts);
     std::vector<uint32_t> order(ntexts);
     std::iota(order.begin(), order.end(), 0u);
-    std::stable_sort(order.begin(), order.end(),
-                     [&](uint32_t x, uint32_t y) { return lens[x] > lens[y]; });
+    std::stable_sort(order.begin(), order.end(), [&](uint32_t x, uint32_t y) {
+        if (set_of_text[x] != set_of_text[y]) return set_of_text[x] < set_of_text[y];
+        return lens[x] > lens[y];
+    });
     std::vector<mpm::BatchTile> tiles;
-    const uint32_t lane_bytes = o.lane_bytes > 0 ? (uint32_t)o.lane_bytes : 1024;
+    std::vector<mpm::BatchUnit> units;
+    const uint32_t lane_bytes = o.lane_bytes > 0 ? (uint32_t)o.lane_bytes : 512;
+    const uint64_t unit_bytes = (uint64_t)(o.unit_kib > 0 ? o.unit_kib : 512) << 10;
     uint32_t max_r = 1;
     for (int i = 0; i < nsets; i++) max_r = std::max<uint32_t>(max_r, (uint32_t)sets[i]->plan.r);
     for (int t = 0; t < ntexts; t++) {
         ht[t] = mpm::BatchText{texts[t], (uint32_t)lens[t], set_of_text[t]};
         b->bytes += lens[t];
     }
-    for (uint32_t t : order) {
-        const mpm::BatchSet& S = hs[set_of_text[t]];
+    // Work units: consecutive tiles of one set whose estimated cost reaches
+    // unit_bytes.  A byte costs 1 to scan plus 10 per window it sends to
+    // verification (rate * q * max(1, k * rate) / (k * q) windows per byte),
+    // so verification-heavy sets get short units and short lanes; units are
+    // handed out most expensive first.
+    std::vector<double> unit_cost;
+    for (size_t oi = 0; oi < order.size(); oi++) {
+        const uint32_t t = order[oi];
+        const uint32_t set = set_of_text[t];
+        const mpm::BatchSet& S = hs[set];
         const uint32_t P = (uint32_t)(S.k * S.q);
+        uint32_t G = P;  // lcm(P, 32)
+        while (G % 32) G += P;
         const uint32_t n = (uint32_t)lens[t];
         if (n < S.m) continue;
-        const uint32_t L = std::max<uint32_t>(P, (lane_bytes + P - 1) / P * P);
+        const double rate = std::min(1.0, std::max(0.0, sets[set]->plan.info.est_candidate_rate));
+        const double w = 1.0 + 10.0 * rate * S.q * std::max(1.0, S.k * rate) / P;
+        // at least 64 tiles per unit, lanes no shorter than 2m
+        const double set_unit = (double)unit_bytes / w;
+        uint32_t L = (uint32_t)std::min<double>(lane_bytes, set_unit / (64.0 * 32.0));
+        L = std::max<uint32_t>(L, std::min<uint32_t>(lane_bytes, 2 * S.m));
+        L = std::max<uint32_t>(G, (L + G - 1) / G * G);
         for (uint32_t start = 0; start < n; start += 32 * L) {
             const uint32_t len = std::min<uint32_t>(32 * L, n - start);
             uint32_t sub = (len + 31) / 32;
-            sub = std::max<uint32_t>(P, (sub + P - 1) / P * P);
+            sub = std::max<uint32_t>(G, (sub + G - 1) / G * G);
+            if (units.empty() || units.back().set != set || unit_cost.back() >= (double)unit_bytes) {
+                units.push_back(mpm::BatchUnit{set, (uint32_t)tiles.size(), (uint32_t)tiles.size(), 0});
+                unit_cost.push_back(0.0);
+            }
             tiles.push_back(mpm::BatchTile{t, start, len, sub});
+            units.back().tile_end = (uint32_t)tiles.size();
+            unit_cost.back() += w * len;
         }
     }
+    {
+        std::vector<uint32_t> by_cost(units.size());
+        std::iota(by_cost.begin(), by_cost.end(), 0u);
+        std::stable_sort(by_cost.begin(), by_cost.end(),
+                         [&](uint32_t x, uint32_t y) { return unit_cost[x] > unit_cost[y]; });
+        std::vector<mpm::BatchUnit> sorted;
+        for (uint32_t i : by_cost) sorted.push_back(units[i]);
+        units.swap(sorted);
+    }
     b->ntiles = (uint32_t)tiles.size();
+    b->nunits = (uint32_t)units.size();
     ok = ok && cudaMalloc(&b->d_sets, sizeof(mpm::BatchSet) * nsets) == cudaSuccess &&
          cudaMalloc(&b->d_texts, sizeof(mpm::BatchText) * ntexts) == cudaSuccess &&
          cudaMalloc(&b->d_tiles, sizeof(mpm::BatchTile) * std::max<size_t>(1, tiles.size())) ==
-             cudaSuccess;
+             cudaSuccess &&
+         cudaMalloc(&b->d_units, sizeof(mpm::BatchUnit) * std::max<size_t>(1, units.size())) ==
+             cudaSuccess &&
+         cudaFuncSetAttribute(mpm::batch_scan_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              mpm::kBatchSmem) == cudaSuccess;
     ok = ok &&
          cudaMemcpy(b->d_sets, hs.data(), sizeof(mpm::BatchSet) * nsets, cudaMemcpyHostToDevice) ==
              cudaSuccess &&
          cudaMemcpy(b->d_texts, ht.data(), sizeof(mpm::BatchText) * ntexts,
                     cudaMemcpyHostToDevice) == cudaSuccess &&
          (tiles.empty() || cudaMemcpy(b->d_tiles, tiles.data(), sizeof(mpm::BatchTile) * tiles.size(),
+                                      cudaMemcpyHostToDevice) == cudaSuccess) &&
+         (units.empty() || cudaMemcpy(b->d_units, units.data(), sizeof(mpm::BatchUnit) * units.size(),
                                       cudaMemcpyHostToDevice) == cudaSuccess);
     // digit positions of the keys that can be non-zero
     const int pid_bits = bits_for(max_r - 1 ? max_r - 1 : 1);

@@ -256,7 +256,7 @@ void make_mu(const uint8_t* P, size_t r, size_t m, int kind, int sigma_r, int sh
 }
 
 int make_plan(const uint8_t* P, size_t r, size_t m, int sigma, const mpm_params* in,
-              Plan* out) {
+              Plan* out, std::vector<Plan>* all) {
     if (!P || !out || r == 0 || m == 0 || sigma < 1 || sigma > 256) return MPM_EINVAL;
     if (r >= (1ull << 31) || m >= (1ull << 20) || r * m / m != r || r * m >= (1ull << 40))
         return MPM_EINVAL;
@@ -319,23 +319,37 @@ int make_plan(const uint8_t* P, size_t r, size_t m, int sigma, const mpm_params*
             if (!(req.q && req.sigma_r && req.k) && tb > kAutoTableBytes) continue;
             double rate = candidate_rate(pt, k, Lk.mprime);
             double cost = plan_cost(kind, q, k, rate, tb);
+            Plan cand;
+            std::memset(&cand, 0, sizeof(cand));
+            cand.p = req;
+            cand.p.q = q;
+            cand.p.sigma_r = sr;
+            cand.p.k = k;
+            cand.p.map_kind = kind;
+            cand.p.map_shift = kind == MPM_MAP_LOWBITS ? shift : 0;
+            cand.ell = ell;
+            cand.info.L = Lk.L;
+            cand.info.mprime = Lk.mprime;
+            cand.info.positions = Lk.positions;
+            cand.info.entry_bytes = eb;
+            cand.info.entries = entries;
+            cand.info.table_bytes = tb;
+            cand.info.est_candidate_rate = rate;
+            cand.r = r;
+            cand.m = m;
+            cand.sigma = sigma;
+            if (all) {
+                Plan c2 = cand;
+                if (c2.p.table_place == MPM_TABLE_AUTO)
+                    c2.p.table_place =
+                        tb <= kSmemTableBudget ? MPM_TABLE_SMEM : MPM_TABLE_GLOBAL;
+                if (!(c2.p.table_place == MPM_TABLE_SMEM && tb > kSmemTableBudget))
+                    all->push_back(c2);
+            }
             if (!found || cost < best_cost) {
                 found = true;
                 best_cost = cost;
-                best.p = req;
-                best.p.q = q;
-                best.p.sigma_r = sr;
-                best.p.k = k;
-                best.p.map_kind = kind;
-                best.p.map_shift = kind == MPM_MAP_LOWBITS ? shift : 0;
-                best.ell = ell;
-                best.info.L = Lk.L;
-                best.info.mprime = Lk.mprime;
-                best.info.positions = Lk.positions;
-                best.info.entry_bytes = eb;
-                best.info.entries = entries;
-                best.info.table_bytes = tb;
-                best.info.est_candidate_rate = rate;
+                best = cand;
             }
         }
     };

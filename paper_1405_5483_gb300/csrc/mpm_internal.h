@@ -44,8 +44,10 @@ struct HostTables {
     int key_bytes;                   // min(m, 16)
 };
 
+// all (may be null) receives every plan scored, one per feasible k, when
+// q, sigma' and the mapping are fixed and k is left to choose.
 int make_plan(const uint8_t* P, size_t r, size_t m, int sigma, const mpm_params* in,
-              Plan* out);
+              Plan* out, std::vector<Plan>* all = nullptr);
 void make_mu(const uint8_t* P, size_t r, size_t m, int kind, int sigma_r, int shift,
              uint8_t mu[256]);
 int make_mask_table(const uint8_t* P, const Plan& plan, const uint8_t mu[256],

@@ -81,6 +81,28 @@ extern "C" int mpm_autotune(const uint8_t* P, size_t r, size_t m, int sigma, con
     while (top < distinct && top < 256) top <<= 1;
 
     std::vector<Candidate> cands;
+    // one planning pass per (mapping, sigma', q) scores every k at once
+    auto add_all_k = [&](int kind, int sr, int q) {
+        mpm_params p{};
+        p.q = q;
+        p.sigma_r = sr;
+        p.map_kind = kind;
+        p.map_shift = -1;
+        mpm::Plan best_k;
+        std::vector<mpm::Plan> all;
+        if (mpm::make_plan(P, r, m, sigma_eff, &p, &best_k, &all) != MPM_OK) return;
+        for (const auto& pl : all) {
+            if (pl.p.k > max_k) continue;
+            if (pl.info.table_bytes > kTuneMaxTable) continue;
+            if (pl.info.positions > max_positions) continue;
+            if (pl.info.est_candidate_rate > max_rate) continue;
+            Candidate c;
+            c.plan = pl;
+            c.p = pl.p;
+            c.key = pl.info.est_candidate_rate / (double)(pl.p.q * pl.p.k);
+            cands.push_back(c);
+        }
+    };
     for (int sr = 2; sr <= top; sr <<= 1) {
         // low-order bits only where they keep the pattern symbols apart
         std::vector<int> kinds = {MPM_MAP_GREEDY};
@@ -94,42 +116,11 @@ extern "C" int mpm_autotune(const uint8_t* P, size_t r, size_t m, int sigma, con
                 kinds.push_back(MPM_MAP_LOWBITS);
         }
         for (int kind : kinds)
-            for (int q = 1; q <= max_q; q++)
-                for (int k = 1; k <= max_k; k++) {
-                    mpm_params p{};
-                    p.q = q;
-                    p.sigma_r = sr;
-                    p.k = k;
-                    p.map_kind = kind;
-                    p.map_shift = -1;
-                    Candidate c;
-                    if (mpm::make_plan(P, r, m, sigma_eff, &p, &c.plan) != MPM_OK) continue;
-                    if (c.plan.info.table_bytes > kTuneMaxTable) continue;
-                    if (c.plan.info.positions > max_positions) continue;
-                    if (c.plan.info.est_candidate_rate > max_rate) continue;
-                    c.p = c.plan.p;
-                    c.key = c.plan.info.est_candidate_rate / (double)(q * k);
-                    cands.push_back(c);
-                }
+            for (int q = 1; q <= max_q; q++) add_all_k(kind, sr, q);
     }
     // q-gram hashing: whole q-grams into 2^10 .. 2^16 bins
     for (int bits = 10; bits <= 16; bits++)
-        for (int q = 1; q <= std::min(max_q, 8); q++)
-            for (int k = 1; k <= max_k; k++) {
-                mpm_params p{};
-                p.q = q;
-                p.sigma_r = 1 << bits;
-                p.k = k;
-                p.map_kind = MPM_MAP_QHASH;
-                Candidate c;
-                if (mpm::make_plan(P, r, m, sigma_eff, &p, &c.plan) != MPM_OK) continue;
-                if (c.plan.info.table_bytes > kTuneMaxTable) continue;
-                if (c.plan.info.positions > max_positions) continue;
-                if (c.plan.info.est_candidate_rate > max_rate) continue;
-                c.p = c.plan.p;
-                c.key = c.plan.info.est_candidate_rate / (double)(q * k);
-                cands.push_back(c);
-            }
+        for (int q = 1; q <= std::min(max_q, 8); q++) add_all_k(MPM_MAP_QHASH, 1 << bits, q);
     std::stable_sort(cands.begin(), cands.end(),
                      [](const Candidate& a, const Candidate& b) { return a.key < b.key; });
     if (cands.size() > max_sets) cands.resize(max_sets);
@@ -156,7 +147,7 @@ extern "C" int mpm_autotune(const uint8_t* P, size_t r, size_t m, int sigma, con
     }
     size_t out_cap = 1 << 16;
     uint32_t* d_out = nullptr;
-    if (cudaMalloc(&d_out, 2 * out_cap * sizeof(uint32_t)) != cudaSuccess) {
+    if (cudaMalloc(&d_out, 3 * out_cap * sizeof(uint32_t)) != cudaSuccess) {
         cudaGetLastError();
         cudaFree(own_text);
         return set_error(MPM_ENOMEM);
@@ -165,28 +156,47 @@ extern "C" int mpm_autotune(const uint8_t* P, size_t r, size_t m, int sigma, con
     size_t timed = 0;
     bool have_best = false;
     double best_ms = 0.0;
-    const int modes[3] = {MPM_KERNEL_SPECIALISED, MPM_KERNEL_SPLIT, MPM_KERNEL_GENERIC};
+    // bit 3 times the batched kernel (one text, the sample) with the generic
+    // parameters the batch runs; the others time mpm_search
+    const int modes[4] = {MPM_KERNEL_SPECIALISED, MPM_KERNEL_SPLIT, MPM_KERNEL_GENERIC,
+                          MPM_KERNEL_GENERIC};
     for (const auto& c : cands) {
-        for (int bit = 0; bit < 3; bit++) {
+        for (int bit = 0; bit < 4; bit++) {
             if (!(kernels & (1 << bit))) continue;
             mpm_tune_entry e{};
             e.params = c.p;
             e.params.kernel = modes[bit];
             e.info = c.plan.info;
-            mpm_handle* h = mpm_build(P, r, m, sigma_eff, &e.params);
-            if (!h) {
-                e.status = mpm_last_error();
+            mpm_handle* h = nullptr;
+            mpm_batch* batch = nullptr;
+            if (bit == 3 && c.plan.info.positions > 32) {
+                e.status = MPM_ENOTSUP;
             } else {
+                h = mpm_build(P, r, m, sigma_eff, &e.params);
+                if (!h) e.status = mpm_last_error();
+            }
+            if (h && bit == 3) {
+                const uint8_t* texts[1] = {dT};
+                const size_t lens[1] = {n};
+                const uint32_t sot[1] = {0};
+                mpm_batch_opts bo{};
+                bo.unit_kib = 256;
+                batch = mpm_batch_create(&h, 1, texts, lens, sot, 1, &bo);
+                if (!batch) e.status = mpm_last_error();
+            }
+            if (h && e.status == MPM_OK) {
                 std::vector<double> ms;
                 for (int it = 0; it <= reps && e.status == MPM_OK; it++) {
                     size_t z = out_cap;
                     const auto t0 = std::chrono::steady_clock::now();
-                    int rc = mpm_search(h, dT, n, d_out, d_out + out_cap, &z);
+                    int rc = batch ? mpm_batch_run(batch, d_out, d_out + out_cap,
+                                                   d_out + 2 * out_cap, &z)
+                                   : mpm_search(h, dT, n, d_out, d_out + out_cap, &z);
                     const auto t1 = std::chrono::steady_clock::now();
                     if (rc == MPM_ECAPACITY) {
                         cudaFree(d_out);
                         out_cap = z + 1024;
-                        if (cudaMalloc(&d_out, 2 * out_cap * sizeof(uint32_t)) != cudaSuccess) {
+                        if (cudaMalloc(&d_out, 3 * out_cap * sizeof(uint32_t)) != cudaSuccess) {
                             cudaGetLastError();
                             d_out = nullptr;
                             e.status = MPM_ENOMEM;
@@ -205,18 +215,26 @@ extern "C" int mpm_autotune(const uint8_t* P, size_t r, size_t m, int sigma, con
                 if (e.status == MPM_OK && !ms.empty()) {
                     std::sort(ms.begin(), ms.end());
                     e.ms = ms[ms.size() / 2];
-                    mpm_stats st;
-                    mpm_get_stats(h, &st);
-                    e.candidates = st.candidates;
-                    e.z = st.z;
+                    if (batch) {
+                        mpm_batch_stats bs;
+                        mpm_batch_get_stats(batch, &bs);
+                        e.candidates = bs.candidates;
+                        e.z = bs.z;
+                    } else {
+                        mpm_stats st;
+                        mpm_get_stats(h, &st);
+                        e.candidates = st.candidates;
+                        e.z = st.z;
+                    }
                     if (!have_best || e.ms < best_ms) {
                         have_best = true;
                         best_ms = e.ms;
                         *best = e.params;
                     }
                 }
-                mpm_free(h);
             }
+            mpm_batch_free(batch);
+            mpm_free(h);
             if (entries && timed < cap) entries[timed] = e;
             timed++;
             if (!d_out) break;

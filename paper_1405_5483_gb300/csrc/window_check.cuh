@@ -19,8 +19,8 @@ struct WindowCtx {
 };
 
 // The first key_bytes (<= 16) bytes of T[i..) as two little-endian words.
-// Away from the end of the text: five independent aligned word loads and
-// funnel shifts; near the end: byte loads.
+// Away from the end of the text: three (key of at most 8 bytes) or five
+// independent aligned word loads and funnel shifts; near the end: byte loads.
 __device__ __forceinline__ void window_key(const WindowCtx& c, unsigned int i,
                                            unsigned long long* lo, unsigned long long* hi) {
     const unsigned char* w = c.T + i;
@@ -28,8 +28,9 @@ __device__ __forceinline__ void window_key(const WindowCtx& c, unsigned int i,
         const unsigned long long a = reinterpret_cast<unsigned long long>(w);
         const unsigned int* b = reinterpret_cast<const unsigned int*>(a & ~3ull);
         const unsigned int sh = (unsigned int)(a & 3) * 8;
-        const unsigned int x0 = __ldg(b), x1 = __ldg(b + 1), x2 = __ldg(b + 2),
-                           x3 = __ldg(b + 3), x4 = __ldg(b + 4);
+        const bool wide = c.key_bytes > 8;
+        const unsigned int x0 = __ldg(b), x1 = __ldg(b + 1), x2 = __ldg(b + 2);
+        const unsigned int x3 = wide ? __ldg(b + 3) : 0u, x4 = wide ? __ldg(b + 4) : 0u;
         unsigned long long l = (unsigned long long)__funnelshift_r(x0, x1, sh) |
                                ((unsigned long long)__funnelshift_r(x1, x2, sh) << 32);
         unsigned long long h = (unsigned long long)__funnelshift_r(x2, x3, sh) |
@@ -59,12 +60,13 @@ __device__ __forceinline__ void window_key(const WindowCtx& c, unsigned int i,
     *hi = h;
 }
 
-// Looks the window T[i..i+m) up among the pattern groups by its key and
-// appends tag | (i << pos_shift) | pid for every pattern equal to it.
-static __device__ __noinline__ void check_window(const WindowCtx& c, unsigned int i) {
-    unsigned long long lo, hi;
-    window_key(c, i, &lo, &hi);
-    unsigned int slot = (unsigned int)key_hash(lo, hi) & c.slot_mask;
+// Looks the window T[i..i+m), whose key is (lo, hi) and key hash h, up
+// among the pattern groups and appends tag | (i << pos_shift) | pid for
+// every pattern equal to it.
+static __device__ __forceinline__ void probe_window(const WindowCtx& c, unsigned int i,
+                                                    unsigned long long lo, unsigned long long hi,
+                                                    unsigned long long h) {
+    unsigned int slot = (unsigned int)h & c.slot_mask;
     for (unsigned int probes = 0; probes <= c.slot_mask; probes++) {
         const Slot sl = c.slots[slot];
         if (sl.count == 0) return;
@@ -84,6 +86,13 @@ static __device__ __noinline__ void check_window(const WindowCtx& c, unsigned in
         }
         slot = (slot + 1) & c.slot_mask;
     }
+}
+
+// The window T[i..i+m) checked against the pattern set.
+static __device__ __noinline__ void check_window(const WindowCtx& c, unsigned int i) {
+    unsigned long long lo, hi;
+    window_key(c, i, &lo, &hi);
+    probe_window(c, i, lo, hi, key_hash(lo, hi));
 }
 
 }  // namespace mpm

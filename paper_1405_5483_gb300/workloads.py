@@ -28,7 +28,9 @@ _CHUNK = 1 << 24
 
 
 class Source:
-    """An i.i.d. symbol source: `symbols[i]` with probability `probs[i]`."""
+    """An i.i.d. symbol source: `symbols[i]` with probability `probs[i]`
+    (drawn through a 2^16-slot inverse-CDF table, so each probability is
+    realised to within 2^-16)."""
 
     def __init__(self, symbols, probs):
         self.symbols = np.asarray(symbols, dtype=np.uint8)
@@ -36,6 +38,9 @@ class Source:
         self.probs = p / p.sum()
         self.cdf = np.cumsum(self.probs)
         self.cdf[-1] = 1.0
+        u = (np.arange(1 << 16) + 0.5) / (1 << 16)
+        idx = np.minimum(np.searchsorted(self.cdf, u), self.symbols.size - 1)
+        self._slot = self.symbols[idx]
 
     @property
     def entropy_bits(self):
@@ -48,11 +53,10 @@ class Source:
         for a in range(0, n, _CHUNK):
             b = min(n, a + _CHUNK)
             if uniform:
-                idx = rng.integers(0, self.symbols.size, size=b - a, dtype=np.uint8)
+                out[a:b] = self.symbols[rng.integers(0, self.symbols.size, size=b - a,
+                                                     dtype=np.uint8)]
             else:
-                idx = np.searchsorted(self.cdf, rng.random(b - a)).astype(np.uint8)
-                np.minimum(idx, self.symbols.size - 1, out=idx)
-            out[a:b] = self.symbols[idx]
+                out[a:b] = self._slot[rng.integers(0, 1 << 16, size=b - a, dtype=np.uint16)]
         return out
 
 
