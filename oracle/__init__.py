@@ -8,6 +8,8 @@ CUDA library.
   native   -- C: naive r x n comparison and textbook Aho-Corasick (Section 1.1),
               optionally threaded over contiguous start ranges
   filter   -- the paper's filter steps (Sections 2, 3.1, 3.2, 3.3) in order
+  mlp      -- the learned cost model's network, loss, gradient and Adam
+              update in fp64 (textbook definitions; not from the paper)
 
 Pins (tests/test_oracle_pins.py) tie each part to something outside itself:
 the worked superimposition example and the q = 2 class example of Section 2,
