@@ -311,7 +311,8 @@ typedef struct {
     int reps;            /* timed searches per parameter set (median); 0 = 3       */
     int kernels;         /* bit 0 specialised, bit 1 split, bit 2 generic (timed
                             through mpm_search), bit 3 the batched kernel (one
-                            mpm_batch over the sample, sets of <= 32 positions);
+                            mpm_batch over copies of the sample, at least 128 MiB
+                            and at most 256 copies, sets of <= 32 positions);
                             0 = 1                                                  */
     int max_sets;        /* at most this many sets are timed, lowest estimated
                             candidate rate first; 0 = 64                            */
@@ -319,13 +320,16 @@ typedef struct {
                             q-gram exceed this are not timed; 0 = 0.05              */
     int max_positions;   /* only sets with at most this many filter positions
                             (32 for mpm_batch); 0 = 64                              */
-    int reserved;
+    int grid;            /* 0: the tuner's grid above; 1: every point of the cost
+                            model's grid (mpm_model_grid), nothing dropped          */
 } mpm_tune_opts;
 
 typedef struct {
     mpm_params params;   /* resolved parameters of the set                         */
     mpm_table_info info;
-    double ms;           /* median wall time of one search of the sample          */
+    double ms;           /* median time of one search of the sample: wall time of
+                            mpm_search, or device time of the batched run divided
+                            by the number of copies                               */
     uint64_t candidates; /* candidate records of that search                        */
     uint64_t z;          /* occurrences                                             */
     int status;          /* MPM_OK, or why the set could not be built or run       */
@@ -348,6 +352,90 @@ typedef struct {
 int mpm_autotune(const uint8_t *P, size_t r, size_t m, int sigma, const uint8_t *T, size_t n,
                  const mpm_tune_opts *opts, mpm_params *best, mpm_tune_entry *entries,
                  size_t cap, size_t *count);
+
+/* ------------------------------------------------------ learned cost model */
+
+/*
+ * A small MLP predicts the batched scan's time for one pattern set and one
+ * parameter set, so that parameters can be proposed without timing them
+ * (not in the paper, which fixes q from log_sigma(rm) and k by a closed
+ * form, Section 3.2).  Inputs x = [sigma, entropy of the text in bits per
+ * symbol, log2 m, log10 r, log2 n, q, log2 sigma', k], standardised with a
+ * per-input mean and standard deviation held by the model; 8 -> 64 -> 64 -> 1
+ * with ReLU hidden units, FP32; the output is the standardised natural log of
+ * the time in ms, mapped back with the model's output mean and deviation.
+ * Parameters: one flat FP32 vector of MPM_MODEL_PARAMS numbers, W1 (64 x 8,
+ * row j = hidden unit j), b1 (64), W2 (64 x 64), b2 (64), w3 (64), b3 (1).
+ * Forward, gradient and Adam run in the library's own kernels; training is
+ * deterministic for a given seed.  A model lives on the device that was
+ * current when it first ran a kernel.
+ */
+#define MPM_MODEL_INPUTS 8
+#define MPM_MODEL_HIDDEN 64
+#define MPM_MODEL_PARAMS 4801
+
+typedef struct mpm_model mpm_model;
+
+typedef struct {
+    float lr;            /* Adam step size; 0 = 1e-3                     */
+    float beta1, beta2;  /* 0 = 0.9, 0.999                               */
+    float eps;           /* 0 = 1e-8                                     */
+    int epochs;          /* 0 = 200                                      */
+    int batch;           /* samples per step; 0 = 256                    */
+    uint64_t seed;       /* the order of each epoch is a function of (seed, epoch) */
+} mpm_train_opts;
+
+/* A new model: He-uniform weights from SplitMix64(seed), zero biases, unit
+ * normalisation, a fresh Adam state.  NULL on error.  Host only. */
+mpm_model *mpm_model_create(uint64_t seed);
+void mpm_model_free(mpm_model *model);
+/* Input/output normalisation (8 means, 8 deviations > 0, output mean and
+ * deviation > 0).  Host only. */
+int mpm_model_set_norm(mpm_model *model, const float *in_mean, const float *in_std,
+                       float out_mean, float out_std);
+int mpm_model_get_norm(const mpm_model *model, float *in_mean, float *in_std, float *out_mean,
+                       float *out_std);
+/* Copy the MPM_MODEL_PARAMS parameters out of / into the model (host
+ * arrays); setting them resets the Adam state. */
+int mpm_model_get_params(const mpm_model *model, float *theta);
+int mpm_model_set_params(mpm_model *model, const float *theta);
+/* y[i] = predicted ln(ms) for the raw features X[i*8 .. i*8+8).  X and y
+ * are host or device arrays.  N = 0 is allowed. */
+int mpm_model_predict(mpm_model *model, const float *X, size_t N, float *y);
+/* Mean squared error of the standardised outputs against the standardised
+ * targets y (raw ln(ms)) over all N samples, and its gradient (host array of
+ * MPM_MODEL_PARAMS; may be NULL).  No parameter changes. */
+int mpm_model_loss_grad(mpm_model *model, const float *X, const float *y, size_t N, float *loss,
+                        float *grad);
+/* One Adam step with the given gradient (host array). */
+int mpm_model_adam_step(mpm_model *model, const float *grad, const mpm_train_opts *opts);
+/* Mini-batch Adam on (X, y): opts->epochs passes, each over a permutation of
+ * the samples; epoch_loss (may be NULL) receives each epoch's mean loss. */
+int mpm_model_train(mpm_model *model, const float *X, const float *y, size_t N,
+                    const mpm_train_opts *opts, float *epoch_loss);
+/* Checkpoint: parameters, normalisation and Adam state (little-endian
+ * binary).  Host only. */
+int mpm_model_save(const mpm_model *model, const char *path);
+mpm_model *mpm_model_load(const char *path);
+/* The feasible points of the model's parameter grid for a pattern set: q in
+ * 2..6 with sigma' in {2, 4, 8, 16} (the planner's mapping for that sigma'),
+ * q in 2..5 with q-gram hashing into 2^12, 2^14 or 2^16 bins, every feasible
+ * k <= 8, tables of at most 16 MiB and at most max_positions filter positions
+ * (0 = 64).  *count receives the number of points; up to cap of them are
+ * written to out (and info, which may be NULL).  Host only. */
+int mpm_model_grid(const uint8_t *P, size_t r, size_t m, int sigma, int max_positions,
+                   mpm_params *out, mpm_table_info *info, size_t cap, size_t *count);
+/* Raw model inputs for `count` parameter sets of one pattern set (r patterns
+ * of length m, declared alphabet sigma) searched in texts of n bytes whose
+ * symbol entropy is `entropy` bits: X[i*8 ..] = [sigma, entropy, log2 m,
+ * log10 r, log2 n, q, log2 sigma', k].  Host only. */
+int mpm_model_features(int sigma, double entropy, size_t m, size_t r, size_t n,
+                       const mpm_params *params, size_t count, float *X);
+/* The grid point (at most 32 positions: the batched kernel's limit) with the
+ * smallest predicted time for a pattern set searched in texts of n bytes
+ * whose symbol entropy is `entropy` bits.  *pred receives its ln(ms). */
+int mpm_model_choose(mpm_model *model, const uint8_t *P, size_t r, size_t m, int sigma,
+                     double entropy, size_t n, mpm_params *best, float *pred);
 
 /* ------------------------------------------- search that allocates nothing */
 

@@ -54,7 +54,16 @@ class TuneOpts(ctypes.Structure):
     _fields_ = [("max_q", ctypes.c_int), ("max_k", ctypes.c_int), ("reps", ctypes.c_int),
                 ("kernels", ctypes.c_int), ("max_sets", ctypes.c_int),
                 ("max_rate", ctypes.c_double), ("max_positions", ctypes.c_int),
-                ("reserved", ctypes.c_int)]
+                ("grid", ctypes.c_int)]
+
+
+MODEL_INPUTS, MODEL_HIDDEN, MODEL_PARAMS = 8, 64, 4801
+
+
+class TrainOpts(ctypes.Structure):
+    _fields_ = [("lr", ctypes.c_float), ("beta1", ctypes.c_float), ("beta2", ctypes.c_float),
+                ("eps", ctypes.c_float), ("epochs", ctypes.c_int), ("batch", ctypes.c_int),
+                ("seed", ctypes.c_uint64)]
 
 
 class TuneEntry(ctypes.Structure):
@@ -110,6 +119,7 @@ def lib():
     vp, sz, u8p = ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p
     Pp, Ip, Sp = ctypes.POINTER(Params), ctypes.POINTER(TableInfo), ctypes.POINTER(Stats)
     szp = ctypes.POINTER(ctypes.c_size_t)
+    fp = ctypes.POINTER(ctypes.c_float)
     sig = {
         "mpm_build": (vp, [u8p, sz, sz, ctypes.c_int, Pp]),
         "mpm_search": (ctypes.c_int, [vp, u8p, sz, vp, vp, szp]),
@@ -139,6 +149,24 @@ def lib():
         "mpm_autotune": (ctypes.c_int, [u8p, sz, sz, ctypes.c_int, u8p, sz,
                                         ctypes.POINTER(TuneOpts), Pp, ctypes.POINTER(TuneEntry),
                                         sz, szp]),
+        "mpm_model_create": (vp, [ctypes.c_uint64]),
+        "mpm_model_free": (None, [vp]),
+        "mpm_model_set_norm": (ctypes.c_int, [vp, fp, fp, ctypes.c_float, ctypes.c_float]),
+        "mpm_model_get_norm": (ctypes.c_int, [vp, fp, fp, fp, fp]),
+        "mpm_model_get_params": (ctypes.c_int, [vp, fp]),
+        "mpm_model_set_params": (ctypes.c_int, [vp, fp]),
+        "mpm_model_predict": (ctypes.c_int, [vp, vp, sz, vp]),
+        "mpm_model_loss_grad": (ctypes.c_int, [vp, vp, vp, sz, fp, fp]),
+        "mpm_model_adam_step": (ctypes.c_int, [vp, fp, ctypes.POINTER(TrainOpts)]),
+        "mpm_model_train": (ctypes.c_int, [vp, vp, vp, sz, ctypes.POINTER(TrainOpts), fp]),
+        "mpm_model_save": (ctypes.c_int, [vp, ctypes.c_char_p]),
+        "mpm_model_load": (vp, [ctypes.c_char_p]),
+        "mpm_model_grid": (ctypes.c_int, [u8p, sz, sz, ctypes.c_int, ctypes.c_int, Pp, Ip, sz,
+                                          szp]),
+        "mpm_model_features": (ctypes.c_int, [ctypes.c_int, ctypes.c_double, sz, sz, sz, Pp, sz,
+                                              fp]),
+        "mpm_model_choose": (ctypes.c_int, [vp, u8p, sz, sz, ctypes.c_int, ctypes.c_double, sz,
+                                            Pp, fp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(L, name)

@@ -19,7 +19,7 @@ OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "libmpm.so")
 
 SOURCES = ["host_build.cpp", "capi.cu", "scan.cu", "encode.cu", "verify.cu", "sort.cu", "jit.cpp",
-           "tune.cpp", "batch.cu"]
+           "tune.cpp", "batch.cu", "mlp.cu"]
 # files concatenated, in this order, into the source of the scan kernel that
 # is compiled at run time
 JIT_PARTS = ["keyhash.h", "scan_jit_args.h", "ptx_common.cuh", "window_check.cuh",

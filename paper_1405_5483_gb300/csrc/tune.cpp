@@ -53,6 +53,37 @@ constexpr uint64_t kTuneMaxTable = 16ull << 20;
 
 }  // namespace
 
+namespace {
+
+// The cost model's parameter grid: q in 2..6 with sigma' in {2, 4, 8, 16}
+// (the mapping the planner picks for that sigma'), and q in 2..5 with q-gram
+// hashing into 2^12, 2^14 or 2^16 bins; every feasible k <= 8.
+void model_grid(const uint8_t* P, size_t r, size_t m, int sigma, int max_positions,
+                std::vector<mpm::Plan>* plans) {
+    const int maxpos = max_positions > 0 ? max_positions : 64;
+    auto add = [&](int kind, int sr, int q) {
+        mpm_params p{};
+        p.q = q;
+        p.sigma_r = sr;
+        p.map_kind = kind;
+        p.map_shift = -1;
+        mpm::Plan best_k;
+        std::vector<mpm::Plan> all;
+        if (mpm::make_plan(P, r, m, sigma, &p, &best_k, &all) != MPM_OK) return;
+        for (const auto& pl : all) {
+            if (pl.p.k > 8 || pl.info.positions > maxpos || pl.info.table_bytes > kTuneMaxTable)
+                continue;
+            plans->push_back(pl);
+        }
+    };
+    for (int q = 2; q <= 6; q++)
+        for (int sr = 2; sr <= 16; sr <<= 1) add(MPM_MAP_AUTO, sr, q);
+    for (int q = 2; q <= 5; q++)
+        for (int bits = 12; bits <= 16; bits += 2) add(MPM_MAP_QHASH, 1 << bits, q);
+}
+
+}  // namespace
+
 extern "C" int mpm_autotune(const uint8_t* P, size_t r, size_t m, int sigma, const uint8_t* T,
                             size_t n, const mpm_tune_opts* opts, mpm_params* best,
                             mpm_tune_entry* entries, size_t cap, size_t* count) {
@@ -81,6 +112,19 @@ extern "C" int mpm_autotune(const uint8_t* P, size_t r, size_t m, int sigma, con
     while (top < distinct && top < 256) top <<= 1;
 
     std::vector<Candidate> cands;
+    if (o.grid < 0 || o.grid > 1) return set_error(MPM_EINVAL);
+    if (o.grid == 1) {
+        // exactly the cost model's grid (max_q, max_k, max_sets and max_rate unused)
+        std::vector<mpm::Plan> plans;
+        model_grid(P, r, m, sigma_eff, max_positions, &plans);
+        for (const auto& pl : plans) {
+            Candidate c;
+            c.plan = pl;
+            c.p = pl.p;
+            c.key = 0.0;
+            cands.push_back(c);
+        }
+    }
     // one planning pass per (mapping, sigma', q) scores every k at once
     auto add_all_k = [&](int kind, int sr, int q) {
         mpm_params p{};
@@ -103,7 +147,7 @@ extern "C" int mpm_autotune(const uint8_t* P, size_t r, size_t m, int sigma, con
             cands.push_back(c);
         }
     };
-    for (int sr = 2; sr <= top; sr <<= 1) {
+    for (int sr = 2; o.grid == 0 && sr <= top; sr <<= 1) {
         // low-order bits only where they keep the pattern symbols apart
         std::vector<int> kinds = {MPM_MAP_GREEDY};
         {
@@ -119,11 +163,13 @@ extern "C" int mpm_autotune(const uint8_t* P, size_t r, size_t m, int sigma, con
             for (int q = 1; q <= max_q; q++) add_all_k(kind, sr, q);
     }
     // q-gram hashing: whole q-grams into 2^10 .. 2^16 bins
-    for (int bits = 10; bits <= 16; bits++)
+    for (int bits = 10; o.grid == 0 && bits <= 16; bits++)
         for (int q = 1; q <= std::min(max_q, 8); q++) add_all_k(MPM_MAP_QHASH, 1 << bits, q);
-    std::stable_sort(cands.begin(), cands.end(),
-                     [](const Candidate& a, const Candidate& b) { return a.key < b.key; });
-    if (cands.size() > max_sets) cands.resize(max_sets);
+    if (o.grid == 0) {
+        std::stable_sort(cands.begin(), cands.end(),
+                         [](const Candidate& a, const Candidate& b) { return a.key < b.key; });
+        if (cands.size() > max_sets) cands.resize(max_sets);
+    }
     if (cands.empty()) return set_error(MPM_EINVAL);
 
     // compile every specialisation up front, in parallel
@@ -153,6 +199,9 @@ extern "C" int mpm_autotune(const uint8_t* P, size_t r, size_t m, int sigma, con
         return set_error(MPM_ENOMEM);
     }
 
+    // batched timing: at least 128 MiB scanned per run (at most 256 copies)
+    const size_t copies =
+        n == 0 ? 1 : std::min<size_t>(256, std::max<size_t>(1, ((128ull << 20) + n - 1) / n));
     size_t timed = 0;
     bool have_best = false;
     double best_ms = 0.0;
@@ -176,12 +225,12 @@ extern "C" int mpm_autotune(const uint8_t* P, size_t r, size_t m, int sigma, con
                 if (!h) e.status = mpm_last_error();
             }
             if (h && bit == 3) {
-                const uint8_t* texts[1] = {dT};
-                const size_t lens[1] = {n};
-                const uint32_t sot[1] = {0};
-                mpm_batch_opts bo{};
-                bo.unit_kib = 256;
-                batch = mpm_batch_create(&h, 1, texts, lens, sot, 1, &bo);
+                // the sample repeated until the batch keeps the whole GPU busy
+                const std::vector<const uint8_t*> texts(copies, dT);
+                const std::vector<size_t> lens(copies, n);
+                const std::vector<uint32_t> sot(copies, 0u);
+                batch = mpm_batch_create(&h, 1, texts.data(), lens.data(), sot.data(),
+                                         (int)copies, nullptr);
                 if (!batch) e.status = mpm_last_error();
             }
             if (h && e.status == MPM_OK) {
@@ -209,8 +258,16 @@ extern "C" int mpm_autotune(const uint8_t* P, size_t r, size_t m, int sigma, con
                         e.status = rc;
                         break;
                     }
-                    if (it > 0)  // the first search warms up
-                        ms.push_back(std::chrono::duration<double, std::milli>(t1 - t0).count());
+                    if (it > 0) {  // the first search warms up
+                        if (batch) {
+                            // device time of the run (events around the graph), per copy
+                            mpm_batch_stats bs;
+                            mpm_batch_get_stats(batch, &bs);
+                            ms.push_back((double)bs.ms / (double)copies);
+                        } else {
+                            ms.push_back(std::chrono::duration<double, std::milli>(t1 - t0).count());
+                        }
+                    }
                 }
                 if (e.status == MPM_OK && !ms.empty()) {
                     std::sort(ms.begin(), ms.end());
@@ -245,4 +302,19 @@ extern "C" int mpm_autotune(const uint8_t* P, size_t r, size_t m, int sigma, con
     cudaFree(own_text);
     *count = timed;
     return set_error(have_best ? MPM_OK : MPM_EINVAL);
+}
+
+
+extern "C" int mpm_model_grid(const uint8_t* P, size_t r, size_t m, int sigma, int max_positions,
+                              mpm_params* out, mpm_table_info* info, size_t cap, size_t* count) {
+    if (!P || !count || r == 0 || m == 0 || sigma < 1 || sigma > 256 || (cap > 0 && !out))
+        return set_error(MPM_EINVAL);
+    std::vector<mpm::Plan> plans;
+    model_grid(P, r, m, sigma, max_positions, &plans);
+    for (size_t i = 0; i < plans.size() && i < cap; i++) {
+        out[i] = plans[i].p;
+        if (info) info[i] = plans[i].info;
+    }
+    *count = plans.size();
+    return set_error(MPM_OK);
 }

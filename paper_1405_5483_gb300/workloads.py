@@ -207,6 +207,23 @@ def config4(ntexts=4096, nsets=64, min_log2=10, max_log2=22, cfg=4):
     return Batch(texts, sets, set_of_text)
 
 
+def config5_set(index, cfg=5):
+    """Pattern set `index` of the cost model's data, config-4-shaped: one text
+    of n bytes, n log-uniform over [2^20, 2^23] (95 printable symbols, Zipf
+    s = 1.0); r log-uniform over [10, 10^4]; m uniform over {8, 16, 32, 64};
+    half of the patterns planted from the text.  Seeds (1000 + cfg, index)
+    for the text and (2000 + cfg, index) for the patterns."""
+    src = english_source()
+    rng_t = np.random.default_rng([1000 + cfg, index])
+    rng_p = np.random.default_rng([2000 + cfg, index])
+    n = int(math.exp(rng_t.uniform(20 * math.log(2), 23 * math.log(2))))
+    T = src.draw(n, rng_t)
+    r = int(round(math.exp(rng_p.uniform(math.log(10), math.log(10_000)))))
+    m = int(rng_p.choice([8, 16, 32, 64]))
+    P, offs = make_patterns(T, src, r, m, r // 2, rng_p)
+    return Case("set %d n=%d r=%d m=%d" % (index, n, r, m), T, P, 95, offs, src)
+
+
 def random_case(rng, sigma, n, r, m, planted=0, base=97):
     """A small random case over `sigma` symbols starting at byte `base`."""
     T = (rng.integers(0, sigma, size=n) + base).astype(np.uint8)
