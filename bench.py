@@ -364,7 +364,7 @@ def main():
     tuning = None
     params = {}
     if args.params:
-        params = json.loads(args.params)
+        params = parse_params(args.params)
     elif not args.no_tune:
         # exhaustive autotuner on a sample of the text; not timed, like the build
         sample = T[: min(case.n, args.tune_sample_mib << 20)]
@@ -470,6 +470,18 @@ def main():
         dist.destroy_process_group()
 
 
+def parse_params(text):
+    """Filter parameters from JSON or from a list like q=5,sigma_r=65536,k=1."""
+    text = text.strip()
+    if text.startswith("{"):
+        return json.loads(text)
+    out = {}
+    for item in filter(None, text.split(",")):
+        k, v = item.split("=", 1)
+        out[k.strip()] = int(v)
+    return out
+
+
 def kernel_rev():
     """A hash of the specialised scan kernel's source and launch geometry, to
     tie DRAM counters recorded under profiles/ to the code that made them."""
@@ -484,27 +496,34 @@ def kernel_rev():
 
 def recorded_traffic(workload, params):
     """DRAM bytes per launch of the scan kernel from the ncu summary of this
-    workload, when it was taken on the current kernel with these parameters."""
+    workload, when it was taken on the current kernel with these parameters.
+    The summary lists `kernel_rev` once and one `record` line (JSON with
+    params and traffic_bytes_per_launch) per captured parameter set."""
     path = os.path.join(ROOT, "profiles", "mpm_scan_jit_%s.md" % workload)
     if not os.path.exists(path):
         return None
-    vals = {}
+    rev, records = None, []
     for line in open(path):
-        if ":" in line and line.startswith("- `"):
-            k, v = line[3:].split("`", 1)
-            vals[k.strip()] = v.split(":", 1)[1].strip().strip("`")
-    if vals.get("kernel_rev") != kernel_rev():
+        if not line.startswith("- `"):
+            continue
+        key, rest = line[3:].split("`", 1)
+        val = rest.split(":", 1)[1].strip().strip("`") if ":" in rest else ""
+        if key == "kernel_rev":
+            rev = val
+        elif key == "record":
+            try:
+                records.append(json.loads(val))
+            except ValueError:
+                pass
+    if rev != kernel_rev():
         return None
-    try:
-        rec = json.loads(vals.get("params", "{}"))
-    except ValueError:
-        return None
-    if any(params.get(k) != v for k, v in rec.items()):
-        return None
-    try:
-        return int(vals["traffic_bytes_per_launch"])
-    except (KeyError, ValueError):
-        return None
+    for rec in records:
+        if all(params.get(k) == v for k, v in rec.get("params", {}).items()):
+            try:
+                return int(rec["traffic_bytes_per_launch"])
+            except (KeyError, ValueError, TypeError):
+                return None
+    return None
 
 
 if __name__ == "__main__":
