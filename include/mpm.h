@@ -179,7 +179,8 @@ int mpm_set_stream(mpm_handle *h, void *stream);
  * sizes that follow from them; info may be NULL. */
 int mpm_get_params(const mpm_handle *h, mpm_params *out, mpm_table_info *info);
 
-/* Counters of the last search or scan on this handle. */
+/* Counters of the last search or scan on this handle (for pipelined
+ * searches: the sums since mpm_reset_stats, complete after mpm_sync). */
 int mpm_get_stats(const mpm_handle *h, mpm_stats *out);
 
 /* on != 0: mpm_search records CUDA events around its scan and verification
@@ -187,6 +188,31 @@ int mpm_get_stats(const mpm_handle *h, mpm_stats *out);
  * mpm_stats (read after the search's own count read-back, so no extra
  * synchronisation).  Off by default. */
 int mpm_set_timing(mpm_handle *h, int on);
+
+/*
+ * Pipelined search: enqueues the whole search of T[0..n) (scan, verification
+ * and the sort of up to 4096 occurrences) on the handle's stream and returns
+ * without waiting, so successive searches keep the GPU busy.  T, out_pos and
+ * out_pid (cap entries each) are device pointers; status points to 4
+ * uint32 in device memory or in mapped host memory (cudaHostAlloc with
+ * cudaHostAllocMapped).  When the stream reaches the end of the call:
+ * status[0] = candidate records, status[1] = z, status[2] = 0 or the error
+ * of the device work (MPM_ETIMEOUT), status[3] = 1 when out_pos/out_pid hold
+ * all z occurrences sorted by (pos, pid); status[3] = 0 when they could not
+ * (z > cap, z > 4096, an internal buffer too small, or an error): then run
+ * mpm_search for this text, which grows what it needs.  Calls on one handle
+ * run in stream order and share its buffers; outputs of a call are
+ * overwritten by later calls that use the same arrays.  Host-side argument
+ * errors return MPM_EINVAL; nothing is enqueued then.  With timing on, each
+ * call's scan and verification times are added to the statistics.
+ */
+int mpm_search_async(mpm_handle *h, const uint8_t *T, size_t n, uint32_t *out_pos,
+                     uint32_t *out_pid, size_t cap, uint32_t *status);
+/* Waits until the handle's stream is idle and completes the statistics of
+ * pipelined searches. */
+int mpm_sync(mpm_handle *h);
+/* Clears the statistics (waiting for timed pipelined searches in flight). */
+int mpm_reset_stats(mpm_handle *h);
 
 /* ---------------------------------------------- host-only planning calls */
 

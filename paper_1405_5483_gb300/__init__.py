@@ -156,11 +156,15 @@ class Matcher:
             raise MpmError(rc, what)
 
     def _stream(self, T):
-        if hasattr(T, "is_cuda") and T.is_cuda:
-            torch = _torch()
-            lib().mpm_set_stream(self._h, ctypes.c_void_p(torch.cuda.current_stream().cuda_stream))
+        # the current PyTorch stream for device texts, the default stream
+        # otherwise; the library is told only when it changes
+        if getattr(T, "is_cuda", False):
+            cur = _torch().cuda.current_stream().cuda_stream
         else:
-            lib().mpm_set_stream(self._h, None)
+            cur = None
+        if cur != getattr(self, "_cur_stream", 0):
+            lib().mpm_set_stream(self._h, ctypes.c_void_p(cur) if cur else None)
+            self._cur_stream = cur
 
     # ------------------------------------------------------------ search
     def search_into(self, T, out_pos, out_pid):
@@ -176,6 +180,23 @@ class Matcher:
             e.z = z.value
             raise e
         return z.value
+
+    def search_async(self, T, out_pos, out_pid, status):
+        """Enqueues the search of device text T on the current stream without
+        waiting (mpm_search_async); status is a 4-entry int32 CUDA tensor (or
+        mapped host memory) that receives [candidates, z, error, complete]."""
+        self._stream(T)
+        rc = lib().mpm_search_async(self._h, _ptr(T), _numel(T), _ptr(out_pos), _ptr(out_pid),
+                                    min(_numel(out_pos), _numel(out_pid)), _ptr(status))
+        if rc:
+            raise MpmError(rc, "mpm_search_async")
+
+    def sync(self):
+        """Waits for the handle's stream (mpm_sync)."""
+        self._check(lib().mpm_sync(self._h), "mpm_sync")
+
+    def reset_stats(self):
+        self._check(lib().mpm_reset_stats(self._h), "mpm_reset_stats")
 
     def search(self, T):
         """All occurrences in T as (pos, pid), 32-bit, sorted by (pos, pid).

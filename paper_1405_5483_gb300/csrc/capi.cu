@@ -85,6 +85,10 @@ void release(mpm_handle* h) {
     cudaFree(h->d_hist);
     cudaFree(h->d_counters);
     if (h->h_counters) cudaFreeHost(h->h_counters);
+    if (h->h_snap) cudaFreeHost(h->h_snap);
+    for (auto& trio : h->ring)
+        for (auto& e : trio)
+            if (e) cudaEventDestroy(e);
     cudaFree(h->d_text);
     cudaFree(h->d_codes);
     cudaFree(h->d_out);
@@ -146,13 +150,17 @@ bool fused_search(const mpm_handle* h) { return h->jit && !h->plan.p.smag; }
 // records (generic and SMAG paths only) to cand.
 int enqueue_filter(mpm_handle* h, const uint8_t* dT, uint32_t n, uint64_t* cand,
                    uint32_t cand_cap, uint64_t* occ, uint32_t occ_cap, uint32_t* counters,
-                   int* launches) {
+                   int* launches, bool reset = true, cudaEvent_t* events = nullptr) {
+    // events: three events recorded before the scan, between scan and
+    // verification and after verification; the handle's when timing is on
+    cudaEvent_t* ev = events ? events : (h->timing ? h->ev : nullptr);
     cudaStream_t s = h->stream;
     const mpm::FilterDev f = filter_dev(h);
-    if (cudaMemsetAsync(counters, 0, mpm::kNumCounters * sizeof(uint32_t), s) != cudaSuccess)
+    if (reset &&
+        cudaMemsetAsync(counters, 0, mpm::kNumCounters * sizeof(uint32_t), s) != cudaSuccess)
         return MPM_ECUDA;
     const mpm::VerifyArgs v = verify_args(h, dT, n, cand, cand_cap, occ, occ_cap, counters);
-    if (h->timing) cudaEventRecord(h->ev[0], s);
+    if (ev) cudaEventRecord(ev[0], s);
     int l;
     if (h->plan.p.smag) {
         const size_t nq = n / (uint32_t)f.q;
@@ -166,9 +174,9 @@ int enqueue_filter(mpm_handle* h, const uint8_t* dT, uint32_t n, uint64_t* cand,
                                  h->num_sms, h->plan.p.chunk, s);
         if (l < 0) return MPM_ECUDA;
         *launches += l;
-        if (h->timing) {
-            cudaEventRecord(h->ev[1], s);
-            cudaEventRecord(h->ev[2], s);
+        if (ev) {
+            cudaEventRecord(ev[1], s);
+            cudaEventRecord(ev[2], s);
         }
         return MPM_OK;
     } else if (h->jit_cand) {
@@ -182,10 +190,10 @@ int enqueue_filter(mpm_handle* h, const uint8_t* dT, uint32_t n, uint64_t* cand,
     if (l == -2) return MPM_ENOTSUP;
     if (l < 0) return MPM_ECUDA;
     *launches += l;
-    if (h->timing) cudaEventRecord(h->ev[1], s);
+    if (ev) cudaEventRecord(ev[1], s);
     if (mpm::launch_verify(v, h->num_sms, s) < 0) return MPM_ECUDA;
     *launches += 1;
-    if (h->timing) cudaEventRecord(h->ev[2], s);
+    if (ev) cudaEventRecord(ev[2], s);
     return MPM_OK;
 }
 
@@ -196,6 +204,89 @@ int read_counters(mpm_handle* h, const uint32_t* counters) {
                         cudaMemcpyDeviceToHost, s) != cudaSuccess)
         return MPM_ECUDA;
     if (cudaStreamSynchronize(s) != cudaSuccess) return MPM_ECUDA;
+    if (h->h_counters[mpm::kErrorFlag]) return (int)h->h_counters[mpm::kErrorFlag];
+    if (h->timing) {
+        float a = 0.f, b = 0.f;
+        cudaEventElapsedTime(&a, h->ev[0], h->ev[1]);
+        cudaEventElapsedTime(&b, h->ev[1], h->ev[2]);
+        h->stats.ms_scan += a;
+        h->stats.ms_verify += b;
+    }
+    return MPM_OK;
+}
+
+// The device address of a status block: device memory as is, mapped host
+// memory through its device alias; null for anything else.
+uint32_t* device_address(uint32_t* p) {
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    if (a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged)
+        return p;
+    if (a.type == cudaMemoryTypeHost && a.devicePointer) return static_cast<uint32_t*>(a.devicePointer);
+    return nullptr;
+}
+
+// Folds the device times of recorded pipelined searches into the
+// statistics; wait = true waits for those still in flight.
+int harvest_timing(mpm_handle* h, bool wait) {
+    for (int i = 0; i < mpm_handle::kRing; i++) {
+        if (!h->ring_used[i]) continue;
+        cudaError_t e = cudaEventQuery(h->ring[i][2]);
+        if (e == cudaErrorNotReady) {
+            if (!wait) continue;
+            e = cudaEventSynchronize(h->ring[i][2]);
+        }
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            return MPM_ECUDA;
+        }
+        float a = 0.f, b = 0.f;
+        cudaEventElapsedTime(&a, h->ring[i][0], h->ring[i][1]);
+        cudaEventElapsedTime(&b, h->ring[i][1], h->ring[i][2]);
+        h->stats.ms_scan += a;
+        h->stats.ms_verify += b;
+        h->ring_used[i] = 0;
+    }
+    return MPM_OK;
+}
+
+// The next event triple of the ring; its earlier recording (long finished in
+// a steady pipeline) is folded into the statistics first.
+int next_timing_slot(mpm_handle* h, cudaEvent_t** ev) {
+    const int i = h->ring_next;
+    if (!h->ring[i][0]) {
+        for (auto& e : h->ring[i])
+            if (cudaEventCreate(&e) != cudaSuccess) {
+                cudaGetLastError();
+                return MPM_ECUDA;
+            }
+    }
+    if (h->ring_used[i]) {
+        if (cudaEventSynchronize(h->ring[i][2]) != cudaSuccess) {
+            cudaGetLastError();
+            return MPM_ECUDA;
+        }
+        float a = 0.f, b = 0.f;
+        cudaEventElapsedTime(&a, h->ring[i][0], h->ring[i][1]);
+        cudaEventElapsedTime(&b, h->ring[i][1], h->ring[i][2]);
+        h->stats.ms_scan += a;
+        h->stats.ms_verify += b;
+    }
+    h->ring_used[i] = 1;
+    h->ring_next = (i + 1) % mpm_handle::kRing;
+    *ev = h->ring[i];
+    return MPM_OK;
+}
+
+// The end of a search closed by the rank sort kernel: wait for the stream and
+// take the counters from the mapped snapshot.
+int finish_counters(mpm_handle* h) {
+    if (cudaStreamSynchronize(h->stream) != cudaSuccess) return MPM_ECUDA;
+    for (int i = 0; i < mpm::kNumCounters; i++)
+        h->h_counters[i] = reinterpret_cast<volatile uint32_t*>(h->h_snap)[i];
     if (h->h_counters[mpm::kErrorFlag]) return (int)h->h_counters[mpm::kErrorFlag];
     if (h->timing) {
         float a = 0.f, b = 0.f;
@@ -277,7 +368,10 @@ mpm_handle* mpm_build(const uint8_t* P, size_t r, size_t m, int sigma, const mpm
               cudaMalloc(&h->d_pat, h->host.sorted_pat.size()) == cudaSuccess &&
               cudaMalloc(&h->d_pid, h->host.sorted_pid.size() * 4) == cudaSuccess &&
               cudaMalloc(&h->d_counters, mpm::kNumCounters * 4) == cudaSuccess &&
-              cudaMallocHost(&h->h_counters, mpm::kNumCounters * 4) == cudaSuccess;
+              cudaMemset(h->d_counters, 0, mpm::kNumCounters * 4) == cudaSuccess &&
+              cudaMallocHost(&h->h_counters, mpm::kNumCounters * 4) == cudaSuccess &&
+              cudaHostAlloc(&h->h_snap, mpm::kNumCounters * 4, cudaHostAllocMapped) == cudaSuccess &&
+              cudaHostGetDevicePointer(&h->d_snap, h->h_snap, 0) == cudaSuccess;
     ok = ok && cudaMemcpy(h->d_mu, h->host.mu, 256, cudaMemcpyHostToDevice) == cudaSuccess &&
          cudaMemcpy(h->d_table, h->host.table.data(), h->table_bytes_padded,
                     cudaMemcpyHostToDevice) == cudaSuccess &&
@@ -357,6 +451,8 @@ int mpm_search(mpm_handle* h, const uint8_t* T, size_t n, uint32_t* out_pos, uin
     int rc = prepare(h);
     if (rc) return set_error(rc);
     const size_t out_capacity = *z;
+    rc = harvest_timing(h, true);  // pipelined searches still timed belong to before
+    if (rc) return set_error(rc);
     h->stats = mpm_stats{};
     h->stats.n = n;
     h->stats.specialised = (h->jit || h->jit_cand) && !h->plan.p.smag ? 1u : 0u;
@@ -398,17 +494,21 @@ int mpm_search(mpm_handle* h, const uint8_t* T, size_t n, uint32_t* out_pos, uin
         oi = h->d_out + rank_cap;
     }
     for (int attempt = 0;; attempt++) {
+        // the counters are zero unless an earlier call left them otherwise;
+        // the rank sort kernel closes the search and zeroes them again
+        const bool reset = h->counters_dirty;
+        h->counters_dirty = true;
         rc = enqueue_filter(h, dT, (uint32_t)n, h->d_cand, (uint32_t)h->cand_cap, h->d_occ,
-                            (uint32_t)h->occ_cap, h->d_counters, &launches);
+                            (uint32_t)h->occ_cap, h->d_counters, &launches, reset);
         if (rc) return set_error(rc);
-        if (rank_cap > 0) {
-            if (mpm::launch_rank_sort(h->d_occ, h->d_counters + mpm::kOccCount, rank_cap, op, oi,
-                                      s) < 0)
-                return set_error(MPM_ECUDA);
-            launches++;
-        }
-        rc = read_counters(h, h->d_counters);
+        if (mpm::launch_rank_sort(h->d_occ, h->d_counters, rank_cap, op, oi, h->d_snap,
+                                  fused_search(h) ? 0xFFFFFFFFu : (uint32_t)h->cand_cap,
+                                  (uint32_t)h->occ_cap, s) < 0)
+            return set_error(MPM_ECUDA);
+        launches++;
+        rc = finish_counters(h);
         if (rc) return set_error(rc);
+        h->counters_dirty = false;
         const uint32_t nc = h->h_counters[mpm::kCandCount];
         const uint32_t nz = h->h_counters[mpm::kOccCount];
         bool again = false;
@@ -460,6 +560,80 @@ int mpm_search(mpm_handle* h, const uint8_t* T, size_t n, uint32_t* out_pos, uin
     }
     h->stats.launches = launches;
     return set_error(MPM_OK);
+}
+
+int mpm_search_async(mpm_handle* h, const uint8_t* T, size_t n, uint32_t* out_pos,
+                     uint32_t* out_pid, size_t cap, uint32_t* status) {
+    if (!h || !status || (n > 0 && !T) || n >= (1ull << 32)) return set_error(MPM_EINVAL);
+    if (cap > 0 && (!out_pos || !out_pid)) return set_error(MPM_EINVAL);
+    int rc = prepare(h);
+    if (rc) return set_error(rc);
+    if ((n > 0 && !is_device_ptr(T)) ||
+        (cap > 0 && (!is_device_ptr(out_pos) || !is_device_ptr(out_pid))))
+        return set_error(MPM_EINVAL);
+    uint32_t* dstatus = device_address(status);
+    if (!dstatus) return set_error(MPM_EINVAL);
+    cudaStream_t s = h->stream;
+    // buffers as mpm_search sizes them on its first call (allocation waits
+    // for the device only the first time)
+    if (!fused_search(h) &&
+        grow(&h->d_cand, &h->cand_cap, std::max<size_t>(1 << 16, n / 64 + 1024)))
+        return set_error(MPM_ENOMEM);
+    if (!h->d_occ || h->occ_cap < (1u << 16)) {
+        size_t c = 0;
+        if (grow(&h->d_occ, &h->occ_cap, 1 << 16) || grow(&h->d_occ_tmp, &c, 1 << 16))
+            return set_error(MPM_ENOMEM);
+    }
+    const uint32_t q = (uint32_t)h->plan.p.q, k = (uint32_t)h->plan.p.k;
+    h->stats.n += n;
+    h->stats.sampled += (n / q) / k;
+    h->stats.specialised = (h->jit || h->jit_cand) && !h->plan.p.smag ? 1u : 0u;
+    cudaEvent_t* ev = nullptr;
+    if (h->timing) {
+        rc = next_timing_slot(h, &ev);
+        if (rc) return set_error(rc);
+    }
+    const bool reset = h->counters_dirty;
+    h->counters_dirty = true;
+    int launches = 0;
+    if (n >= h->plan.m) {
+        rc = enqueue_filter(h, T, (uint32_t)n, h->d_cand, (uint32_t)h->cand_cap, h->d_occ,
+                            (uint32_t)h->occ_cap, h->d_counters, &launches, reset, ev);
+        if (rc) return set_error(rc);
+    } else {
+        if (reset && cudaMemsetAsync(h->d_counters, 0, mpm::kNumCounters * 4, s) != cudaSuccess)
+            return set_error(MPM_ECUDA);
+        if (ev) {
+            for (int i = 0; i < 3; i++) cudaEventRecord(ev[i], s);
+        }
+    }
+    const uint32_t rank_cap = (uint32_t)std::min<size_t>(cap, mpm::kRankSortMax);
+    if (mpm::launch_rank_sort(h->d_occ, h->d_counters, rank_cap, out_pos, out_pid, dstatus,
+                              fused_search(h) ? 0xFFFFFFFFu : (uint32_t)h->cand_cap,
+                              (uint32_t)h->occ_cap, s) < 0)
+        return set_error(MPM_ECUDA);
+    launches++;
+    h->stats.launches += (uint32_t)launches;
+    h->counters_dirty = false;
+    return set_error(MPM_OK);
+}
+
+int mpm_sync(mpm_handle* h) {
+    if (!h) return set_error(MPM_EINVAL);
+    int rc = prepare(h);
+    if (rc) return set_error(rc);
+    if (cudaStreamSynchronize(h->stream) != cudaSuccess) {
+        cudaGetLastError();
+        return set_error(MPM_ECUDA);
+    }
+    return set_error(harvest_timing(h, true));
+}
+
+int mpm_reset_stats(mpm_handle* h) {
+    if (!h) return set_error(MPM_EINVAL);
+    int rc = harvest_timing(h, true);
+    h->stats = mpm_stats{};
+    return set_error(rc);
 }
 
 int mpm_jit_compile(const uint8_t* P, size_t r, size_t m, int sigma, const mpm_params* params,
@@ -516,6 +690,7 @@ int mpm_scan(mpm_handle* h, const uint8_t* T, size_t n, uint64_t* cand, size_t* 
         if (!h->jit_cand && h->plan.p.kernel == MPM_KERNEL_SPECIALISED)
             return set_error(err ? err : MPM_ENOTSUP);
     }
+    h->counters_dirty = true;  // this call leaves its counts behind
     if (cudaMemsetAsync(h->d_counters, 0, mpm::kNumCounters * 4, s) != cudaSuccess)
         return set_error(MPM_ECUDA);
     int l = 0;
@@ -627,7 +802,8 @@ extern "C" int mpm_search_noalloc(mpm_handle* h, const uint8_t* T, size_t n, uin
     if (rc) return set_error(rc);
     const uint32_t rank_cap = (uint32_t)std::min<size_t>(out_capacity, mpm::kRankSortMax);
     if (rank_cap > 0) {
-        if (mpm::launch_rank_sort(occ, counters + mpm::kOccCount, rank_cap, out_pos, out_pid, s) < 0)
+        if (mpm::launch_rank_sort(occ, counters, rank_cap, out_pos, out_pid, nullptr, 0u, 0u,
+                                  s) < 0)
             return set_error(MPM_ECUDA);
         launches++;
     }

@@ -29,6 +29,9 @@ struct mpm_handle {
     size_t hist_cap = 0;
     uint32_t* d_counters = nullptr;
     uint32_t* h_counters = nullptr;  // pinned
+    uint32_t* h_snap = nullptr;      // mapped pinned: counters at the end of a search
+    uint32_t* d_snap = nullptr;      // its device address
+    bool counters_dirty = false;     // d_counters not known to be zero
     uint8_t* d_text = nullptr;       // staging for host text
     size_t text_cap = 0;
     uint32_t* d_codes = nullptr;     // SMAG codes
@@ -42,5 +45,10 @@ struct mpm_handle {
     bool jit_cand_tried = false;
     int timing = 0;
     cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};
+    // event triples of pipelined searches (mpm_search_async), reused in turn
+    static constexpr int kRing = 64;
+    cudaEvent_t ring[kRing][3] = {};
+    int ring_used[kRing] = {};
+    int ring_next = 0;
 };
 

@@ -16,6 +16,7 @@ enum Counter : int {
     kCandCount = 0,   // candidate records produced by the scan
     kOccCount = 1,    // occurrences produced by verification
     kErrorFlag = 2,   // MPM_ETIMEOUT when a bounded wait gave up
+    kDoneCount = 3,   // blocks of the closing kernel that have read the counts
     kNumCounters = 4
 };
 
@@ -97,10 +98,16 @@ bool jit_verifies(const JitKernel* k);
 int launch_scan_jit(const ScanArgs& a, const VerifyArgs* v, const JitKernel* k, int num_sms,
                     int chunk, cudaStream_t s);
 
-// Sorts the device-counted occurrence keys (*count, in keys) into
-// out_pos/out_pid without the host knowing the count: one grid-wide rank
-// sort, valid while the count is at most kRankSortMax and at most out_cap;
-// otherwise it writes nothing and leaves the outputs to launch_sort_output.
+// Sorts the device-counted occurrence keys (counters[kOccCount], in keys)
+// into out_pos/out_pid without the host knowing the count: one grid-wide
+// rank sort, valid while the count is at most kRankSortMax and at most
+// out_cap; otherwise it writes nothing and leaves the outputs to
+// launch_sort_output.  With a snapshot (device address of device or mapped
+// host memory), it also closes the search: the counters (candidates,
+// occurrences, error) are copied there, with a fourth word that is 1 when
+// the outputs hold every occurrence (no error, count <= out_cap, <= the rank
+// sort's limit, <= occ_cap, candidates <= cand_cap), and are zeroed for the
+// next search, so no reset or copy-back is enqueued.
 constexpr uint32_t kRankSortMax = 4096;
 
 // LSD radix sort of keys[0 .. min(*count, cap)) over the 8-bit digits at
@@ -112,8 +119,9 @@ size_t sort_dev_hist_entries(uint32_t cap);
 int launch_sort_dev(uint64_t* keys, uint64_t* tmp, uint32_t* hist, uint32_t cap,
                     const uint32_t* count, const int* shifts, int nshifts, int num_sms,
                     uint64_t** sorted, cudaStream_t s);
-int launch_rank_sort(const uint64_t* keys, const uint32_t* count, uint32_t out_cap,
-                     uint32_t* out_pos, uint32_t* out_pid, cudaStream_t s);
+int launch_rank_sort(const uint64_t* keys, uint32_t* counters, uint32_t out_cap,
+                     uint32_t* out_pos, uint32_t* out_pid, uint32_t* snapshot, uint32_t cand_cap,
+                     uint32_t occ_cap, cudaStream_t s);
 
 // Sorts z keys (in d_keys, device count unknown to the kernels: z is passed)
 // and writes out_pos/out_pid.  tmp must hold z keys; returns launches or -1.

@@ -153,11 +153,35 @@ __global__ void __launch_bounds__(kRadixThreads)
 constexpr int kRankThreads = 256;
 constexpr int kRankTile = 2048;
 
+// counters: the search's counter block (occurrences at kOccCount).  With a
+// snapshot, every block counts itself in (kDoneCount) after reading the
+// occurrence count, and the last one copies the counters to the snapshot
+// (mapped host memory) and zeroes them for the next search.
 __global__ void __launch_bounds__(kRankThreads)
-    rank_sort_kernel(const uint64_t* keys, const uint32_t* count, uint32_t out_cap,
-                     uint32_t* out_pos, uint32_t* out_pid) {
+    rank_sort_kernel(const uint64_t* keys, uint32_t* counters, uint32_t out_cap,
+                     uint32_t* out_pos, uint32_t* out_pid, uint32_t* snapshot,
+                     uint32_t cand_cap, uint32_t occ_cap) {
     __shared__ uint64_t tile[kRankTile];
-    const uint32_t z = *count;
+    __shared__ uint32_t s_z;
+    if (threadIdx.x == 0) s_z = *(volatile uint32_t*)&counters[kOccCount];
+    __syncthreads();
+    const uint32_t z = s_z;
+    if (snapshot && threadIdx.x == 0) {
+        __threadfence();
+        if (atomicAdd(&counters[kDoneCount], 1u) == gridDim.x - 1) {
+            __threadfence();
+            volatile uint32_t* c = counters;
+            const uint32_t cand = c[kCandCount], occ = c[kOccCount], err = c[kErrorFlag];
+            snapshot[kCandCount] = cand;
+            snapshot[kOccCount] = occ;
+            snapshot[kErrorFlag] = err;
+            // 1: the outputs hold every occurrence, sorted
+            snapshot[kDoneCount] = (err == 0 && occ <= out_cap && occ <= kRankSortMax &&
+                                    occ <= occ_cap && cand <= cand_cap) ? 1u : 0u;
+            for (int i = 0; i < kNumCounters; i++) c[i] = 0;
+            __threadfence_system();
+        }
+    }
     if (z > kRankSortMax || z > out_cap) return;
     if (blockIdx.x * blockDim.x >= z) return;
     const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -329,10 +353,12 @@ int launch_sort_dev(uint64_t* keys, uint64_t* tmp, uint32_t* hist, uint32_t cap,
     return cudaPeekAtLastError() == cudaSuccess ? launches : -1;
 }
 
-int launch_rank_sort(const uint64_t* keys, const uint32_t* count, uint32_t out_cap,
-                     uint32_t* out_pos, uint32_t* out_pid, cudaStream_t s) {
+int launch_rank_sort(const uint64_t* keys, uint32_t* counters, uint32_t out_cap,
+                     uint32_t* out_pos, uint32_t* out_pid, uint32_t* snapshot, uint32_t cand_cap,
+                     uint32_t occ_cap, cudaStream_t s) {
     const uint32_t blocks = (kRankSortMax + kRankThreads - 1) / kRankThreads;
-    rank_sort_kernel<<<blocks, kRankThreads, 0, s>>>(keys, count, out_cap, out_pos, out_pid);
+    rank_sort_kernel<<<blocks, kRankThreads, 0, s>>>(keys, counters, out_cap, out_pos, out_pid,
+                                                     snapshot, cand_cap, occ_cap);
     return cudaPeekAtLastError() == cudaSuccess ? 1 : -1;
 }
 
