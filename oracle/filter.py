@@ -40,6 +40,12 @@ Steps and where they come from
   verify / search                     Section 3.2: verification against the
                                       r patterns in the original alphabet
                                       (Section 3.3).
+  overlap=True                        Section 2's first filter, before MAG's
+                                      non-overlapping factoring: the m-q+1
+                                      overlapping q-grams of every pattern
+                                      superimposed, the text's q-gram at
+                                      every position, a window standing for
+                                      its own start (no shifts).
 
 Readings where the paper is silent or garbled (each is listed with its
 reason in the design notes):
@@ -53,6 +59,8 @@ reason in the design notes):
   * rank ties are broken by byte value; the greedy heuristic is
     longest-processing-time first, ties to the lowest bin; bytes absent
     from the patterns go to bin sigma'-1;
+  * with overlapping q-grams the AOSO scan reads the text q-grams h = k-1
+    (mod k) by byte position, the same recurrence over a longer sequence;
   * q-gram digit order: "lsd" is the formula of Section 3.2 (S[1] least
     significant); "msd" is the order the multiply trick of Section 3.3
     produces (S[1] most significant).  Both are bijections, so the filter's
@@ -192,35 +200,45 @@ class FilterParams:
     digits; with qhash=True, sigma' is the number of q-gram bins and a
     q-gram's code is qgram_hash of its raw bytes."""
 
-    def __init__(self, q, sigma_r, k, mu=None, order="msd", qhash=False):
+    def __init__(self, q, sigma_r, k, mu=None, order="msd", qhash=False, overlap=False):
         self.q, self.sigma_r, self.k = int(q), int(sigma_r), int(k)
         self.qhash = bool(qhash)
+        self.overlap = bool(overlap)
         self.mu = None if mu is None else np.asarray(mu, dtype=np.uint8)
         self.order = order
 
     def lengths(self, m):
-        """(L', m', m''): common q-gram length, AOSO subpattern length and the
-        number of filter positions k*m' (at most 64)."""
-        Lc = (m - self.q + 1) // self.q
+        """(L', m', m''): the q-gram pattern length (m - q + 1 overlapping
+        q-grams, or the common length floor((m - q + 1) / q) of the q shifts'
+        non-overlapping q-grams), the AOSO subpattern length and the number of
+        filter positions k*m' (at most 64)."""
+        Lc = (m - self.q + 1) if self.overlap else (m - self.q + 1) // self.q
         Lf = min(Lc, 64)
         mp = Lf // self.k
         return Lc, mp, self.k * mp
 
 
+def _qgram_patterns(rows, fp, Lc):
+    if fp.overlap:
+        return overlapping_qgram_patterns(rows, fp.q)
+    return nonoverlapping_qgram_patterns(rows, fp.q, shifts=True, length=Lc)
+
+
 def pattern_classes(P, fp):
     """Cls[p] for the filter positions p < m'': the reduced-alphabet codes of
-    the p-th non-overlapping q-gram of every pattern and every shift."""
+    the p-th q-gram of every pattern (every shift of it, for non-overlapping
+    q-grams)."""
     P = np.asarray(P, dtype=np.uint8)
     m = P.shape[1]
     Lc, mp, mpp = fp.lengths(m)
     assert mp >= 1, "infeasible: need floor(min(L',64)/k) >= 1"
     if fp.qhash:
-        qp = nonoverlapping_qgram_patterns([list(row) for row in P], fp.q, shifts=True, length=Lc)
+        qp = _qgram_patterns([list(row) for row in P], fp, Lc)
         classes = superimpose(qp)[:mpp]
         bits = log2i(fp.sigma_r)
         return [set(qgram_hash(g, bits) for g in cls) for cls in classes]
     reduced = [[int(fp.mu[c]) for c in row] for row in P]
-    qp = nonoverlapping_qgram_patterns(reduced, fp.q, shifts=True, length=Lc)
+    qp = _qgram_patterns(reduced, fp, Lc)
     classes = superimpose(qp)[:mpp]
     return [set(qgram_code(g, fp.sigma_r, fp.order) for g in cls) for cls in classes]
 
@@ -239,8 +257,17 @@ def mask_table(classes, fp):
 
 def text_codes(T, fp):
     """t'(h) for h = 0..floor(n/q)-1: the codes of the text's non-overlapping
-    q-grams (the text factored like the patterns, Section 2)."""
+    q-grams (the text factored like the patterns, Section 2); with overlap,
+    the code of T[h..h+q) for every h = 0..n-q."""
     T = np.asarray(T, dtype=np.uint8)
+    if fp.overlap:
+        nh = max(0, T.size - fp.q + 1)
+        grams = [T[h:h + fp.q] for h in range(nh)]
+        if fp.qhash:
+            bits = log2i(fp.sigma_r)
+            return np.array([qgram_hash(g.tobytes(), bits) for g in grams], dtype=np.int64)
+        return np.array([qgram_code([int(fp.mu[c]) for c in g], fp.sigma_r, fp.order)
+                         for g in grams], dtype=np.int64)
     nq = T.size // fp.q
     if fp.qhash:
         bits = log2i(fp.sigma_r)
@@ -320,11 +347,11 @@ def verify(T, P, windows, q):
     return out
 
 
-def make_params(P, q, sigma_r, k, map_kind, shift=0, order="msd"):
+def make_params(P, q, sigma_r, k, map_kind, shift=0, order="msd", overlap=False):
     """Convenience: the mapping of `map_kind` ("rank", "greedy", "lowbits",
     "qhash")."""
     if map_kind == "qhash":
-        return FilterParams(q, sigma_r, k, None, order, qhash=True)
+        return FilterParams(q, sigma_r, k, None, order, qhash=True, overlap=overlap)
     if map_kind == "rank":
         mu = map_rank(P, sigma_r)
     elif map_kind == "greedy":
@@ -333,7 +360,7 @@ def make_params(P, q, sigma_r, k, map_kind, shift=0, order="msd"):
         mu = map_lowbits(sigma_r, shift)
     else:
         raise ValueError(map_kind)
-    return FilterParams(q, sigma_r, k, mu, order)
+    return FilterParams(q, sigma_r, k, mu, order, overlap=overlap)
 
 
 def search(T, P, fp):
@@ -343,7 +370,8 @@ def search(T, P, fp):
     B = mask_table(classes, fp)
     codes = text_codes(T, fp)
     windows = aoso_scan(codes, B, fp, len(classes))
-    return verify(T, P, windows, fp.q)
+    # a window of overlapping q-grams starts at its own text position
+    return verify(T, P, windows, 1 if fp.overlap else fp.q)
 
 
 def expected_class_size(sigma, r):

@@ -11,9 +11,10 @@
 // loads the unit's mask table into shared memory (at its own entry width,
 // when it fits) and its warps pop the unit's tiles from a shared counter.
 // Each lane runs the Shift-Or recurrence over its range (after warming up
-// on the m'-1 sampled q-grams before it), reading 32 bytes at a time,
-// verifies its candidates on the spot against its set's pattern groups and
-// appends (text << 44) | (pos << 20) | pid.  A radix sort driven by the
+// on the m'-1 sampled q-grams before it), reading 32 bytes at a time; the
+// warp queues its fired steps in shared memory and verifies them 32 at a time
+// against the set's key bitmap and pattern groups, appending
+// (text << 44) | (pos << 20) | pid.  A radix sort driven by the
 // device count orders the keys; the whole run -- counter reset, scan, sort,
 // split into (text, pos, pid) and the count read-back -- is captured once
 // into a CUDA graph and replayed by every run.
@@ -85,10 +86,40 @@ constexpr int kPosBits = 24;   // text positions < 2^24 in a batch
 constexpr int kPidBits = 20;   // pattern ids < 2^20 per set
 constexpr int kTextShift = kPosBits + kPidBits;  // 44
 
+constexpr int kWarpQueue = 64;  // fired steps a warp holds before it verifies them
+
+// The warp verifies its queued fired steps, one record per lane at a time:
+// record (hq << 32) | fired bits stands for the windows
+// (hq - (m'-1)k - j) q - s, j a fired bit, s = 0 .. q-1 (Section 3.2).
+__device__ __forceinline__ void flush_queue(const uint64_t* queue, int count, const BatchSet& S,
+                                            const uint32_t* keys, uint32_t key_mask,
+                                            const WindowCtx& wc, int rsh) {
+    for (int r = (int)(threadIdx.x & 31); r < count; r += 32) {
+        const uint64_t rec = queue[r];
+        const int64_t hq = (int64_t)(rec >> 32);
+        uint32_t fired = (uint32_t)rec;
+        while (fired) {
+            const int j = __ffs((int)fired) - 1;
+            fired &= fired - 1;
+            for (int sh = 0; sh < S.q; sh++) {
+                const int64_t i = (hq - rsh - j) * S.q - sh;
+                if (i < 0 || i + (int64_t)S.m > (int64_t)wc.n) continue;
+                batch_check(wc, keys, key_mask, (uint32_t)i);
+            }
+        }
+    }
+}
+
+// All 32 lanes of a warp call this together for one tile; lane range
+// [a, b) (live = a < b).  Lane ranges are multiples of the sampling period
+// from the text start, so every lane's steps fall at the same offsets and the
+// step loop is uniform across the warp; fired steps go to the warp's queue
+// (ballot + prefix count) and are verified 32 at a time.
 template <int MODE, typename ET>
 __device__ void batch_lane(const BatchSet& S, const ET* tab, const uint8_t* smu,
                            const uint32_t* keys, uint32_t key_mask, const BatchText& tx,
-                           uint32_t a, uint32_t b, const WindowCtx& wc, uint32_t& ncand) {
+                           uint32_t a, uint32_t b, bool live, const WindowCtx& wc,
+                           uint64_t* queue, uint32_t& ncand) {
     using DT = typename Stepper<MODE, ET>::DT;
     FilterDev f{};
     f.q = S.q;
@@ -100,20 +131,24 @@ __device__ void batch_lane(const BatchSet& S, const ET* tab, const uint8_t* smu,
     sp.init(f, tab, smu);
     const uint32_t P = (uint32_t)(S.k * S.q);
     const uint32_t Wr = (((uint32_t)(S.mprime - 1) * P) + 3) & ~3u;
-    warm_up(sp, tx.T, tx.n, a, Wr, P, true);
+    warm_up(sp, tx.T, tx.n, a, Wr, P, live);
     const int rsh = (S.mprime - 1) * S.k;
     const uint32_t kmask = S.k >= 32 ? 0xFFFFFFFFu : ((1u << S.k) - 1u);
+    const uint32_t lane = threadIdx.x & 31;
+    const uint32_t below = (1u << lane) - 1u;
     uint32_t hq = a / (uint32_t)S.q + (uint32_t)(S.k - 1);
     int pos = 0, nxt = (int)P;
-    const uint32_t words = (b - a + 3) / 4;
+    const uint32_t words = live ? (b - a + 3) / 4 : 0;
+    uint32_t wmax = words;
+    for (int o = 16; o > 0; o >>= 1) wmax = max(wmax, __shfl_xor_sync(0xFFFFFFFFu, wmax, o));
     // a is a multiple of 32 from the text start: whole 32-byte sectors, read
     // as two 16-byte loads that stay in L1 between them
     const bool vec = (reinterpret_cast<uintptr_t>(tx.T) & 15) == 0;
-    bool done = false;
-    for (uint32_t w0 = 0; w0 < words && !done; w0 += 8) {
+    int qcount = 0;  // the same in every lane
+    for (uint32_t w0 = 0; w0 < wmax; w0 += 8) {
         uint32_t x[8];
         const uint32_t at0 = a + 4 * w0;
-        if (vec && at0 + 32 <= tx.n) {
+        if (vec && w0 + 8 <= words && at0 + 32 <= tx.n) {
             const uint4 lo = __ldg(reinterpret_cast<const uint4*>(tx.T + at0));
             const uint4 hi = __ldg(reinterpret_cast<const uint4*>(tx.T + at0 + 16));
             x[0] = lo.x; x[1] = lo.y; x[2] = lo.z; x[3] = lo.w;
@@ -135,30 +170,37 @@ __device__ void batch_lane(const BatchSet& S, const ET* tab, const uint8_t* smu,
         }
 #pragma unroll
         for (int u = 0; u < 8; u++) {
-            if (w0 + u >= words || done) break;
+            if (w0 + u >= wmax) break;
             sp.push(x[u]);
             pos += 4;
-            while (nxt <= pos && a + (uint32_t)nxt <= b) {
+            while (nxt <= pos) {
                 const uint32_t c = sp.code(pos - nxt);
                 sp.D = (sp.D << S.k) | (DT)tab[c];
-                uint32_t fired = (uint32_t)(~sp.D >> rsh) & kmask;
-                if (fired) {
-                    ncand++;
-                    while (fired) {
-                        const int j = __ffs((int)fired) - 1;
-                        fired &= fired - 1;
-                        for (int sh = 0; sh < S.q; sh++) {
-                            const int64_t i = ((int64_t)hq - rsh - j) * S.q - sh;
-                            if (i < 0 || i + (int64_t)S.m > (int64_t)tx.n) continue;
-                            batch_check(wc, keys, key_mask, (uint32_t)i);
-                        }
+                const bool act = live && a + (uint32_t)nxt <= b;
+                const uint32_t fired = act ? ((uint32_t)(~sp.D >> rsh) & kmask) : 0u;
+                const uint32_t bal = __ballot_sync(0xFFFFFFFFu, fired != 0);
+                if (bal) {
+                    if (fired) {
+                        queue[qcount + __popc(bal & below)] = ((uint64_t)hq << 32) | fired;
+                        ncand++;
+                    }
+                    qcount += __popc(bal);
+                    if (qcount >= 32) {
+                        __syncwarp();
+                        flush_queue(queue, qcount, S, keys, key_mask, wc, rsh);
+                        qcount = 0;
+                        __syncwarp();
                     }
                 }
                 nxt += (int)P;
                 hq += (uint32_t)S.k;
             }
-            if (nxt <= pos) done = true;
         }
+    }
+    if (qcount) {
+        __syncwarp();
+        flush_queue(queue, qcount, S, keys, key_mask, wc, rsh);
+        __syncwarp();
     }
 }
 
@@ -166,17 +208,21 @@ template <int MODE>
 __device__ __forceinline__ void batch_lane_eb(const BatchSet& S, const void* tab,
                                               const uint8_t* smu, const uint32_t* keys,
                                               uint32_t key_mask, const BatchText& tx,
-                                              uint32_t a, uint32_t b, const WindowCtx& wc,
+                                              uint32_t a, uint32_t b, bool live,
+                                              const WindowCtx& wc, uint64_t* queue,
                                               uint32_t& ncand) {
     switch (S.entry_bytes) {
         case 1:
-            batch_lane<MODE>(S, (const uint8_t*)tab, smu, keys, key_mask, tx, a, b, wc, ncand);
+            batch_lane<MODE>(S, (const uint8_t*)tab, smu, keys, key_mask, tx, a, b, live, wc,
+                             queue, ncand);
             break;
         case 2:
-            batch_lane<MODE>(S, (const uint16_t*)tab, smu, keys, key_mask, tx, a, b, wc, ncand);
+            batch_lane<MODE>(S, (const uint16_t*)tab, smu, keys, key_mask, tx, a, b, live, wc,
+                             queue, ncand);
             break;
         default:
-            batch_lane<MODE>(S, (const uint32_t*)tab, smu, keys, key_mask, tx, a, b, wc, ncand);
+            batch_lane<MODE>(S, (const uint32_t*)tab, smu, keys, key_mask, tx, a, b, live, wc,
+                             queue, ncand);
             break;
     }
 }
@@ -190,6 +236,7 @@ __global__ void __launch_bounds__(kBatchThreads, 1)
     uint8_t* s_tab = smem + 256;
     uint32_t* s_keys = reinterpret_cast<uint32_t*>(smem + 256 + kBatchSmemTable);
     __shared__ uint32_t s_unit, s_next;
+    __shared__ uint64_t s_queue[kBatchThreads / 32][kWarpQueue];
     const int lane = threadIdx.x & 31;
     uint32_t ncand = 0;
     for (;;) {
@@ -236,13 +283,14 @@ __global__ void __launch_bounds__(kBatchThreads, 1)
             wc.pos_shift = kPidBits;
             const uint32_t a = tl.start + (uint32_t)lane * tl.sub;
             const uint32_t b = min(tl.start + tl.len, a + tl.sub);
-            if (a >= b) continue;
+            const bool live = a < b;
+            uint64_t* queue = s_queue[threadIdx.x >> 5];
             switch (S.mode) {
-                case kLow2: batch_lane_eb<kLow2>(S, tab, s_mu, s_keys, kmask, tx, a, b, wc, ncand); break;
-                case kLowG: batch_lane_eb<kLowG>(S, tab, s_mu, s_keys, kmask, tx, a, b, wc, ncand); break;
-                case kLutRed: batch_lane_eb<kLutRed>(S, tab, s_mu, s_keys, kmask, tx, a, b, wc, ncand); break;
-                case kLutRaw: batch_lane_eb<kLutRaw>(S, tab, s_mu, s_keys, kmask, tx, a, b, wc, ncand); break;
-                default: batch_lane_eb<kQHash>(S, tab, s_mu, s_keys, kmask, tx, a, b, wc, ncand); break;
+                case kLow2: batch_lane_eb<kLow2>(S, tab, s_mu, s_keys, kmask, tx, a, b, live, wc, queue, ncand); break;
+                case kLowG: batch_lane_eb<kLowG>(S, tab, s_mu, s_keys, kmask, tx, a, b, live, wc, queue, ncand); break;
+                case kLutRed: batch_lane_eb<kLutRed>(S, tab, s_mu, s_keys, kmask, tx, a, b, live, wc, queue, ncand); break;
+                case kLutRaw: batch_lane_eb<kLutRaw>(S, tab, s_mu, s_keys, kmask, tx, a, b, live, wc, queue, ncand); break;
+                default: batch_lane_eb<kQHash>(S, tab, s_mu, s_keys, kmask, tx, a, b, live, wc, queue, ncand); break;
             }
         }
     }

@@ -385,3 +385,84 @@ def test_qhash_filter_equals_definition_and_search_is_exact():
         wins = F.aoso_scan(codes, F.mask_table(cls, fp), fp, len(cls))
         assert wins == F.candidate_windows_by_definition(codes, cls, fp)
         assert F.search(T, P, fp) == brute.occurrences(T.tobytes(), [p.tobytes() for p in P])
+
+
+# ------------------------------------------------ overlapping q-grams (Section 2)
+
+def _overlap_case(rng, sigma, n, r, m, planted):
+    T = rng.integers(0, sigma, n).astype(np.uint8) + 97
+    P = rng.integers(0, sigma, (r, m)).astype(np.uint8) + 97
+    for i in range(min(planted, r)):
+        o = int(rng.integers(0, n - m + 1))
+        P[i] = T[o:o + m]
+    return T, P
+
+
+def test_overlapping_classes_follow_the_worked_example():
+    # Section 2's overlapping 2-grams of {abba, bbac}: {ab, bb}, {bb, ba}, {ba, ac}
+    g = _golden("section2_examples.json")
+    P = np.array([list(p.encode()) for p in g["patterns"]], np.uint8)
+    mu = np.zeros(256, np.uint8)
+    for c in b"abc":
+        mu[c] = c - 97
+    fp = F.FilterParams(2, 4, 1, mu, overlap=True)
+    classes = F.pattern_classes(P, fp)
+    code = lambda s2: F.qgram_code([ord(c) - 97 for c in s2], 4, "msd")  # noqa: E731
+    want = [set(code(x) for x in cls) for cls in g["overlapping_q2_superimposed"]]
+    assert classes == want
+    assert fp.lengths(4) == (3, 3, 3)
+
+
+def test_overlap_with_q1_equals_the_nonoverlapping_filter():
+    rng = np.random.default_rng(71)
+    for _ in range(40):
+        T, P = _overlap_case(rng, 4, 300, 5, int(rng.integers(2, 12)), 2)
+        k = int(rng.integers(1, 4))
+        if P.shape[1] // k < 1:
+            continue
+        a = F.make_params(P, 1, 4, k, "rank")
+        b = F.make_params(P, 1, 4, k, "rank", overlap=True)
+        ca, cb = F.pattern_classes(P, a), F.pattern_classes(P, b)
+        assert ca == cb
+        ta, tb = F.text_codes(T, a), F.text_codes(T, b)
+        assert np.array_equal(ta, tb)
+        assert F.aoso_scan(ta, F.mask_table(ca, a), a, len(ca)) == \
+            F.aoso_scan(tb, F.mask_table(cb, b), b, len(cb))
+
+
+def test_overlap_single_pattern_lossless_filter_is_exact():
+    # one pattern, an injective map, k = 1: every position's class is one
+    # q-gram, and the m - q + 1 overlapping q-grams cover the whole window,
+    # so the candidates are exactly the occurrences
+    rng = np.random.default_rng(72)
+    for _ in range(60):
+        m = int(rng.integers(2, 20))
+        q = int(rng.integers(1, min(m, 4) + 1))
+        T, P = _overlap_case(rng, 3, 400, 1, m, 1)
+        fp = F.make_params(P, q, 4, 1, "rank", overlap=True)
+        classes = F.pattern_classes(P, fp)
+        windows = F.aoso_scan(F.text_codes(T, fp), F.mask_table(classes, fp), fp, len(classes))
+        occ = [i for i in range(T.size - m + 1) if bytes(T[i:i + m]) == bytes(P[0])]
+        assert windows == occ
+
+
+def test_overlap_scan_equals_definition_and_search_equals_brute_force():
+    rng = np.random.default_rng(73)
+    for it in range(80):
+        m = int(rng.integers(3, 24))
+        q = int(rng.integers(1, min(m, 5) + 1))
+        Lc = m - q + 1
+        k = int(rng.integers(1, min(Lc, 6) + 1))
+        sigma = int(rng.choice([2, 4, 8]))
+        T, P = _overlap_case(rng, sigma, 500, int(rng.integers(1, 12)), m, 2)
+        kind = ["rank", "greedy", "qhash"][it % 3]
+        sr = 1 << 10 if kind == "qhash" else min(8, max(2, sigma // 2))
+        fp = F.make_params(P, q, sr, k, kind, overlap=True)
+        classes = F.pattern_classes(P, fp)
+        codes = F.text_codes(T, fp)
+        windows = F.aoso_scan(codes, F.mask_table(classes, fp), fp, len(classes))
+        assert windows == F.candidate_windows_by_definition(codes, classes, fp)
+        got = F.search(T, P, fp)
+        assert got == sorted(brute.occurrences(T, P))
+        # no false negatives: every occurrence is a candidate window
+        assert {i for i, _ in got} <= set(windows)
