@@ -83,6 +83,11 @@ extern "C" {
  *            request outside that fails with MPM_ENOTSUP); the generic one
  *            hashes q-grams of at most 5 bytes (MPM_ENOTSUP from the search
  *            otherwise).
+ *   overlap  0: MAG's non-overlapping q-grams of all q shifts; 1: the
+ *            overlapping q-grams of Section 2 (P_i[j..j+q-1], j < m-q+1, no
+ *            shifts; the text's q-gram at every byte, every k-th one read),
+ *            L' = m - q + 1.  Runs in the generic kernel (AUTO resolves to
+ *            it; SPECIALISED, SPLIT, SMAG and mpm_batch answer MPM_ENOTSUP).
  */
 #define MPM_KERNEL_AUTO        0
 #define MPM_KERNEL_GENERIC     1
@@ -99,6 +104,7 @@ typedef struct {
     int smag;
     int chunk;
     int kernel;
+    int overlap;
 } mpm_params;
 
 /* Sizes that follow from resolved parameters and m (Sections 3.1, 3.2). */

@@ -12,7 +12,7 @@ import ctypes
 
 import numpy as np
 
-from ._native import (KERNEL_AUTO, KERNEL_GENERIC, KERNEL_SPECIALISED,  # noqa: F401
+from ._native import (KERNEL_AUTO, KERNEL_GENERIC, KERNEL_SPECIALISED, KERNEL_SPLIT,  # noqa: F401,E501
                       MAP_AUTO, MAP_GREEDY, MAP_LOWBITS, MAP_QHASH, MAP_RANK, MPM_ECAPACITY, MPM_EINVAL,
                       MPM_ENOTSUP, MPM_OK, TABLE_AUTO, TABLE_GLOBAL, TABLE_SMEM, MpmError,
                       Params, Stats, TableInfo, declared_functions, lib)
@@ -27,8 +27,9 @@ def _torch():
 
 
 def make_params(q=0, sigma_r=0, k=0, map_kind=MAP_AUTO, map_shift=-1, table_place=TABLE_AUTO,
-                smag=0, chunk=0, kernel=KERNEL_AUTO):
-    return Params(q, sigma_r, k, map_kind, map_shift, table_place, smag, chunk, kernel)
+                smag=0, chunk=0, kernel=KERNEL_AUTO, overlap=0):
+    return Params(q, sigma_r, k, map_kind, map_shift, table_place, smag, chunk, kernel,
+                  overlap)
 
 
 def jit_compile(P, sigma, **kw):

@@ -483,7 +483,7 @@ mpm_batch* mpm_batch_create(mpm_handle* const* sets, int nsets, const uint8_t* c
             set_error(MPM_ENOTSUP);
             return nullptr;
         }
-        if (h->plan.p.map_kind == MPM_MAP_QHASH && h->plan.p.q > 5) {
+        if ((h->plan.p.map_kind == MPM_MAP_QHASH && h->plan.p.q > 5) || h->plan.p.overlap) {
             set_error(MPM_ENOTSUP);
             return nullptr;
         }

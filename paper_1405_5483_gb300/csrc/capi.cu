@@ -67,6 +67,7 @@ mpm::FilterDev filter_dev(const mpm_handle* h) {
     f.shift = h->plan.p.map_shift;
     f.mprime = h->plan.info.mprime;
     f.positions = h->plan.info.positions;
+    f.overlap = h->plan.p.overlap;
     return f;
 }
 
@@ -110,7 +111,8 @@ mpm::ScanArgs scan_args(const mpm_handle* h, const uint8_t* dT, uint32_t n, uint
     a.T = dT;
     a.n = n;
     a.f = filter_dev(h);
-    a.P = (uint32_t)(a.f.k * a.f.q);
+    // bytes per sampled q-gram: k q non-overlapping, k overlapping
+    a.P = (uint32_t)(a.f.overlap ? a.f.k : a.f.k * a.f.q);
     const uint32_t wb = (uint32_t)(a.f.mprime - 1) * a.P;
     a.warm_bytes = (wb + 3) & ~3u;
     a.cand = cand;
@@ -126,7 +128,9 @@ mpm::VerifyArgs verify_args(const mpm_handle* h, const uint8_t* dT, uint32_t n,
     v.T = dT;
     v.n = n;
     v.m = (uint32_t)h->plan.m;
-    v.q = h->plan.p.q;
+    // a record's window h0 stands for the starts h0 q - s, s < q; an
+    // overlapping q-gram window for its own start h0 (one shift, factor 1)
+    v.q = h->plan.p.overlap ? 1 : h->plan.p.q;
     v.k = h->plan.p.k;
     v.mprime = h->plan.info.mprime;
     v.cand = cand;
@@ -340,6 +344,16 @@ mpm_handle* mpm_build(const uint8_t* P, size_t r, size_t m, int sigma, const mpm
         delete h;
         set_error(rc);
         return nullptr;
+    }
+    if (h->plan.p.overlap) {
+        // overlapping q-grams run in the generic kernel only
+        if (h->plan.p.smag || h->plan.p.kernel == MPM_KERNEL_SPECIALISED ||
+            h->plan.p.kernel == MPM_KERNEL_SPLIT) {
+            delete h;
+            set_error(MPM_ENOTSUP);
+            return nullptr;
+        }
+        h->plan.p.kernel = MPM_KERNEL_GENERIC;
     }
     // host tables
     try {
@@ -641,6 +655,7 @@ int mpm_jit_compile(const uint8_t* P, size_t r, size_t m, int sigma, const mpm_p
     mpm::Plan plan;
     int rc = mpm::make_plan(P, r, m, sigma, params, &plan);
     if (rc) return set_error(rc);
+    if (plan.p.overlap) return set_error(MPM_ENOTSUP);  // generic kernel only
     mpm::FilterDev f{};
     f.table_bytes = (uint32_t)((plan.info.table_bytes + 15) & ~uint64_t(15));
     f.entry_bytes = plan.info.entry_bytes;

@@ -86,9 +86,11 @@ struct Lengths {
     int L, Lf, mprime, positions;
 };
 
-Lengths lengths(size_t m, int q, int k) {
+// L' = the q-gram pattern length: floor((m-q+1)/q) non-overlapping q-grams
+// (common to the q shifts), or m-q+1 overlapping ones.
+Lengths lengths(size_t m, int q, int k, bool overlap) {
     Lengths x;
-    long L = ((long)m - q + 1) / q;
+    long L = overlap ? ((long)m - q + 1) : ((long)m - q + 1) / q;
     x.L = (int)std::max(0L, L);
     x.Lf = std::min(x.L, kMaxPositions);
     x.mprime = k >= 1 ? x.Lf / k : 0;
@@ -106,9 +108,12 @@ int entry_bytes_for(int positions) {
 // Probability, under the pattern-set symbol frequencies mapped by mu, that a
 // random text q-gram falls in the class of each filter position
 // (the "p" of Section 3.2, measured on the actual classes).
+// Position t's q-grams start at s + t * stride for s < shifts: q and q for
+// non-overlapping q-grams of all shifts, 1 and 1 for overlapping ones.
 std::vector<double> class_probabilities(const uint8_t* P, size_t r, size_t m, int q,
                                         int ell, const uint8_t mu[256],
-                                        const uint64_t h[256], int npos) {
+                                        const uint64_t h[256], int npos, bool overlap) {
+    const int shifts = overlap ? 1 : q, stride = overlap ? 1 : q;
     const int sr = 1 << ell;
     std::vector<double> ps(sr, 0.0);
     const double tot = (double)(r * m);
@@ -119,8 +124,9 @@ std::vector<double> class_probabilities(const uint8_t* P, size_t r, size_t m, in
     for (auto& v : codes) v.reserve(r * q);
     for (size_t i = 0; i < r; i++) {
         for (size_t j = 0; j < m; j++) red[j] = mu[P[i * m + j]];
-        for (int s = 0; s < q; s++)
-            for (int t = 0; t < npos; t++) codes[t].push_back(msd_code(&red[s + t * q], q, ell));
+        for (int s = 0; s < shifts; s++)
+            for (int t = 0; t < npos; t++)
+                codes[t].push_back(msd_code(&red[s + t * stride], q, ell));
     }
     for (int t = 0; t < npos; t++) {
         auto& v = codes[t];
@@ -153,7 +159,8 @@ struct GramStats {
 };
 
 GramStats gram_stats(const uint8_t* P, size_t r, size_t m, int q, const uint64_t h[256],
-                     int npos) {
+                     int npos, bool overlap) {
+    const int shifts = overlap ? 1 : q, stride = overlap ? 1 : q;
     double pb[256];
     const double tot = (double)(r * m);
     for (int c = 0; c < 256; c++) pb[c] = (double)h[c] / tot;
@@ -162,8 +169,9 @@ GramStats gram_stats(const uint8_t* P, size_t r, size_t m, int q, const uint64_t
     g.ptrue.assign(npos, 0.0);
     for (auto& v : g.grams) v.reserve(r * q);
     for (size_t i = 0; i < r; i++)
-        for (int s = 0; s < q; s++)
-            for (int t = 0; t < npos; t++) g.grams[t].push_back(raw_qgram(P + i * m + s + t * q, q));
+        for (int s = 0; s < shifts; s++)
+            for (int t = 0; t < npos; t++)
+                g.grams[t].push_back(raw_qgram(P + i * m + s + t * stride, q));
     for (int t = 0; t < npos; t++) {
         auto& v = g.grams[t];
         std::sort(v.begin(), v.end());
@@ -212,12 +220,15 @@ constexpr uint64_t kAutoTableBytes = 64ull << 20;
 
 // Relative cost per text byte of one parameter choice (a planning
 // heuristic; the autotuner replaces it with measurements).
-double plan_cost(int kind, int q, int k, double rate, uint64_t table_bytes) {
-    const double P = (double)q * k;
+double plan_cost(int kind, int q, int k, double rate, uint64_t table_bytes, bool overlap) {
+    // bytes per sampled q-gram; a candidate record stands for q windows (one
+    // per shift), or one with overlapping q-grams
+    const double P = overlap ? (double)k : (double)q * k;
+    const int shifts = overlap ? 1 : q;
     const double per_byte = kind == MPM_MAP_QHASH ? 0.5 : (kind == MPM_MAP_LOWBITS ? 1.5 : 3.5);
     double alu = per_byte + 10.0 / P;
     double scan = std::max(1.0, alu / 4.0);
-    double verify = rate / P * q * 48.0;
+    double verify = rate / P * shifts * 48.0;
     double table = table_bytes <= kSmemTableBudget ? 0.0
                    : (table_bytes <= (8ull << 20) ? 6.0 / P : 14.0 / P);
     return scan + verify + table;
@@ -281,6 +292,8 @@ int make_plan(const uint8_t* P, size_t r, size_t m, int sigma, const mpm_params*
     if (req.map_shift > 7) return MPM_EINVAL;
     if (req.table_place < 0 || req.table_place > MPM_TABLE_GLOBAL) return MPM_EINVAL;
     if (req.smag < 0 || req.smag > 1 || req.chunk < 0) return MPM_EINVAL;
+    if (req.overlap < 0 || req.overlap > 1) return MPM_EINVAL;
+    const bool ov = req.overlap == 1;
     if (req.kernel < MPM_KERNEL_AUTO || req.kernel > MPM_KERNEL_SPLIT) return MPM_EINVAL;
 
     uint64_t h[256];
@@ -311,14 +324,14 @@ int make_plan(const uint8_t* P, size_t r, size_t m, int sigma, const mpm_params*
             for (int k = 1; k <= std::min(L1.Lf, kMaxK); k++) ks.push_back(k);
         }
         for (int k : ks) {
-            Lengths Lk = lengths(m, q, k);
+            Lengths Lk = lengths(m, q, k, ov);
             if (Lk.mprime < 1) continue;
             const int eb = entry_bytes_for(Lk.positions);
             const uint64_t tb = entries * (uint64_t)eb;
             if (tb > kMaxTableBytes) continue;
             if (!(req.q && req.sigma_r && req.k) && tb > kAutoTableBytes) continue;
             double rate = candidate_rate(pt, k, Lk.mprime);
-            double cost = plan_cost(kind, q, k, rate, tb);
+            double cost = plan_cost(kind, q, k, rate, tb, ov);
             Plan cand;
             std::memset(&cand, 0, sizeof(cand));
             cand.p = req;
@@ -361,16 +374,18 @@ int make_plan(const uint8_t* P, size_t r, size_t m, int sigma, const mpm_params*
         } else if (!req.sigma_r) {
             for (int b = 10; b <= 16; b++) bins.push_back(1 << b);
         }
+        // overlapping q-grams run in the generic kernel, which hashes q <= 5
+        const int qmax = ov ? 5 : 8;
         std::vector<int> qs;
         if (req.q) {
-            if (req.q <= 8) qs.push_back(req.q);
+            if (req.q <= qmax) qs.push_back(req.q);
         } else {
-            for (int q = 2; q <= 8; q++) qs.push_back(q);
+            for (int q = 2; q <= qmax; q++) qs.push_back(q);
         }
         for (int q : qs) {
-            Lengths L1 = lengths(m, q, 1);
+            Lengths L1 = lengths(m, q, 1, ov);
             if (L1.L < 1) continue;
-            const GramStats g = gram_stats(P, r, m, q, h, L1.Lf);
+            const GramStats g = gram_stats(P, r, m, q, h, L1.Lf, ov);
             for (int sr : bins) {
                 const int bits = log2_exact(sr);
                 std::vector<double> pt = qhash_class_probabilities(g, q, bits);
@@ -405,12 +420,12 @@ int make_plan(const uint8_t* P, size_t r, size_t m, int sigma, const mpm_params*
         }
         for (int q : qs) {
             if (q * ell > 30) continue;
-            Lengths L1 = lengths(m, q, 1);
+            Lengths L1 = lengths(m, q, 1, ov);
             if (L1.L < 1) continue;
             const uint64_t entries = 1ull << (q * ell);
             if (!req.q && entries * 8 > kAutoTableBytes * 8 && q * ell > 26) continue;
             std::vector<double> pt =
-                class_probabilities(P, r, m, q, ell, mu, h, L1.Lf);
+                class_probabilities(P, r, m, q, ell, mu, h, L1.Lf, ov);
             consider(kind, sr, ell, shift, q, entries, pt, L1);
         }
     }
@@ -432,12 +447,15 @@ int make_mask_table(const uint8_t* P, const Plan& plan, const uint8_t mu[256],
     const int q = plan.p.q, ell = plan.ell, eb = plan.info.entry_bytes;
     const int npos = plan.info.positions;
     const size_t r = plan.r, m = plan.m;
+    // position t's q-grams: s + t * stride, s < shifts (see class_probabilities)
+    const int shifts = plan.p.overlap ? 1 : q, stride = plan.p.overlap ? 1 : q;
     std::memset(table, 0xFF, plan.info.table_bytes);
     if (plan.p.map_kind == MPM_MAP_QHASH) {
         for (size_t i = 0; i < r; i++)
-            for (int s = 0; s < q; s++)
+            for (int s = 0; s < shifts; s++)
                 for (int t = 0; t < npos; t++) {
-                    const uint32_t c = qgram_bin(raw_qgram(P + i * m + s + t * q, q), q, ell);
+                    const uint32_t c =
+                        qgram_bin(raw_qgram(P + i * m + s + t * stride, q), q, ell);
                     uint8_t* e = table + (size_t)c * eb;
                     e[t >> 3] &= (uint8_t)~(1u << (t & 7));
                 }
@@ -446,9 +464,9 @@ int make_mask_table(const uint8_t* P, const Plan& plan, const uint8_t mu[256],
     std::vector<uint8_t> red(m);
     for (size_t i = 0; i < r; i++) {
         for (size_t j = 0; j < m; j++) red[j] = mu[P[i * m + j]];
-        for (int s = 0; s < q; s++) {
+        for (int s = 0; s < shifts; s++) {
             for (int t = 0; t < npos; t++) {
-                uint32_t c = msd_code(&red[s + t * q], q, ell);
+                uint32_t c = msd_code(&red[s + t * stride], q, ell);
                 uint8_t* e = table + (size_t)c * eb;
                 e[t >> 3] &= (uint8_t)~(1u << (t & 7));
             }

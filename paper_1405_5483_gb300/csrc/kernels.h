@@ -28,6 +28,7 @@ struct FilterDev {
     int smem_table;           // copy the table into shared memory
     const uint8_t* mu;        // 256-entry byte -> reduced symbol map
     int map_kind, q, k, ell, shift, mprime, positions;
+    int overlap;              // 1: overlapping q-grams (generic kernel only)
 };
 
 // The scan's view of one text.

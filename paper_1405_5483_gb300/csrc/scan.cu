@@ -213,6 +213,62 @@ __global__ void __launch_bounds__(256) scan_plain_kernel(const ScanArgs A) {
     }
 }
 
+// ------------------------------------------ overlapping q-grams (Section 2)
+
+// The text's q-gram T[h..h+q) at every byte position h; the sampled ones are
+// h = k-1 (mod k), and D <- (D << k) | B[code].  Stream s owns the sampled
+// positions in [a, b), a = s Ls (Ls a multiple of lcm(k, 4)); it starts at
+// the earliest of the m'-1 sampled positions before its first one (positions
+// below 0 are skipped: they would leave D's bits at one), and emits records
+// (fired << 32) | h only for its own positions.  Verification reads a
+// record's windows as the starts h - (m'-1) k - j themselves.
+template <int MODE, typename ET>
+__global__ void __launch_bounds__(256) scan_overlap_kernel(const ScanArgs A) {
+    using DT = typename Stepper<MODE, ET>::DT;
+    __shared__ uint8_t s_mu[256];
+    for (uint32_t i = threadIdx.x; i < 256; i += blockDim.x) s_mu[i] = A.f.mu[i];
+    __syncthreads();
+    const ET* tab = reinterpret_cast<const ET*>(A.f.table);
+    const int k = A.f.k, q = A.f.q;
+    const int rsh = (A.f.mprime - 1) * k;
+    const uint32_t kmask = (k >= 32) ? 0xFFFFFFFFu : ((1u << k) - 1u);
+    const uint32_t nh = A.n >= (uint32_t)q ? A.n - (uint32_t)q + 1 : 0;  // q-gram positions
+    const uint32_t stride = gridDim.x * blockDim.x;
+    const uint32_t warp_first = (blockIdx.x * blockDim.x + threadIdx.x) & ~31u;
+    for (uint32_t s0 = warp_first; s0 < A.nstreams; s0 += stride) {
+        const uint32_t s = s0 + (threadIdx.x & 31);
+        const bool live = s < A.nstreams;
+        const uint32_t a = live ? s * A.Ls : 0;
+        const uint32_t b = live ? min(nh, a + A.Ls) : 0;
+        Stepper<MODE, ET> sp;
+        sp.init(A.f, tab, s_mu);
+        int64_t h = (int64_t)a + (k - 1) - (int64_t)(A.f.mprime - 1) * k;
+        if (h < 0) h += (-h + k - 1) / k * k;
+        uint32_t at = (uint32_t)h & ~3u;  // next byte to push
+        while ((uint64_t)h < (uint64_t)b) {
+            const uint32_t end = (uint32_t)h + (uint32_t)q;  // <= n
+            while (at < end) {
+                uint32_t x;
+                if (at + 4 <= A.n) {
+                    x = load_word(A.T, at);
+                } else {
+                    x = 0;
+                    for (uint32_t u = 0; u < 4 && at + u < A.n; u++)
+                        x |= (uint32_t)A.T[at + u] << (8 * u);
+                }
+                sp.push(x);
+                at += 4;
+            }
+            const uint32_t c = sp.code((int)(at - end));
+            sp.D = (sp.D << k) | (DT)tab[c];
+            if ((uint64_t)h >= a)
+                emit(__activemask(), fired_bits(sp.D, rsh, kmask), (uint32_t)h, A.cand, A.cap,
+                     A.counters);
+            h += k;
+        }
+    }
+}
+
 // ------------------------------------------------------ SMAG: scan of codes
 
 template <typename ET>
@@ -344,8 +400,33 @@ int launch_typed(const ScanArgs& A0, int num_sms, int chunk, cudaStream_t s) {
     return launches;
 }
 
+template <int MODE, typename ET>
+int launch_overlap(const ScanArgs& A0, int num_sms, int chunk, cudaStream_t s) {
+    ScanArgs A = A0;
+    const uint32_t nh = A.n >= (uint32_t)A.f.q ? A.n - (uint32_t)A.f.q + 1 : 0;
+    if (nh == 0) return 0;
+    const uint32_t L4 = lcm_u((uint32_t)A.f.k, 4);
+    uint32_t Ls = chunk > 0 ? (uint32_t)chunk : nh / (uint32_t)(num_sms * 256);
+    Ls = std::max(L4 * std::max(1u, 64u / L4), (Ls + L4 - 1) / L4 * L4);
+    A.Ls = Ls;
+    A.nstreams = (nh + Ls - 1) / Ls;
+    const uint32_t threads = 256;
+    const uint32_t blocks =
+        std::min<uint32_t>((A.nstreams + threads - 1) / threads, (uint32_t)num_sms * 8);
+    scan_overlap_kernel<MODE, ET><<<blocks, threads, 0, s>>>(A);
+    return cudaPeekAtLastError() == cudaSuccess ? 1 : -1;
+}
+
 template <int MODE>
 int launch_mode(const ScanArgs& A, int num_sms, int chunk, cudaStream_t s) {
+    if (A.f.overlap) {
+        switch (A.f.entry_bytes) {
+            case 1: return launch_overlap<MODE, uint8_t>(A, num_sms, chunk, s);
+            case 2: return launch_overlap<MODE, uint16_t>(A, num_sms, chunk, s);
+            case 4: return launch_overlap<MODE, uint32_t>(A, num_sms, chunk, s);
+            default: return launch_overlap<MODE, uint64_t>(A, num_sms, chunk, s);
+        }
+    }
     switch (A.f.entry_bytes) {
         case 1: return launch_typed<MODE, uint8_t>(A, num_sms, chunk, s);
         case 2: return launch_typed<MODE, uint16_t>(A, num_sms, chunk, s);

@@ -62,7 +62,8 @@ def _oracle_tables(P, p):
 
 def _oracle_fp(P, p):
     kind = {1: "rank", 2: "greedy", 3: "lowbits", 4: "qhash"}[p["map_kind"]]
-    return F.make_params(P, p["q"], p["sigma_r"], p["k"], kind, shift=p["map_shift"])
+    return F.make_params(P, p["q"], p["sigma_r"], p["k"], kind, shift=p["map_shift"],
+                         overlap=bool(p.get("overlap", 0)))
 
 
 def _oracle_mu(P, p):
@@ -124,6 +125,44 @@ def test_host_tables_qgram_hashing_equal_oracle(mpm, seed):
     assert np.array_equal(mu, omu)
     got = _table_positions(table, info["entry_bytes"], npos)
     assert np.array_equal(got, otab.astype(np.uint64))
+
+
+@pytest.mark.parametrize("seed", range(24))
+def test_host_tables_overlapping_qgrams_equal_oracle(mpm, seed):
+    rng = np.random.default_rng(500 + seed)
+    sigma = int(rng.choice([4, 20, 95]))
+    r = int(rng.integers(1, 120))
+    m = int(rng.choice([4, 8, 16, 32, 64, 80]))
+    kind = int(rng.integers(1, 5))
+    q = int(rng.integers(1, 6))
+    sr = 1 << 12 if kind == 4 else int(rng.choice([s for s in (2, 4, 8, 16) if s <= max(2, sigma)]))
+    while kind != 4 and q * int(np.log2(sr)) > 20:
+        q -= 1
+    Lc = min(m - q + 1, 64)
+    k = int(rng.integers(1, min(Lc, 32) + 1))
+    P = (rng.integers(0, sigma, size=(r, m)) + 33).astype(np.uint8)
+    kw = dict(q=q, sigma_r=sr, k=k, map_kind=kind, overlap=1,
+              map_shift=int(rng.integers(0, 3)) if kind == 3 else -1)
+    mu, table, info = mpm.host_tables(P, sigma, **kw)
+    # L' = m - q + 1 overlapping q-grams, at most 64 positions
+    assert info["L"] == m - q + 1 and info["positions"] == k * (Lc // k)
+    p = dict(q=q, sigma_r=sr, k=k, map_kind=kind, map_shift=info["map_shift"], overlap=1)
+    omu, otab, npos = _oracle_tables(P, p)
+    assert np.array_equal(mu, omu)
+    assert info["positions"] == npos
+    got = _table_positions(table, info["entry_bytes"], npos)
+    assert np.array_equal(got, otab.astype(np.uint64))
+
+
+def test_overlap_refusals(mpm):
+    P = np.frombuffer(b"ACGTACGTACGTACGT", np.uint8).reshape(1, 16)
+    rc, _ = mpm.jit_compile(P, 4, q=3, sigma_r=4, k=1, map_kind=2, overlap=1)
+    assert rc == mpm.MPM_ENOTSUP
+    # the planner keeps q-gram hashing to the generic kernel's 5 bytes
+    p, _ = mpm.plan(P, 4, map_kind=4, sigma_r=1 << 12, overlap=1)
+    assert p["q"] <= 5 and p["overlap"] == 1
+    with pytest.raises(mpm.MpmError):
+        mpm.plan(P, 4, q=3, sigma_r=4, k=1, overlap=2)
 
 
 def test_host_tables_auto_params_equal_oracle(mpm):
