@@ -496,7 +496,8 @@ def main():
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": traffic,
                          "kernel": ("mpm_scan_jit (specialised)" if st["specialised"]
-                                    else "scan_tma_kernel (generic)"),
+                                    else "scan_overlap_kernel (generic, overlapping q-grams)"
+                                    if m.params.get("overlap") else "scan_tma_kernel (generic)"),
                          "peak_kind": peak_kind, "scan_ms": scan_avg,
                          "verify_ms": verify_avg},
             "e2e": {"value": e2e_value, "unit": "GB/s", "h2d_bytes_per_step": case.n,
