@@ -149,9 +149,55 @@ def cpu_baseline(case, sample_bytes):
                       "(%.2f s, %d occurrences)" % (n >> 20, case.r, threads, dt, pos.size)}
 
 
+def run_reference_batch(args):
+    """The oracle on the batch workload: one Aho-Corasick automaton per
+    pattern set, each text searched with its set's automaton, over a bounded
+    sample of the texts (in text order) per step."""
+    from oracle import native
+    from paper_1405_5483_gb300 import workloads as W
+    b = W.config4()
+    threads = os.cpu_count() or 1
+    budget = max(4 << 20, min(args.ref_sample_mib << 20, (2 << 30) // max(1, args.steps)))
+    picked, total = [], 0
+    for t, T in enumerate(b.texts):
+        if total >= budget:
+            break
+        picked.append(t)
+        total += T.size
+    acs = {s: native.AhoCorasick(b.sets[s]) for s in sorted(set(int(b.set_of_text[t])
+                                                               for t in picked))}
+
+    def step():
+        for t in picked:
+            acs[int(b.set_of_text[t])].search(b.texts[t], threads=threads)
+
+    for _ in range(args.warmup):
+        step()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        step()
+    dt = time.perf_counter() - t0
+    value = total * args.steps / dt / 1e9
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "GB/s",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": dt * 1e3 / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "u8", "data": "synthetic",
+        "config": {"workload": "batch-4096", "texts": len(picked), "bytes": total},
+        "cpu_baseline": {"value": value, "unit": "GB/s", "cores": threads, "kind": "oracle",
+                         "sample": "the first %d texts (%d MiB), each with its set's "
+                                   "Aho-Corasick automaton over %d threads"
+                                   % (len(picked), total >> 20, threads)},
+        "e2e": {"value": value, "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+
+
 def run_reference(args, rank):
     if rank != 0:
         return
+    if args.workload == "batch-4096":
+        return run_reference_batch(args)
     case, sigma, desc = make_case(args.workload)
     # per-step sample: at most 64 MiB, and about 2 GiB over all steps, so
     # that the whole run stays within a few minutes on the host cores
