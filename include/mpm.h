@@ -153,6 +153,20 @@ mpm_handle *mpm_build(const uint8_t *P, size_t r, size_t m, int sigma,
                       const mpm_params *params);
 
 /*
+ * Patterns of different lengths (the problem of Section 1 with a length per
+ * pattern): pattern p is P[off[p] .. off[p+1]) (off has r + 1 entries,
+ * off[0] = 0, every pattern at least one byte, off[r] < 2^32).  The filter is
+ * built from the first m_min bytes of every pattern, m_min the shortest
+ * length (params as for mpm_build with m = m_min); every candidate window is
+ * verified against each pattern's full length, so an occurrence (pos, pid)
+ * is reported exactly when T[pos .. pos + len_pid) = P_pid.  P and off are
+ * host arrays, copied.  NULL on error (mpm_last_error: MPM_EINVAL for bad
+ * offsets, else as mpm_build).
+ */
+mpm_handle *mpm_build_var(const uint8_t *P, const size_t *off, size_t r, int sigma,
+                          const mpm_params *params);
+
+/*
  * Finds all occurrences in T[0..n).  T may be device or host memory (host
  * text is copied to a device buffer the handle owns).  out_pos / out_pid
  * receive the sorted occurrence list and may be device or host memory; *z is

@@ -72,7 +72,8 @@ typedef struct {
     ac_node *nodes;
     int32_t nnodes, cap;
     int32_t *pid_next;     /* pattern ids ending at the same node, a list */
-    uint64_t r, m;
+    uint64_t r, m;         /* m: the longest pattern                      */
+    uint64_t mmin;         /* the shortest pattern                        */
 } ac_automaton;
 
 static int32_t ac_child(const ac_automaton *a, int32_t v, uint8_t c)
@@ -111,13 +112,19 @@ void oracle_ac_free(void *h)
     free(a);
 }
 
-/* Builds the automaton for r patterns of length m (row-major in P). */
-void *oracle_ac_build(const uint8_t *P, uint64_t r, uint64_t m)
+/* Builds the automaton for r patterns; pattern p is P[off[p] .. off[p+1]). */
+void *oracle_ac_build_var(const uint8_t *P, const uint64_t *off, uint64_t r)
 {
     ac_automaton *a = (ac_automaton *)calloc(1, sizeof(ac_automaton));
     if (!a) return NULL;
     a->r = r;
-    a->m = m;
+    a->m = 0;
+    a->mmin = r ? (uint64_t)-1 : 0;
+    for (uint64_t p = 0; p < r; p++) {
+        const uint64_t len = off[p + 1] - off[p];
+        if (len > a->m) a->m = len;
+        if (len < a->mmin) a->mmin = len;
+    }
     a->pid_next = (int32_t *)malloc(sizeof(int32_t) * (r ? r : 1));
     if (!a->pid_next || ac_new_node(a, 0, 0) < 0) { oracle_ac_free(a); return NULL; }
 
@@ -125,8 +132,9 @@ void *oracle_ac_build(const uint8_t *P, uint64_t r, uint64_t m)
     int32_t *pid_tail = NULL;
     for (uint64_t p = 0; p < r; p++) {
         int32_t v = 0;
-        for (uint64_t j = 0; j < m; j++) {
-            uint8_t c = P[p * m + j];
+        const uint64_t len = off[p + 1] - off[p];
+        for (uint64_t j = 0; j < len; j++) {
+            uint8_t c = P[off[p] + j];
             int32_t u = ac_child(a, v, c);
             if (u < 0) {
                 u = ac_new_node(a, c, (int32_t)(j + 1));
@@ -171,6 +179,17 @@ void *oracle_ac_build(const uint8_t *P, uint64_t r, uint64_t m)
         }
     }
     free(queue);
+    return a;
+}
+
+/* Builds the automaton for r patterns of length m (row-major in P). */
+void *oracle_ac_build(const uint8_t *P, uint64_t r, uint64_t m)
+{
+    uint64_t *off = (uint64_t *)malloc(sizeof(uint64_t) * (r + 1));
+    if (!off) return NULL;
+    for (uint64_t p = 0; p <= r; p++) off[p] = p * m;
+    void *a = oracle_ac_build_var(P, off, r);
+    free(off);
     return a;
 }
 
@@ -237,13 +256,14 @@ static void *ac_job_run(void *arg)
 }
 
 /* Returns the total number of occurrences (or -1 on allocation failure) and
- * writes at most `cap` of them, sorted by (position, pattern id). */
+ * writes at most `cap` of them, sorted by (position, pattern id) when all
+ * patterns have one length (in order of their end position otherwise). */
 int64_t oracle_ac_search(void *h, const uint8_t *T, uint64_t n, int threads,
                          uint32_t *out_pos, uint32_t *out_pid, uint64_t cap)
 {
     const ac_automaton *a = (const ac_automaton *)h;
-    if (!a || a->m == 0 || n < a->m) return 0;
-    uint64_t starts = n - a->m + 1;
+    if (!a || a->mmin == 0 || n < a->mmin) return 0;
+    uint64_t starts = n - a->mmin + 1;
     if (threads < 1) threads = 1;
     if ((uint64_t)threads > starts) threads = (int)starts;
     ac_job *jobs = (ac_job *)calloc((size_t)threads, sizeof(ac_job));

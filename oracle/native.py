@@ -46,6 +46,8 @@ def _load():
                                  u32p, u32p, ctypes.c_uint64]
     lib.oracle_ac_build.restype = ctypes.c_void_p
     lib.oracle_ac_build.argtypes = [u8p, ctypes.c_uint64, ctypes.c_uint64]
+    lib.oracle_ac_build_var.restype = ctypes.c_void_p
+    lib.oracle_ac_build_var.argtypes = [u8p, ctypes.POINTER(ctypes.c_uint64), ctypes.c_uint64]
     lib.oracle_ac_search.restype = ctypes.c_int64
     lib.oracle_ac_search.argtypes = [ctypes.c_void_p, u8p, ctypes.c_uint64, ctypes.c_int,
                                      u32p, u32p, ctypes.c_uint64]
@@ -97,14 +99,33 @@ def naive(T, P, cap=None):
         cap = int(z)
 
 
+def _variable(P):
+    """A list of patterns of different lengths -> (concatenation, offsets)."""
+    rows = [np.frombuffer(bytes(p), np.uint8) for p in P]
+    off = np.zeros(len(rows) + 1, np.uint64)
+    off[1:] = np.cumsum([r.size for r in rows])
+    cat = np.concatenate(rows) if rows else np.zeros(0, np.uint8)
+    return np.ascontiguousarray(cat), off
+
+
 class AhoCorasick:
-    """Textbook Aho-Corasick automaton over bytes (Section 1.1)."""
+    """Textbook Aho-Corasick automaton over bytes (Section 1.1); P is an
+    (r, m) array or a list of patterns, which may differ in length."""
 
     def __init__(self, P):
         self._lib = _load()
-        self.P = _as_patterns(P)
-        self.r, self.m = self.P.shape
-        self._h = self._lib.oracle_ac_build(_u8(self.P), self.r, self.m)
+        self.variable = (isinstance(P, (list, tuple)) and
+                         len(set(len(bytes(p)) for p in P)) > 1)
+        if self.variable:
+            self.cat, self.off = _variable(P)
+            self.r = len(P)
+            self.m = int(min(self.off[1:] - self.off[:-1]))
+            self._h = self._lib.oracle_ac_build_var(
+                _u8(self.cat), self.off.ctypes.data_as(ctypes.POINTER(ctypes.c_uint64)), self.r)
+        else:
+            self.P = _as_patterns(P)
+            self.r, self.m = self.P.shape
+            self._h = self._lib.oracle_ac_build(_u8(self.P), self.r, self.m)
         if not self._h:
             raise MemoryError("oracle_ac_build failed")
 
@@ -125,7 +146,11 @@ class AhoCorasick:
             if z < 0:
                 raise MemoryError("oracle_ac_search failed")
             if z <= cap:
-                return pos[:z].copy(), pid[:z].copy()
+                pos, pid = pos[:z].copy(), pid[:z].copy()
+                if self.variable:  # reported in order of end position
+                    order = np.lexsort((pid, pos))
+                    pos, pid = pos[order], pid[order]
+                return pos, pid
             cap = int(z)
 
     def close(self):

@@ -120,11 +120,30 @@ class Matcher:
     """A built pattern set (mpm_build) and searches over texts (mpm_search)."""
 
     def __init__(self, P, sigma=256, **params):
-        P = _patterns(P)
-        self.r, self.m = P.shape
+        """P: an (r, m) uint8 array, or a list of byte strings, which may
+        differ in length (mpm_build_var; m is then the shortest)."""
         self.sigma = sigma
-        self._h = lib().mpm_build(P.ctypes.data, self.r, self.m, sigma,
-                                  ctypes.byref(make_params(**params)))
+        rows = None
+        if isinstance(P, (list, tuple)):
+            rows = [bytes(p) for p in P]
+            if len(set(len(x) for x in rows)) <= 1:
+                rows = None
+        if rows is None:
+            P = _patterns(P)
+            self.r, self.m = P.shape
+            self._h = lib().mpm_build(P.ctypes.data, self.r, self.m, sigma,
+                                      ctypes.byref(make_params(**params)))
+        else:
+            cat = np.frombuffer(b"".join(rows), np.uint8)
+            off = (ctypes.c_size_t * (len(rows) + 1))()
+            at = 0
+            for i, x in enumerate(rows):
+                off[i] = at
+                at += len(x)
+            off[len(rows)] = at
+            self.r, self.m = len(rows), min(len(x) for x in rows)
+            self._h = lib().mpm_build_var(cat.ctypes.data, off, self.r, sigma,
+                                          ctypes.byref(make_params(**params)))
         if not self._h:
             raise MpmError(lib().mpm_last_error(), "mpm_build")
         self._cap = max(1024, 4 * self.r)

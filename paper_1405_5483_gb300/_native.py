@@ -122,6 +122,7 @@ def lib():
     fp = ctypes.POINTER(ctypes.c_float)
     sig = {
         "mpm_build": (vp, [u8p, sz, sz, ctypes.c_int, Pp]),
+        "mpm_build_var": (vp, [u8p, ctypes.POINTER(ctypes.c_size_t), sz, ctypes.c_int, Pp]),
         "mpm_search": (ctypes.c_int, [vp, u8p, sz, vp, vp, szp]),
         "mpm_free": (None, [vp]),
         "mpm_last_error": (ctypes.c_int, []),

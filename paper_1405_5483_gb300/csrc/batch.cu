@@ -38,6 +38,7 @@ struct BatchSet {
     const Slot* slots;
     const uint8_t* pat;
     const uint32_t* pid;
+    const uint32_t* pat_off;  // row starts when the set's patterns differ in length
     const uint32_t* keys;   // bitmap of key hashes (key_bits bits), or null
     uint32_t slot_mask, key_bytes, m, table_bytes;  // table_bytes padded to 16
     int q, k, mprime, ell, shift, mode, map_kind, entry_bytes;
@@ -277,6 +278,7 @@ __global__ void __launch_bounds__(kBatchThreads, 1)
             wc.slots = S.slots;
             wc.pat = S.pat;
             wc.pid = S.pid;
+            wc.off = S.pat_off;
             wc.occ = reinterpret_cast<unsigned long long*>(occ);
             wc.occ_count = &counters[kBOcc];
             wc.tag = (unsigned long long)tl.text << kTextShift;
@@ -530,6 +532,7 @@ mpm_batch* mpm_batch_create(mpm_handle* const* sets, int nsets, const uint8_t* c
         S.slots = h->d_slots;
         S.pat = h->d_pat;
         S.pid = h->d_pid;
+        S.pat_off = h->d_pat_off;
         S.slot_mask = (uint32_t)h->host.slots.size() - 1;
         S.key_bytes = (uint32_t)h->host.key_bytes;
         // key bitmap: 64 bits per pattern group, 2^10 .. 2^19 bits

@@ -6,6 +6,7 @@
 // buffer and re-runs if one overflowed, then enqueues the sort that writes
 // the caller's outputs.
 #include <algorithm>
+#include <cstdint>
 #include <cstdio>
 #include <cstring>
 #include <mutex>
@@ -79,6 +80,7 @@ void release(mpm_handle* h) {
     cudaFree(h->d_table);
     cudaFree(h->d_slots);
     cudaFree(h->d_pat);
+    cudaFree(h->d_pat_off);
     cudaFree(h->d_pid);
     cudaFree(h->d_cand);
     cudaFree(h->d_occ);
@@ -139,6 +141,7 @@ mpm::VerifyArgs verify_args(const mpm_handle* h, const uint8_t* dT, uint32_t n,
     v.slot_mask = (uint32_t)h->host.slots.size() - 1;
     v.pat = h->d_pat;
     v.pid = h->d_pid;
+    v.pat_off = h->d_pat_off;
     v.key_bytes = h->host.key_bytes;
     v.occ = occ;
     v.occ_cap = occ_cap;
@@ -333,7 +336,11 @@ const char* mpm_strerror(int code) {
     }
 }
 
-mpm_handle* mpm_build(const uint8_t* P, size_t r, size_t m, int sigma, const mpm_params* params) {
+// P: r x m (the filter's patterns).  full/off (may be null): the patterns
+// themselves when they differ in length, pattern p = full[off[p] .. off[p+1]),
+// P holding their first m bytes.
+static mpm_handle* build_handle(const uint8_t* P, size_t r, size_t m, int sigma,
+                                const mpm_params* params, const uint8_t* full, const size_t* off) {
     mpm_handle* h = new (std::nothrow) mpm_handle();
     if (!h) {
         set_error(MPM_ENOMEM);
@@ -362,7 +369,10 @@ mpm_handle* mpm_build(const uint8_t* P, size_t r, size_t m, int sigma, const mpm
         h->table_bytes_padded = (uint32_t)((h->plan.info.table_bytes + 15) & ~uint64_t(15));
         h->host.table.assign(h->table_bytes_padded, 0xFF);
         mpm::make_mask_table(P, h->plan, h->host.mu, h->host.table.data());
-        mpm::make_verify_tables(P, r, m, &h->host);
+        if (full)
+            mpm::make_verify_tables_var(full, off, r, m, &h->host);
+        else
+            mpm::make_verify_tables(P, r, m, &h->host);
     } catch (const std::bad_alloc&) {
         delete h;
         set_error(MPM_ENOMEM);
@@ -381,6 +391,8 @@ mpm_handle* mpm_build(const uint8_t* P, size_t r, size_t m, int sigma, const mpm
               cudaMalloc(&h->d_slots, h->host.slots.size() * sizeof(mpm::Slot)) == cudaSuccess &&
               cudaMalloc(&h->d_pat, h->host.sorted_pat.size()) == cudaSuccess &&
               cudaMalloc(&h->d_pid, h->host.sorted_pid.size() * 4) == cudaSuccess &&
+              (h->host.sorted_off.empty() ||
+               cudaMalloc(&h->d_pat_off, h->host.sorted_off.size() * 4) == cudaSuccess) &&
               cudaMalloc(&h->d_counters, mpm::kNumCounters * 4) == cudaSuccess &&
               cudaMemset(h->d_counters, 0, mpm::kNumCounters * 4) == cudaSuccess &&
               cudaMallocHost(&h->h_counters, mpm::kNumCounters * 4) == cudaSuccess &&
@@ -394,7 +406,10 @@ mpm_handle* mpm_build(const uint8_t* P, size_t r, size_t m, int sigma, const mpm
          cudaMemcpy(h->d_pat, h->host.sorted_pat.data(), h->host.sorted_pat.size(),
                     cudaMemcpyHostToDevice) == cudaSuccess &&
          cudaMemcpy(h->d_pid, h->host.sorted_pid.data(), h->host.sorted_pid.size() * 4,
-                    cudaMemcpyHostToDevice) == cudaSuccess;
+                    cudaMemcpyHostToDevice) == cudaSuccess &&
+         (h->host.sorted_off.empty() ||
+          cudaMemcpy(h->d_pat_off, h->host.sorted_off.data(), h->host.sorted_off.size() * 4,
+                     cudaMemcpyHostToDevice) == cudaSuccess);
     if (!ok) {
         cudaGetLastError();
         release(h);
@@ -422,6 +437,42 @@ mpm_handle* mpm_build(const uint8_t* P, size_t r, size_t m, int sigma, const mpm
     }
     set_error(MPM_OK);
     return h;
+}
+
+mpm_handle* mpm_build(const uint8_t* P, size_t r, size_t m, int sigma, const mpm_params* params) {
+    return build_handle(P, r, m, sigma, params, nullptr, nullptr);
+}
+
+mpm_handle* mpm_build_var(const uint8_t* P, const size_t* off, size_t r, int sigma,
+                          const mpm_params* params) {
+    if (!P || !off || r == 0 || off[0] != 0) {
+        set_error(MPM_EINVAL);
+        return nullptr;
+    }
+    size_t mmin = SIZE_MAX, mmax = 0;
+    for (size_t p = 0; p < r; p++) {
+        if (off[p + 1] <= off[p]) {  // every pattern at least one byte
+            set_error(MPM_EINVAL);
+            return nullptr;
+        }
+        mmin = std::min(mmin, off[p + 1] - off[p]);
+        mmax = std::max(mmax, off[p + 1] - off[p]);
+    }
+    if (off[r] >= (1ull << 32)) {
+        set_error(MPM_EINVAL);
+        return nullptr;
+    }
+    // the filter runs on the first mmin bytes of every pattern
+    std::vector<uint8_t> prefix;
+    try {
+        prefix.resize(r * mmin);
+    } catch (const std::bad_alloc&) {
+        set_error(MPM_ENOMEM);
+        return nullptr;
+    }
+    for (size_t p = 0; p < r; p++) std::memcpy(&prefix[p * mmin], P + off[p], mmin);
+    if (mmin == mmax) return build_handle(prefix.data(), r, mmin, sigma, params, nullptr, nullptr);
+    return build_handle(prefix.data(), r, mmin, sigma, params, P, off);
 }
 
 void mpm_free(mpm_handle* h) { release(h); }

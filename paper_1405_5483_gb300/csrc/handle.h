@@ -17,6 +17,7 @@ struct mpm_handle {
     uint32_t table_bytes_padded = 0;
     mpm::Slot* d_slots = nullptr;
     uint8_t* d_pat = nullptr;
+    uint32_t* d_pat_off = nullptr;  // row starts when the patterns differ in length
     uint32_t* d_pid = nullptr;
 
     // scratch, grown on demand

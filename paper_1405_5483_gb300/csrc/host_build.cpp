@@ -15,6 +15,7 @@
 //                probability allows; this file scores a small grid with an
 //                estimate of that probability instead of a closed form).
 #include <algorithm>
+#include <functional>
 #include <cmath>
 #include <cstring>
 #include <numeric>
@@ -475,32 +476,22 @@ int make_mask_table(const uint8_t* P, const Plan& plan, const uint8_t mu[256],
     return MPM_OK;
 }
 
-int make_verify_tables(const uint8_t* P, size_t r, size_t m, HostTables* out) {
-    std::vector<uint32_t> idx(r);
-    std::iota(idx.begin(), idx.end(), 0u);
-    std::stable_sort(idx.begin(), idx.end(), [&](uint32_t a, uint32_t b) {
-        return std::memcmp(P + (size_t)a * m, P + (size_t)b * m, m) < 0;
-    });
-    out->sorted_pat.resize(r * m);
-    out->sorted_pid.resize(r);
-    for (size_t i = 0; i < r; i++) {
-        std::memcpy(&out->sorted_pat[i * m], P + (size_t)idx[i] * m, m);
-        out->sorted_pid[i] = idx[i];
-    }
-    const int kb = (int)std::min<size_t>(m, 16);
+namespace {
+
+// The open-addressing table of pattern groups: rows with equal first kb
+// bytes are contiguous in lexicographic order and form one group.
+void build_slots(HostTables* out, size_t r, int kb, const std::function<const uint8_t*(size_t)>& row) {
     out->key_bytes = kb;
-    auto key_of = [&](size_t row, uint64_t* lo, uint64_t* hi) {
+    auto key_of = [&](size_t i, uint64_t* lo, uint64_t* hi) {
         uint8_t buf[16] = {0};
-        std::memcpy(buf, &out->sorted_pat[row * m], kb);
+        std::memcpy(buf, row(i), kb);
         std::memcpy(lo, buf, 8);
         std::memcpy(hi, buf + 8, 8);
     };
-    // groups of equal keys are contiguous in lexicographic order
     std::vector<std::pair<size_t, size_t>> groups;
     for (size_t i = 0; i < r;) {
         size_t j = i + 1;
-        while (j < r && std::memcmp(&out->sorted_pat[i * m], &out->sorted_pat[j * m], kb) == 0)
-            j++;
+        while (j < r && std::memcmp(row(i), row(j), kb) == 0) j++;
         groups.push_back({i, j - i});
         i = j;
     }
@@ -514,6 +505,52 @@ int make_verify_tables(const uint8_t* P, size_t r, size_t m, HostTables* out) {
         while (out->slots[s].count) s = (s + 1) & (nslots - 1);
         out->slots[s] = Slot{lo, hi, (uint32_t)g.first, (uint32_t)g.second};
     }
+}
+
+}  // namespace
+
+int make_verify_tables(const uint8_t* P, size_t r, size_t m, HostTables* out) {
+    std::vector<uint32_t> idx(r);
+    std::iota(idx.begin(), idx.end(), 0u);
+    std::stable_sort(idx.begin(), idx.end(), [&](uint32_t a, uint32_t b) {
+        return std::memcmp(P + (size_t)a * m, P + (size_t)b * m, m) < 0;
+    });
+    out->sorted_pat.resize(r * m);
+    out->sorted_pid.resize(r);
+    out->sorted_off.clear();
+    for (size_t i = 0; i < r; i++) {
+        std::memcpy(&out->sorted_pat[i * m], P + (size_t)idx[i] * m, m);
+        out->sorted_pid[i] = idx[i];
+    }
+    const int kb = (int)std::min<size_t>(m, 16);
+    build_slots(out, r, kb, [&](size_t i) { return &out->sorted_pat[i * m]; });
+    return MPM_OK;
+}
+
+int make_verify_tables_var(const uint8_t* cat, const size_t* off, size_t r, size_t mmin,
+                           HostTables* out) {
+    std::vector<uint32_t> idx(r);
+    std::iota(idx.begin(), idx.end(), 0u);
+    auto less = [&](uint32_t a, uint32_t b) {
+        const size_t la = off[a + 1] - off[a], lb = off[b + 1] - off[b];
+        const int c = std::memcmp(cat + off[a], cat + off[b], std::min(la, lb));
+        return c != 0 ? c < 0 : la < lb;
+    };
+    std::stable_sort(idx.begin(), idx.end(), less);
+    out->sorted_pat.resize(off[r]);
+    out->sorted_pid.resize(r);
+    out->sorted_off.resize(r + 1);
+    size_t at = 0;
+    for (size_t i = 0; i < r; i++) {
+        const size_t len = off[idx[i] + 1] - off[idx[i]];
+        out->sorted_off[i] = (uint32_t)at;
+        std::memcpy(&out->sorted_pat[at], cat + off[idx[i]], len);
+        out->sorted_pid[i] = idx[i];
+        at += len;
+    }
+    out->sorted_off[r] = (uint32_t)at;
+    const int kb = (int)std::min<size_t>(mmin, 16);
+    build_slots(out, r, kb, [&](size_t i) { return &out->sorted_pat[out->sorted_off[i]]; });
     return MPM_OK;
 }
 

@@ -396,6 +396,7 @@ int launch_scan_jit(const ScanArgs& A, const VerifyArgs* V, const JitKernel* K, 
         J.slots = V->slots;
         J.pat = V->pat;
         J.pid = V->pid;
+        J.pat_off = V->pat_off;
         J.occ = reinterpret_cast<unsigned long long*>(V->occ);
         J.slot_mask = V->slot_mask;
         J.key_bytes = (uint32_t)V->key_bytes;

@@ -54,8 +54,9 @@ struct VerifyArgs {
     uint32_t cand_cap;
     const Slot* slots;
     uint32_t slot_mask;
-    const uint8_t* pat;   // sorted patterns, r * m
+    const uint8_t* pat;   // sorted patterns, r * m (or concatenated, see pat_off)
     const uint32_t* pid;  // pattern id of each sorted row
+    const uint32_t* pat_off;  // row starts when the patterns differ in length, else null
     int key_bytes;
     uint64_t* occ;        // (pos << 32) | pid
     uint32_t occ_cap;

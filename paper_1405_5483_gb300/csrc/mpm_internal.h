@@ -41,6 +41,7 @@ struct HostTables {
     std::vector<Slot> slots;         // power of two
     std::vector<uint8_t> sorted_pat; // r * m, patterns in lexicographic order
     std::vector<uint32_t> sorted_pid;
+    std::vector<uint32_t> sorted_off; // patterns of different lengths: row starts (r + 1)
     int key_bytes;                   // min(m, 16)
 };
 
@@ -53,5 +54,9 @@ void make_mu(const uint8_t* P, size_t r, size_t m, int kind, int sigma_r, int sh
 int make_mask_table(const uint8_t* P, const Plan& plan, const uint8_t mu[256],
                     uint8_t* table);
 int make_verify_tables(const uint8_t* P, size_t r, size_t m, HostTables* out);
+// Patterns of different lengths: pattern p is cat[off[p] .. off[p+1]), the
+// shortest mmin bytes long; keys are their first min(mmin, 16) bytes.
+int make_verify_tables_var(const uint8_t* cat, const size_t* off, size_t r, size_t mmin,
+                           HostTables* out);
 
 }  // namespace mpm

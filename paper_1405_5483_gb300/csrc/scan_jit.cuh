@@ -169,6 +169,7 @@ __device__ __forceinline__ WindowCtx window_ctx(const JitScanArgs& A) {
     c.slots = reinterpret_cast<const Slot*>(A.slots);
     c.pat = A.pat;
     c.pid = A.pid;
+    c.off = A.pat_off;
     c.occ = A.occ;
     c.occ_count = &A.counters[kOccCountJ];
     c.tag = 0;

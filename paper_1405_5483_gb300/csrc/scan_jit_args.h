@@ -25,6 +25,7 @@ struct JitScanArgs {
     const void* slots;            // open-addressing table of pattern groups
     const unsigned char* pat;     // patterns sorted by bytes, r * m
     const unsigned int* pid;      // pattern id of each sorted row
+    const unsigned int* pat_off;  // row starts for patterns of different lengths, or null
     unsigned long long* occ;      // occurrences (pos << 32) | pid
     unsigned int slot_mask;
     unsigned int key_bytes;       // min(m, 16)

@@ -32,6 +32,7 @@ __global__ void __launch_bounds__(256) verify_kernel(const VerifyArgs A) {
     wc.slots = A.slots;
     wc.pat = A.pat;
     wc.pid = A.pid;
+    wc.off = A.pat_off;
     wc.occ = reinterpret_cast<unsigned long long*>(A.occ);
     wc.occ_count = &A.counters[kOccCount];
     wc.tag = 0;

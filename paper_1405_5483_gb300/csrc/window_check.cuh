@@ -12,6 +12,8 @@ struct WindowCtx {
     const Slot* slots;
     const unsigned char* pat;     // patterns sorted by bytes, r * m
     const unsigned int* pid;      // pattern id of each sorted row
+    const unsigned int* off;      // null: rows of m bytes; else row i is
+                                  // pat[off[i] .. off[i+1]) (lengths >= m)
     unsigned long long* occ;      // tag | (pos << pos_shift) | pid
     unsigned int* occ_count;
     unsigned long long tag;       // 0 for one text; the text id's bits in a batch
@@ -62,7 +64,8 @@ __device__ __forceinline__ void window_key(const WindowCtx& c, unsigned int i,
 
 // Looks the window T[i..i+m), whose key is (lo, hi) and key hash h, up
 // among the pattern groups and appends tag | (i << pos_shift) | pid for
-// every pattern equal to it.
+// every pattern equal to the text there (for patterns of different lengths,
+// each compared over its own length; m is then the shortest).
 static __device__ __forceinline__ void probe_window(const WindowCtx& c, unsigned int i,
                                                     unsigned long long lo, unsigned long long hi,
                                                     unsigned long long h) {
@@ -73,10 +76,19 @@ static __device__ __forceinline__ void probe_window(const WindowCtx& c, unsigned
         if (sl.lo == lo && sl.hi == hi) {
             const unsigned char* w = c.T + i;
             for (unsigned int row = sl.first; row < sl.first + sl.count; row++) {
-                const unsigned char* p = c.pat + (unsigned long long)row * c.m;
+                const unsigned char* p;
+                unsigned int len;
+                if (c.off) {  // patterns of different lengths: each its own
+                    p = c.pat + c.off[row];
+                    len = c.off[row + 1] - c.off[row];
+                    if ((unsigned long long)i + len > c.n) continue;
+                } else {
+                    p = c.pat + (unsigned long long)row * c.m;
+                    len = c.m;
+                }
                 unsigned int u = c.key_bytes;
-                while (u < c.m && __ldg(w + u) == __ldg(p + u)) u++;
-                if (u == c.m) {
+                while (u < len && __ldg(w + u) == __ldg(p + u)) u++;
+                if (u == len) {
                     const unsigned int idx = atomicAdd(c.occ_count, 1u);
                     if (idx < c.occ_cap)
                         c.occ[idx] = c.tag | ((unsigned long long)i << c.pos_shift) | c.pid[row];

@@ -466,3 +466,20 @@ def test_overlap_scan_equals_definition_and_search_equals_brute_force():
         assert got == sorted(brute.occurrences(T, P))
         # no false negatives: every occurrence is a candidate window
         assert {i for i, _ in got} <= set(windows)
+
+
+def test_aho_corasick_variable_lengths_equals_brute_force():
+    from oracle import native
+    native.build()
+    rng = random.Random(81)
+    for _ in range(300):
+        alpha = "ab" if rng.random() < 0.5 else "abcd"
+        T = "".join(rng.choice(alpha) for _ in range(rng.randint(0, 60))).encode()
+        P = ["".join(rng.choice(alpha) for _ in range(rng.randint(1, 7))).encode()
+             for _ in range(rng.randint(1, 6))]
+        if rng.random() < 0.3:
+            P.append(P[0])   # a duplicate
+        want = brute.occurrences(T, P)
+        for threads in (1, 3):
+            pos, pid = native.AhoCorasick(P).search(np.frombuffer(T, np.uint8), threads=threads)
+            assert list(zip(pos.tolist(), pid.tolist())) == want
