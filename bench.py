@@ -34,6 +34,9 @@ WORKLOADS = {
     "dna-1GiB": ("config1_scaled", 4,
                  "uniform DNA text 1 GiB, r=100, m=16, half planted (config-1 shape at scale)"),
     "dna-1MiB": ("config1", 4, "uniform DNA text 1 MiB, r=100, m=16, half planted"),
+    "protein-256MiB-varlen": ("config2_varlen", 20,
+                              "protein-like text 256 MiB, r=1000 patterns of lengths 16..64, "
+                              "half planted (filter on the 16-byte prefixes)"),
 }
 
 
@@ -415,7 +418,10 @@ def main():
         # exhaustive autotuner on a sample of the text; not timed, like the build
         sample = T[: min(case.n, args.tune_sample_mib << 20)]
         t0 = time.perf_counter()
-        params, sets = mpm.autotune(case.P, sigma, sample, kernels=3, max_sets=args.tune_sets)
+        # patterns of different lengths: the filter's parameters are tuned on
+        # their common-length prefixes
+        params, sets = mpm.autotune(case.prefix_matrix(), sigma, sample, kernels=3,
+                                    max_sets=args.tune_sets)
         tuning = {"sample_bytes": int(sample.numel()), "sets_timed": len(sets),
                   "seconds": round(time.perf_counter() - t0, 2)}
     m = mpm.Matcher(case.P, sigma=sigma, **params)

@@ -96,7 +96,8 @@ def make_patterns(text, source, r, m, planted, rng):
 
 
 class Case:
-    """One search problem: text T (uint8[n]) and patterns P (uint8[r, m])."""
+    """One search problem: text T (uint8[n]) and patterns P (uint8[r, m], or
+    a list of byte strings of different lengths)."""
 
     def __init__(self, name, T, P, sigma, planted_offsets, source):
         self.name, self.T, self.P, self.sigma = name, T, P, sigma
@@ -104,16 +105,28 @@ class Case:
         self.source = source
 
     @property
+    def variable(self):
+        return isinstance(self.P, list)
+
+    @property
     def n(self):
         return int(self.T.size)
 
     @property
     def r(self):
-        return int(self.P.shape[0])
+        return len(self.P) if self.variable else int(self.P.shape[0])
 
     @property
     def m(self):
-        return int(self.P.shape[1])
+        """The pattern length (the shortest one for variable lengths)."""
+        return min(len(p) for p in self.P) if self.variable else int(self.P.shape[1])
+
+    def prefix_matrix(self):
+        """uint8[r, m]: every pattern's first m bytes."""
+        if not self.variable:
+            return self.P
+        m = self.m
+        return np.stack([np.frombuffer(p[:m], np.uint8) for p in self.P])
 
 
 def dna_case(n, r, m, planted, cfg=1, name=None):
@@ -152,6 +165,26 @@ def config1_scaled(n=1 << 30):
 def config2(n=1 << 28):
     """Protein-like, n = 2^28, r = 1000, m = 32, half planted."""
     return protein_case(n, 1000, 32, 500, cfg=2, name="protein-%dMiB r=1000 m=32" % (n >> 20))
+
+
+def config2_varlen(n=1 << 28, r=1000, lo=16, hi=64):
+    """Config 2's text with patterns of different lengths: r patterns with
+    lengths uniform over [lo, hi], half planted (text seed 1002, pattern
+    seed 2102)."""
+    src = protein_source()
+    T = src.draw(n, np.random.default_rng(1000 + 2))
+    rng = np.random.default_rng(2100 + 2)
+    P, offs = [], []
+    for i in range(r):
+        L = int(rng.integers(lo, hi + 1))
+        if i < r // 2:
+            o = int(rng.integers(0, n - L + 1))
+            P.append(T[o:o + L].tobytes())
+            offs.append(o)
+        else:
+            P.append(src.draw(L, rng).tobytes())
+    return Case("protein-%dMiB r=%d m=%d..%d" % (n >> 20, r, lo, hi), T, P, 20,
+                np.array(offs, np.int64), src)
 
 
 def config3(n=1 << 30, r=100_000, m=32):
