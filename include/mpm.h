@@ -305,6 +305,10 @@ int mpm_scan(mpm_handle *h, const uint8_t *T, size_t n, uint64_t *cand,
  * device.  The handles and texts must outlive the batch.  Occurrences are
  * reported as (text index, position, pattern id), sorted in that order.
  *
+ * Mask tables of at most MPM_BATCH_SMEM_TABLE_BYTES are read from shared
+ * memory by the batched kernel, larger ones from L2 (where, next to the text
+ * stream of a large batch, they are often evicted).
+ *
  * mpm_batch_create cuts every text into tiles of up to 32 lanes x lane_bytes
  * (each lane's share a multiple of lcm(k*q, 4) for its set), groups the
  * tiles of each set into work units, builds per-set device descriptors
@@ -320,11 +324,13 @@ int mpm_scan(mpm_handle *h, const uint8_t *T, size_t n, uint64_t *cand,
  */
 typedef struct mpm_batch mpm_batch;
 
+#define MPM_BATCH_SMEM_TABLE_BYTES (128u << 10)
+
 typedef struct {
     int lane_bytes;  /* text bytes per lane of a tile; 0 = 512 */
     int no_graph;    /* 1: launch the kernels on every run instead of a graph */
     int unit_kib;    /* estimated cost of a work unit, in KiB of scanned text
-                        (verification counted as extra bytes); 0 = 512 */
+                        (verification counted as extra bytes); 0 = 1024 */
 } mpm_batch_opts;
 
 typedef struct {
@@ -367,7 +373,9 @@ typedef struct {
     int max_positions;   /* only sets with at most this many filter positions
                             (32 for mpm_batch); 0 = 64                              */
     int grid;            /* 0: the tuner's grid above; 1: every point of the cost
-                            model's grid (mpm_model_grid), nothing dropped          */
+                            model's grid (mpm_model_grid)                          */
+    int max_table_kib;   /* only sets whose mask table has at most this many KiB;
+                            0 = 16384                                               */
 } mpm_tune_opts;
 
 typedef struct {
@@ -477,11 +485,14 @@ int mpm_model_grid(const uint8_t *P, size_t r, size_t m, int sigma, int max_posi
  * log10 r, log2 n, q, log2 sigma', k].  Host only. */
 int mpm_model_features(int sigma, double entropy, size_t m, size_t r, size_t n,
                        const mpm_params *params, size_t count, float *X);
-/* The grid point (at most 32 positions: the batched kernel's limit) with the
+/* The grid point (at most 32 positions: the batched kernel's limit; a mask
+ * table of at most max_table_bytes, 0 = no limit beyond the grid's) with the
  * smallest predicted time for a pattern set searched in texts of n bytes
- * whose symbol entropy is `entropy` bits.  *pred receives its ln(ms). */
+ * whose symbol entropy is `entropy` bits.  *pred receives its ln(ms).
+ * MPM_EINVAL when no grid point qualifies. */
 int mpm_model_choose(mpm_model *model, const uint8_t *P, size_t r, size_t m, int sigma,
-                     double entropy, size_t n, mpm_params *best, float *pred);
+                     double entropy, size_t n, size_t max_table_bytes, mpm_params *best,
+                     float *pred);
 
 /* ------------------------------------------- search that allocates nothing */
 

@@ -79,13 +79,14 @@ def host_tables(P, sigma, **kw):
 
 
 def autotune(P, sigma, T, max_q=0, max_k=0, reps=0, kernels=0, max_sets=0, max_rate=0.0,
-             max_positions=0, grid=0):
+             max_positions=0, grid=0, max_table_kib=0):
     """Exhaustive parameter search timed on the sample text T (CUDA tensor or
     numpy).  grid=1 times every point of the cost model's grid.  Returns
     (best params dict, list of timed sets)."""
     from ._native import TuneEntry, TuneOpts
     P = _patterns(P)
-    opts = TuneOpts(max_q, max_k, reps, kernels, max_sets, max_rate, max_positions, grid)
+    opts = TuneOpts(max_q, max_k, reps, kernels, max_sets, max_rate, max_positions, grid,
+                    max_table_kib)
     cap = 4096
     entries = (TuneEntry * cap)()
     best = Params()

@@ -54,10 +54,11 @@ class TuneOpts(ctypes.Structure):
     _fields_ = [("max_q", ctypes.c_int), ("max_k", ctypes.c_int), ("reps", ctypes.c_int),
                 ("kernels", ctypes.c_int), ("max_sets", ctypes.c_int),
                 ("max_rate", ctypes.c_double), ("max_positions", ctypes.c_int),
-                ("grid", ctypes.c_int)]
+                ("grid", ctypes.c_int), ("max_table_kib", ctypes.c_int)]
 
 
 MODEL_INPUTS, MODEL_HIDDEN, MODEL_PARAMS = 8, 64, 4801
+BATCH_SMEM_TABLE_BYTES = 128 << 10
 
 
 class TrainOpts(ctypes.Structure):
@@ -170,7 +171,7 @@ def lib():
         "mpm_model_features": (ctypes.c_int, [ctypes.c_int, ctypes.c_double, sz, sz, sz, Pp, sz,
                                               fp]),
         "mpm_model_choose": (ctypes.c_int, [vp, u8p, sz, sz, ctypes.c_int, ctypes.c_double, sz,
-                                            Pp, fp]),
+                                            sz, Pp, fp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(L, name)

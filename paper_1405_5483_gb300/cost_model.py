@@ -199,14 +199,16 @@ class Model:
                                      ctypes.byref(opts), _fptr(losses)), "mpm_model_train")
         return losses
 
-    def choose(self, P, sigma, entropy, n):
-        """Grid point with the smallest predicted time: (params dict, ln ms)."""
+    def choose(self, P, sigma, entropy, n, max_table_bytes=0):
+        """Grid point with the smallest predicted time among those whose mask
+        table has at most max_table_bytes (0: any): (params dict, ln ms)."""
         P = np.ascontiguousarray(np.asarray(P, dtype=np.uint8))
         best = Params()
         pred = ctypes.c_float()
         _check(lib().mpm_model_choose(self._h, P.ctypes.data, P.shape[0], P.shape[1], sigma,
-                                      float(entropy), int(n), ctypes.byref(best),
-                                      ctypes.byref(pred)), "mpm_model_choose")
+                                      float(entropy), int(n), int(max_table_bytes),
+                                      ctypes.byref(best), ctypes.byref(pred)),
+               "mpm_model_choose")
         return best.as_dict(), pred.value
 
 

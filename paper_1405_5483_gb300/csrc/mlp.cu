@@ -738,14 +738,20 @@ int mpm_model_features(int sigma, double entropy, size_t m, size_t r, size_t n,
 }
 
 int mpm_model_choose(mpm_model* md, const uint8_t* P, size_t r, size_t m, int sigma,
-                     double entropy, size_t n, mpm_params* best, float* pred) {
+                     double entropy, size_t n, size_t max_table_bytes, mpm_params* best,
+                     float* pred) {
     if (!md || !P || !best || n == 0) return set_error(MPM_EINVAL);
     size_t count = 0;
     int rc = mpm_model_grid(P, r, m, sigma, 32, nullptr, nullptr, 0, &count);
     if (rc) return set_error(rc);
+    std::vector<mpm_params> all(count);
+    std::vector<mpm_table_info> info(count);
+    mpm_model_grid(P, r, m, sigma, 32, all.data(), info.data(), count, &count);
+    std::vector<mpm_params> grid;
+    for (size_t i = 0; i < count; i++)
+        if (max_table_bytes == 0 || info[i].table_bytes <= max_table_bytes) grid.push_back(all[i]);
+    count = grid.size();
     if (count == 0) return set_error(MPM_EINVAL);
-    std::vector<mpm_params> grid(count);
-    mpm_model_grid(P, r, m, sigma, 32, grid.data(), nullptr, count, &count);
     std::vector<float> X(count * NI), y(count);
     if ((rc = mpm_model_features(sigma, entropy, m, r, n, grid.data(), count, X.data())) ||
         (rc = mpm_model_predict(md, X.data(), count, y.data())))

@@ -98,6 +98,9 @@ extern "C" int mpm_autotune(const uint8_t* P, size_t r, size_t m, int sigma, con
     const size_t max_sets = o.max_sets > 0 ? (size_t)o.max_sets : 64;
     const double max_rate = o.max_rate > 0 ? o.max_rate : 0.05;
     const int max_positions = o.max_positions > 0 ? o.max_positions : 64;
+    const uint64_t max_table =
+        o.max_table_kib > 0 ? std::min<uint64_t>((uint64_t)o.max_table_kib << 10, kTuneMaxTable)
+                            : kTuneMaxTable;
 
     // the pattern alphabet bounds sigma'
     bool seen[256] = {false};
@@ -118,6 +121,7 @@ extern "C" int mpm_autotune(const uint8_t* P, size_t r, size_t m, int sigma, con
         std::vector<mpm::Plan> plans;
         model_grid(P, r, m, sigma_eff, max_positions, &plans);
         for (const auto& pl : plans) {
+            if (pl.info.table_bytes > max_table) continue;
             Candidate c;
             c.plan = pl;
             c.p = pl.p;
@@ -137,7 +141,7 @@ extern "C" int mpm_autotune(const uint8_t* P, size_t r, size_t m, int sigma, con
         if (mpm::make_plan(P, r, m, sigma_eff, &p, &best_k, &all) != MPM_OK) return;
         for (const auto& pl : all) {
             if (pl.p.k > max_k) continue;
-            if (pl.info.table_bytes > kTuneMaxTable) continue;
+            if (pl.info.table_bytes > max_table) continue;
             if (pl.info.positions > max_positions) continue;
             if (pl.info.est_candidate_rate > max_rate) continue;
             Candidate c;
