@@ -149,6 +149,10 @@ __device__ void batch_lane(const BatchSet& S, const ET* tab, const uint8_t* smu,
     for (uint32_t w0 = 0; w0 < wmax; w0 += 8) {
         uint32_t x[8];
         const uint32_t at0 = a + 4 * w0;
+        // the lane's sector four blocks ahead (inside the text: at0 + 160 <= b + 3),
+        // into L2 while this one is scanned
+        if (w0 + 40 <= words)
+            asm volatile("prefetch.global.L2 [%0];" ::"l"(tx.T + at0 + 128));
         if (vec && w0 + 8 <= words && at0 + 32 <= tx.n) {
             const uint4 lo = __ldg(reinterpret_cast<const uint4*>(tx.T + at0));
             const uint4 hi = __ldg(reinterpret_cast<const uint4*>(tx.T + at0 + 16));
