@@ -458,6 +458,7 @@ def main():
             ev0.record(stream)
             for i in range(steps):
                 m.search_async(T, out_pos, out_pid, status[i])
+            m.join()  # the last searches' closing sorts belong to the timed region
             ev1.record(stream)
             barrier()
         m.sync()

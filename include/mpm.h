@@ -220,16 +220,24 @@ int mpm_set_timing(mpm_handle *h, int on);
  * of the device work (MPM_ETIMEOUT), status[3] = 1 when out_pos/out_pid hold
  * all z occurrences sorted by (pos, pid); status[3] = 0 when they could not
  * (z > cap, z > 4096, an internal buffer too small, or an error): then run
- * mpm_search for this text, which grows what it needs.  Calls on one handle
- * run in stream order and share its buffers; outputs of a call are
- * overwritten by later calls that use the same arrays.  Host-side argument
- * errors return MPM_EINVAL; nothing is enqueued then.  With timing on, each
- * call's scan and verification times are added to the statistics.
+ * mpm_search for this text, which grows what it needs.  Successive calls
+ * alternate between two internal buffer sets: the scan runs on the handle's
+ * stream and the closing sort on an internal stream after it, overlapping the
+ * next call's scan, so the outputs and status of a call are complete on the
+ * handle's stream only after mpm_join (or mpm_sync, or any synchronous call).
+ * Outputs of a call are overwritten by later calls that use the same arrays.
+ * Host-side argument errors return MPM_EINVAL; nothing is enqueued then.
+ * With timing on, each call's scan and verification times are added to the
+ * statistics.
  */
 int mpm_search_async(mpm_handle *h, const uint8_t *T, size_t n, uint32_t *out_pos,
                      uint32_t *out_pid, size_t cap, uint32_t *status);
-/* Waits until the handle's stream is idle and completes the statistics of
- * pipelined searches. */
+/* Orders all later work on the handle's stream after the pipelined searches
+ * enqueued so far (their outputs and status included), without waiting on
+ * the host. */
+int mpm_join(mpm_handle *h);
+/* mpm_join, then waits until the handle's stream is idle and completes the
+ * statistics of pipelined searches. */
 int mpm_sync(mpm_handle *h);
 /* Clears the statistics (waiting for timed pipelined searches in flight). */
 int mpm_reset_stats(mpm_handle *h);

@@ -212,8 +212,13 @@ class Matcher:
         if rc:
             raise MpmError(rc, "mpm_search_async")
 
+    def join(self):
+        """Orders later work on the handle's stream after the pipelined
+        searches so far (mpm_join)."""
+        self._check(lib().mpm_join(self._h), "mpm_join")
+
     def sync(self):
-        """Waits for the handle's stream (mpm_sync)."""
+        """Waits for the handle's stream and the pipelined searches (mpm_sync)."""
         self._check(lib().mpm_sync(self._h), "mpm_sync")
 
     def reset_stats(self):

@@ -139,6 +139,7 @@ def lib():
         "mpm_search_noalloc": (ctypes.c_int, [vp, u8p, sz, vp, vp, szp]),
         "mpm_search_async": (ctypes.c_int, [vp, u8p, sz, vp, vp, sz, vp]),
         "mpm_sync": (ctypes.c_int, [vp]),
+        "mpm_join": (ctypes.c_int, [vp]),
         "mpm_reset_stats": (ctypes.c_int, [vp]),
         "mpm_batch_create": (vp, [ctypes.POINTER(vp), ctypes.c_int, ctypes.POINTER(vp),
                                   ctypes.POINTER(ctypes.c_size_t), ctypes.POINTER(ctypes.c_uint32),

@@ -89,6 +89,17 @@ void release(mpm_handle* h) {
     cudaFree(h->d_counters);
     if (h->h_counters) cudaFreeHost(h->h_counters);
     if (h->h_snap) cudaFreeHost(h->h_snap);
+    if (h->side) {
+        cudaStreamSynchronize(h->side);
+        cudaStreamDestroy(h->side);
+    }
+    for (int b = 0; b < 2; b++) {
+        if (h->scan_done[b]) cudaEventDestroy(h->scan_done[b]);
+        if (h->sort_done[b]) cudaEventDestroy(h->sort_done[b]);
+    }
+    cudaFree(h->d_cand1);
+    cudaFree(h->d_occ1);
+    cudaFree(h->d_counters1);
     for (auto& trio : h->ring)
         for (auto& e : trio)
             if (e) cudaEventDestroy(e);
@@ -288,6 +299,20 @@ int next_timing_slot(mpm_handle* h, cudaEvent_t** ev) {
     return MPM_OK;
 }
 
+// Orders everything enqueued on the handle's stream from now on after the
+// closing sorts of pipelined searches still running on the side stream.
+int join_sorts(mpm_handle* h) {
+    for (int b = 0; b < 2; b++) {
+        if (!h->sort_pending[b]) continue;
+        if (cudaStreamWaitEvent(h->stream, h->sort_done[b], 0) != cudaSuccess) {
+            cudaGetLastError();
+            return MPM_ECUDA;
+        }
+        h->sort_pending[b] = false;
+    }
+    return MPM_OK;
+}
+
 // The end of a search closed by the rank sort kernel: wait for the stream and
 // take the counters from the mapped snapshot.
 int finish_counters(mpm_handle* h) {
@@ -480,7 +505,8 @@ void mpm_free(mpm_handle* h) { release(h); }
 int mpm_set_stream(mpm_handle* h, void* stream) {
     if (!h) return set_error(MPM_EINVAL);
     h->stream = reinterpret_cast<cudaStream_t>(stream);
-    return set_error(MPM_OK);
+    // the new stream comes after the closing sorts still in flight
+    return set_error(join_sorts(h));
 }
 
 int mpm_get_params(const mpm_handle* h, mpm_params* out, mpm_table_info* info) {
@@ -516,6 +542,8 @@ int mpm_search(mpm_handle* h, const uint8_t* T, size_t n, uint32_t* out_pos, uin
     int rc = prepare(h);
     if (rc) return set_error(rc);
     const size_t out_capacity = *z;
+    rc = join_sorts(h);  // set 0's buffers may still be read by a pipelined sort
+    if (rc) return set_error(rc);
     rc = harvest_timing(h, true);  // pipelined searches still timed belong to before
     if (rc) return set_error(rc);
     h->stats = mpm_stats{};
@@ -639,16 +667,41 @@ int mpm_search_async(mpm_handle* h, const uint8_t* T, size_t n, uint32_t* out_po
     uint32_t* dstatus = device_address(status);
     if (!dstatus) return set_error(MPM_EINVAL);
     cudaStream_t s = h->stream;
-    // buffers as mpm_search sizes them on its first call (allocation waits
-    // for the device only the first time)
+    // the side stream, its events and buffer set 1 on first use
+    if (!h->side) {
+        if (cudaStreamCreateWithFlags(&h->side, cudaStreamNonBlocking) != cudaSuccess ||
+            cudaMalloc(&h->d_counters1, mpm::kNumCounters * 4) != cudaSuccess ||
+            cudaMemset(h->d_counters1, 0, mpm::kNumCounters * 4) != cudaSuccess) {
+            cudaGetLastError();
+            return set_error(MPM_ECUDA);
+        }
+        for (int b = 0; b < 2; b++)
+            if (cudaEventCreateWithFlags(&h->scan_done[b], cudaEventDisableTiming) != cudaSuccess ||
+                cudaEventCreateWithFlags(&h->sort_done[b], cudaEventDisableTiming) != cudaSuccess) {
+                cudaGetLastError();
+                return set_error(MPM_ECUDA);
+            }
+    }
+    // buffers as mpm_search sizes them on its first call, the same in both
+    // sets (allocation waits for the device only when a buffer grows)
     if (!fused_search(h) &&
-        grow(&h->d_cand, &h->cand_cap, std::max<size_t>(1 << 16, n / 64 + 1024)))
+        (grow(&h->d_cand, &h->cand_cap, std::max<size_t>(1 << 16, n / 64 + 1024)) ||
+         grow(&h->d_cand1, &h->cand1_cap, h->cand_cap)))
         return set_error(MPM_ENOMEM);
     if (!h->d_occ || h->occ_cap < (1u << 16)) {
         size_t c = 0;
         if (grow(&h->d_occ, &h->occ_cap, 1 << 16) || grow(&h->d_occ_tmp, &c, 1 << 16))
             return set_error(MPM_ENOMEM);
     }
+    if (grow(&h->d_occ1, &h->occ1_cap, h->occ_cap)) return set_error(MPM_ENOMEM);
+    const int b = h->async_set;
+    uint64_t* cand = b ? h->d_cand1 : h->d_cand;
+    const size_t cand_cap = b ? h->cand1_cap : h->cand_cap;
+    uint64_t* occ = b ? h->d_occ1 : h->d_occ;
+    const size_t occ_cap = b ? h->occ1_cap : h->occ_cap;
+    uint32_t* counters = b ? h->d_counters1 : h->d_counters;
+    bool& dirty = b ? h->counters1_dirty : h->counters_dirty;
+
     const uint32_t q = (uint32_t)h->plan.p.q, k = (uint32_t)h->plan.p.k;
     h->stats.n += n;
     h->stats.sampled += (n / q) / k;
@@ -658,34 +711,56 @@ int mpm_search_async(mpm_handle* h, const uint8_t* T, size_t n, uint32_t* out_po
         rc = next_timing_slot(h, &ev);
         if (rc) return set_error(rc);
     }
-    const bool reset = h->counters_dirty;
-    h->counters_dirty = true;
+    // the set's previous sort must have read its keys and zeroed its counters
+    if (h->sort_pending[b] && cudaStreamWaitEvent(s, h->sort_done[b], 0) != cudaSuccess) {
+        cudaGetLastError();
+        return set_error(MPM_ECUDA);
+    }
+    const bool reset = dirty;
+    dirty = true;
     int launches = 0;
     if (n >= h->plan.m) {
-        rc = enqueue_filter(h, T, (uint32_t)n, h->d_cand, (uint32_t)h->cand_cap, h->d_occ,
-                            (uint32_t)h->occ_cap, h->d_counters, &launches, reset, ev);
+        rc = enqueue_filter(h, T, (uint32_t)n, cand, (uint32_t)cand_cap, occ, (uint32_t)occ_cap,
+                            counters, &launches, reset, ev);
         if (rc) return set_error(rc);
     } else {
-        if (reset && cudaMemsetAsync(h->d_counters, 0, mpm::kNumCounters * 4, s) != cudaSuccess)
+        if (reset && cudaMemsetAsync(counters, 0, mpm::kNumCounters * 4, s) != cudaSuccess)
             return set_error(MPM_ECUDA);
         if (ev) {
             for (int i = 0; i < 3; i++) cudaEventRecord(ev[i], s);
         }
     }
+    // the closing sort on the side stream, after this scan
     const uint32_t rank_cap = (uint32_t)std::min<size_t>(cap, mpm::kRankSortMax);
-    if (mpm::launch_rank_sort(h->d_occ, h->d_counters, rank_cap, out_pos, out_pid, dstatus,
-                              fused_search(h) ? 0xFFFFFFFFu : (uint32_t)h->cand_cap,
-                              (uint32_t)h->occ_cap, s) < 0)
+    if (cudaEventRecord(h->scan_done[b], s) != cudaSuccess ||
+        cudaStreamWaitEvent(h->side, h->scan_done[b], 0) != cudaSuccess ||
+        mpm::launch_rank_sort(occ, counters, rank_cap, out_pos, out_pid, dstatus,
+                              fused_search(h) ? 0xFFFFFFFFu : (uint32_t)cand_cap,
+                              (uint32_t)occ_cap, h->side) < 0 ||
+        cudaEventRecord(h->sort_done[b], h->side) != cudaSuccess) {
+        cudaGetLastError();
         return set_error(MPM_ECUDA);
+    }
     launches++;
+    h->sort_pending[b] = true;
     h->stats.launches += (uint32_t)launches;
-    h->counters_dirty = false;
+    dirty = false;
+    h->async_set = b ^ 1;
     return set_error(MPM_OK);
+}
+
+int mpm_join(mpm_handle* h) {
+    if (!h) return set_error(MPM_EINVAL);
+    int rc = prepare(h);
+    if (rc) return set_error(rc);
+    return set_error(join_sorts(h));
 }
 
 int mpm_sync(mpm_handle* h) {
     if (!h) return set_error(MPM_EINVAL);
     int rc = prepare(h);
+    if (rc) return set_error(rc);
+    rc = join_sorts(h);
     if (rc) return set_error(rc);
     if (cudaStreamSynchronize(h->stream) != cudaSuccess) {
         cudaGetLastError();
@@ -745,6 +820,8 @@ int mpm_scan(mpm_handle* h, const uint8_t* T, size_t n, uint64_t* cand, size_t* 
     if (!h || !count || (n > 0 && !T) || n >= (1ull << 32)) return set_error(MPM_EINVAL);
     if (*count > 0 && !cand) return set_error(MPM_EINVAL);
     int rc = prepare(h);
+    if (rc) return set_error(rc);
+    rc = join_sorts(h);  // set 0's counters may still be closed by a pipelined sort
     if (rc) return set_error(rc);
     cudaStream_t s = h->stream;
     const mpm::FilterDev f = filter_dev(h);

@@ -46,6 +46,22 @@ struct mpm_handle {
     bool jit_cand_tried = false;
     int timing = 0;
     cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};
+    // Pipelined searches alternate between two buffer sets (set 0 is
+    // d_cand, d_occ and d_counters above).  A search's scan runs on `stream`;
+    // its closing sort runs on `side` once the scan is done, so that it
+    // overlaps the next search's scan; a search waits for the sort that last
+    // used its set.
+    cudaStream_t side = nullptr;
+    cudaEvent_t scan_done[2] = {nullptr, nullptr};
+    cudaEvent_t sort_done[2] = {nullptr, nullptr};
+    bool sort_pending[2] = {false, false};
+    uint64_t* d_cand1 = nullptr;
+    size_t cand1_cap = 0;
+    uint64_t* d_occ1 = nullptr;
+    size_t occ1_cap = 0;
+    uint32_t* d_counters1 = nullptr;
+    bool counters1_dirty = false;
+    int async_set = 0;
     // event triples of pipelined searches (mpm_search_async), reused in turn
     static constexpr int kRing = 64;
     cudaEvent_t ring[kRing][3] = {};

@@ -178,8 +178,9 @@ __global__ void __launch_bounds__(kRankThreads)
             // 1: the outputs hold every occurrence, sorted
             snapshot[kDoneCount] = (err == 0 && occ <= out_cap && occ <= kRankSortMax &&
                                     occ <= occ_cap && cand <= cand_cap) ? 1u : 0u;
+            // the snapshot is read after the stream completes, which makes
+            // these writes visible (also in mapped host memory): no fence
             for (int i = 0; i < kNumCounters; i++) c[i] = 0;
-            __threadfence_system();
         }
     }
     if (z > kRankSortMax || z > out_cap) return;

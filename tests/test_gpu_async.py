@@ -136,3 +136,34 @@ def test_mapped_status_interleaving_and_timing(mpm, native):
     assert st["launches"] >= 6 and st["ms_scan"] > 0 and st["n"] == 3 * case.n
     assert np.all(pinned.numpy()[:, 1] == z) and np.all(pinned.numpy()[:, 3] == 1)
     assert np.array_equal(as_u32(pos)[:z], want[0]) and np.array_equal(as_u32(pid)[:z], want[1])
+
+
+def test_join_orders_later_stream_work_and_stream_switches(mpm, native):
+    case = W.protein_case(1 << 21, 500, 24, 250, cfg=12)
+    T = torch.from_numpy(case.T).cuda()
+    want = native.aho_corasick(case.T, case.P)
+    z = want[0].size
+    assert 0 < z <= 4096
+    m = mpm.Matcher(case.P, sigma=20)
+    outs = [(torch.empty(4096, dtype=torch.int32, device="cuda"),
+             torch.empty(4096, dtype=torch.int32, device="cuda")) for _ in range(5)]
+    status = torch.zeros((5, 4), dtype=torch.int32, device="cuda")
+    copies = []
+    for i in range(3):
+        m.search_async(T, outs[i][0], outs[i][1], status[i])
+    m.join()
+    # later work on the same stream sees the finished outputs without a host wait
+    copies = [o[0][:z].clone() for o in outs[:3]] + [status[:3].clone()]
+    side = torch.cuda.Stream()
+    with torch.cuda.stream(side):
+        for i in range(3, 5):
+            m.search_async(T, outs[i][0], outs[i][1], status[i])
+        m.join()
+        late = [o[1][:z].clone() for o in outs[3:]]
+    torch.cuda.synchronize()
+    for c in copies[:3]:
+        assert np.array_equal(c.cpu().numpy().view(np.uint32), want[0])
+    assert np.all(copies[3].cpu().numpy()[:, 1] == z)
+    for c in late:
+        assert np.array_equal(c.cpu().numpy().view(np.uint32), want[1])
+    assert np.all(status.cpu().numpy()[:, 3] == 1)
