@@ -147,36 +147,37 @@ __device__ void batch_lane(const BatchSet& S, const ET* tab, const uint8_t* smu,
     const bool vec = (reinterpret_cast<uintptr_t>(tx.T) & 15) == 0;
     int qcount = 0;  // the same in every lane
     for (uint32_t w0 = 0; w0 < wmax; w0 += 8) {
-        uint32_t x[8];
         const uint32_t at0 = a + 4 * w0;
         // the lane's sector four blocks ahead (inside the text: at0 + 160 <= b + 3),
         // into L2 while this one is scanned
         if (w0 + 40 <= words)
             asm volatile("prefetch.global.L2 [%0];" ::"l"(tx.T + at0 + 128));
-        if (vec && w0 + 8 <= words && at0 + 32 <= tx.n) {
-            const uint4 lo = __ldg(reinterpret_cast<const uint4*>(tx.T + at0));
-            const uint4 hi = __ldg(reinterpret_cast<const uint4*>(tx.T + at0 + 16));
-            x[0] = lo.x; x[1] = lo.y; x[2] = lo.z; x[3] = lo.w;
-            x[4] = hi.x; x[5] = hi.y; x[6] = hi.z; x[7] = hi.w;
-        } else {
-#pragma unroll
-            for (int u = 0; u < 8; u++) {
-                const uint32_t at = at0 + 4 * u;
-                x[u] = 0;
-                if (w0 + u < words) {
-                    if (at + 4 <= tx.n) {
-                        x[u] = load_word(tx.T, at);
-                    } else {
-                        for (uint32_t v = 0; v < 4 && at + v < tx.n; v++)
-                            x[u] |= (uint32_t)tx.T[at + v] << (8 * v);
-                    }
-                }
-            }
+        const bool whole = vec && w0 + 8 <= words && at0 + 32 <= tx.n;
+        uint4 lo4 = make_uint4(0, 0, 0, 0), hi4 = make_uint4(0, 0, 0, 0);
+        if (whole) {
+            lo4 = __ldg(reinterpret_cast<const uint4*>(tx.T + at0));
+            hi4 = __ldg(reinterpret_cast<const uint4*>(tx.T + at0 + 16));
         }
-#pragma unroll
+        // one copy of the step loop (the instruction caches are shared by
+        // the kernel's mapping and entry-width instantiations)
+#pragma unroll 1
         for (int u = 0; u < 8; u++) {
             if (w0 + u >= wmax) break;
-            sp.push(x[u]);
+            uint32_t x = 0;
+            if (whole) {
+                const uint4 v = u < 4 ? lo4 : hi4;
+                const int t = u & 3;
+                x = t == 0 ? v.x : t == 1 ? v.y : t == 2 ? v.z : v.w;
+            } else if (w0 + u < words) {
+                const uint32_t at = at0 + 4 * u;
+                if (at + 4 <= tx.n) {
+                    x = load_word(tx.T, at);
+                } else {
+                    for (uint32_t v = 0; v < 4 && at + v < tx.n; v++)
+                        x |= (uint32_t)tx.T[at + v] << (8 * v);
+                }
+            }
+            sp.push(x);
             pos += 4;
             while (nxt <= pos) {
                 const uint32_t c = sp.code(pos - nxt);
