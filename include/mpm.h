@@ -338,7 +338,7 @@ typedef struct {
     int lane_bytes;  /* text bytes per lane of a tile; 0 = 512 */
     int no_graph;    /* 1: launch the kernels on every run instead of a graph */
     int unit_kib;    /* estimated cost of a work unit, in KiB of scanned text
-                        (verification counted as extra bytes); 0 = 1024 */
+                        (verification counted as extra bytes); 0 = 2048 */
 } mpm_batch_opts;
 
 typedef struct {

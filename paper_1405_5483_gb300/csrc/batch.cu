@@ -590,7 +590,7 @@ mpm_batch* mpm_batch_create(mpm_handle* const* sets, int nsets, const uint8_t* c
     std::vector<mpm::BatchTile> tiles;
     std::vector<mpm::BatchUnit> units;
     const uint32_t lane_bytes = o.lane_bytes > 0 ? (uint32_t)o.lane_bytes : 512;
-    const uint64_t unit_bytes = (uint64_t)(o.unit_kib > 0 ? o.unit_kib : 1024) << 10;
+    const uint64_t unit_bytes = (uint64_t)(o.unit_kib > 0 ? o.unit_kib : 2048) << 10;
     uint32_t max_r = 1;
     for (int i = 0; i < nsets; i++) max_r = std::max<uint32_t>(max_r, (uint32_t)sets[i]->plan.r);
     for (int t = 0; t < ntexts; t++) {
