@@ -502,6 +502,19 @@ int mpm_model_choose(mpm_model *model, const uint8_t *P, size_t r, size_t m, int
                      double entropy, size_t n, size_t max_table_bytes, mpm_params *best,
                      float *pred);
 
+/* ------------------------------------------------------------ test hook */
+
+/*
+ * Failure detection without a GPU fault: fault = 1 arms the next launch of a
+ * specialised scan (MPM_KERNEL_SPECIALISED or SPLIT, rows read through TMA)
+ * so that one warp's first stage barrier expects 16 bytes more than its copy
+ * brings; that warp's bounded wait gives up after about a second, it records
+ * MPM_ETIMEOUT, waits (bounded) for its other copies and returns, and the
+ * search returns MPM_ETIMEOUT.  The handle stays usable.  One-shot; 0
+ * disarms.  MPM_EINVAL for other values.  Host only.
+ */
+int mpm_test_inject(int fault);
+
 /* ------------------------------------------- search that allocates nothing */
 
 /*

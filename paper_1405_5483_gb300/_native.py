@@ -140,6 +140,7 @@ def lib():
         "mpm_search_async": (ctypes.c_int, [vp, u8p, sz, vp, vp, sz, vp]),
         "mpm_sync": (ctypes.c_int, [vp]),
         "mpm_join": (ctypes.c_int, [vp]),
+        "mpm_test_inject": (ctypes.c_int, [ctypes.c_int]),
         "mpm_reset_stats": (ctypes.c_int, [vp]),
         "mpm_batch_create": (vp, [ctypes.POINTER(vp), ctypes.c_int, ctypes.POINTER(vp),
                                   ctypes.POINTER(ctypes.c_size_t), ctypes.POINTER(ctypes.c_uint32),

@@ -8,6 +8,7 @@
 #include <dlfcn.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
@@ -353,6 +354,14 @@ const JitKernel* jit_scan_kernel(const FilterDev& f, bool verify, int device, in
 
 bool jit_verifies(const JitKernel* k) { return k && k->spec.verify; }
 
+namespace {
+std::atomic<int> g_injected_fault{0};
+}  // namespace
+
+// Test hook (mpm_test_inject): a fault armed for the next specialised scan.
+int take_injected_fault() { return g_injected_fault.exchange(0); }
+void set_injected_fault(int f) { g_injected_fault.store(f); }
+
 int launch_scan_jit(const ScanArgs& A, const VerifyArgs* V, const JitKernel* K, int num_sms,
                     int chunk, cudaStream_t stream) {
     if (A.n == 0) return 0;
@@ -372,6 +381,7 @@ int launch_scan_jit(const ScanArgs& A, const VerifyArgs* V, const JitKernel* K, 
     const uint64_t R = aligned ? n / Lst : 0;
 
     JitScanArgs J{};
+    J.inject = (uint32_t)take_injected_fault();
     J.T = A.T;
     J.table = A.f.table;
     J.mu = A.f.mu;
@@ -424,3 +434,9 @@ int launch_scan_jit(const ScanArgs& A, const VerifyArgs* V, const JitKernel* K, 
 }
 
 }  // namespace mpm
+
+extern "C" int mpm_test_inject(int fault) {
+    if (fault < 0 || fault > 1) return mpm::set_error(MPM_EINVAL);
+    mpm::set_injected_fault(fault);
+    return mpm::set_error(MPM_OK);
+}

@@ -30,7 +30,8 @@ struct JitScanArgs {
     unsigned int slot_mask;
     unsigned int key_bytes;       // min(m, 16)
     unsigned int occ_cap;
-    unsigned int pad;
+    unsigned int inject;          // test hook: 1 = warp 0 over-arms its first stage's
+                                  // barrier, so its bounded wait runs out (MPM_ETIMEOUT)
 };
 
 }  // namespace mpm
