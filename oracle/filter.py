@@ -53,7 +53,8 @@ reason in the design notes):
     garbled and lists q-1 of them; with fewer shifts occurrences are lost);
   * the shifted q-gram patterns are cut to the common length
     L' = floor((m - q + 1) / q), the length of the shortest shift;
-  * the filter uses at most 64 q-gram positions (one 64-bit word);
+  * the filter uses at most 64 q-gram positions (one 64-bit word), or 128
+    with two words of state (Section 3.2's ceil((m/q)/w) words, w = 64);
   * AOSO subpattern j, element i sits at bit i*k + j, the sampled text
     q-grams are those with index h = k-1 (mod k), D starts all ones;
   * rank ties are broken by byte value; the greedy heuristic is
@@ -200,10 +201,12 @@ class FilterParams:
     digits; with qhash=True, sigma' is the number of q-gram bins and a
     q-gram's code is qgram_hash of its raw bytes."""
 
-    def __init__(self, q, sigma_r, k, mu=None, order="msd", qhash=False, overlap=False):
+    def __init__(self, q, sigma_r, k, mu=None, order="msd", qhash=False, overlap=False,
+                 max_positions=64):
         self.q, self.sigma_r, self.k = int(q), int(sigma_r), int(k)
         self.qhash = bool(qhash)
         self.overlap = bool(overlap)
+        self.max_positions = int(max_positions)
         self.mu = None if mu is None else np.asarray(mu, dtype=np.uint8)
         self.order = order
 
@@ -211,9 +214,10 @@ class FilterParams:
         """(L', m', m''): the q-gram pattern length (m - q + 1 overlapping
         q-grams, or the common length floor((m - q + 1) / q) of the q shifts'
         non-overlapping q-grams), the AOSO subpattern length and the number of
-        filter positions k*m' (at most 64)."""
+        filter positions k*m' (at most max_positions: 64 for one 64-bit word
+        of Shift-Or state, 128 for two)."""
         Lc = (m - self.q + 1) if self.overlap else (m - self.q + 1) // self.q
-        Lf = min(Lc, 64)
+        Lf = min(Lc, self.max_positions)
         mp = Lf // self.k
         return Lc, mp, self.k * mp
 
@@ -252,7 +256,8 @@ def mask_table(classes, fp):
     for p, cls in enumerate(classes):
         for c in cls:
             B[c] &= ~(1 << p)
-    return np.array(B, dtype=np.uint64)
+    # more than 64 positions: entries as Python integers (two words of state)
+    return np.array(B, dtype=np.uint64 if len(classes) <= 64 else object)
 
 
 def text_codes(T, fp):
@@ -347,11 +352,13 @@ def verify(T, P, windows, q):
     return out
 
 
-def make_params(P, q, sigma_r, k, map_kind, shift=0, order="msd", overlap=False):
+def make_params(P, q, sigma_r, k, map_kind, shift=0, order="msd", overlap=False,
+                max_positions=64):
     """Convenience: the mapping of `map_kind` ("rank", "greedy", "lowbits",
     "qhash")."""
     if map_kind == "qhash":
-        return FilterParams(q, sigma_r, k, None, order, qhash=True, overlap=overlap)
+        return FilterParams(q, sigma_r, k, None, order, qhash=True, overlap=overlap,
+                            max_positions=max_positions)
     if map_kind == "rank":
         mu = map_rank(P, sigma_r)
     elif map_kind == "greedy":
@@ -360,7 +367,7 @@ def make_params(P, q, sigma_r, k, map_kind, shift=0, order="msd", overlap=False)
         mu = map_lowbits(sigma_r, shift)
     else:
         raise ValueError(map_kind)
-    return FilterParams(q, sigma_r, k, mu, order, overlap=overlap)
+    return FilterParams(q, sigma_r, k, mu, order, overlap=overlap, max_positions=max_positions)
 
 
 def search(T, P, fp):

@@ -483,3 +483,26 @@ def test_aho_corasick_variable_lengths_equals_brute_force():
         for threads in (1, 3):
             pos, pid = native.AhoCorasick(P).search(np.frombuffer(T, np.uint8), threads=threads)
             assert list(zip(pos.tolist(), pid.tolist())) == want
+
+
+# ------------------------------------------- two words of Shift-Or state (Section 3.2)
+
+def test_wider_filter_is_exact_for_long_single_patterns_and_tighter_than_64():
+    rng = np.random.default_rng(91)
+    for _ in range(25):
+        m = int(rng.integers(70, 140))
+        T, P = _overlap_case(rng, 2, 3000, 1, m, 1)
+        for k in (1, 2):
+            wide = F.make_params(P, 1, 2, k, "rank", max_positions=128)
+            narrow = F.make_params(P, 1, 2, k, "rank")
+            assert wide.lengths(m)[2] == k * (min(m, 128) // k)
+            cw, cn = F.pattern_classes(P, wide), F.pattern_classes(P, narrow)
+            # the first classes coincide; the wider filter adds positions
+            assert cw[:len(cn)] == cn
+            ww = F.aoso_scan(F.text_codes(T, wide), F.mask_table(cw, wide), wide, len(cw))
+            wn = F.aoso_scan(F.text_codes(T, narrow), F.mask_table(cn, narrow), narrow, len(cn))
+            assert ww == F.candidate_windows_by_definition(F.text_codes(T, wide), cw, wide)
+            occ = [i for i in range(T.size - m + 1) if bytes(T[i:i + m]) == bytes(P[0])]
+            if k == 1 and m <= 128:
+                assert ww == occ   # one pattern, injective map, every position checked
+            assert F.search(T, P, wide) == sorted(brute.occurrences(T, P))
