@@ -88,6 +88,11 @@ extern "C" {
  *            shifts; the text's q-gram at every byte, every k-th one read),
  *            L' = m - q + 1.  Runs in the generic kernel (AUTO resolves to
  *            it; SPECIALISED, SPLIT, SMAG and mpm_batch answer MPM_ENOTSUP).
+ *   wide     0: at most 64 filter positions (one 64-bit word of Shift-Or
+ *            state); 1: at most 128 (two words, Section 3.2's ceil((m/q)/w)
+ *            words; mask table entries of 16 bytes above 64 positions).  Runs
+ *            in the generic kernel (AUTO resolves to it; SPECIALISED, SPLIT
+ *            and SMAG answer MPM_ENOTSUP).
  */
 #define MPM_KERNEL_AUTO        0
 #define MPM_KERNEL_GENERIC     1
@@ -105,14 +110,15 @@ typedef struct {
     int chunk;
     int kernel;
     int overlap;
+    int wide;
 } mpm_params;
 
 /* Sizes that follow from resolved parameters and m (Sections 3.1, 3.2). */
 typedef struct {
     int L;             /* common q-gram length of the q shifted patterns, L'  */
-    int mprime;        /* AOSO subpattern length m' = floor(min(L',64)/k)     */
-    int positions;     /* filter positions m'' = k * m' (<= 64)               */
-    int entry_bytes;   /* bytes per mask-table entry: 1, 2, 4 or 8            */
+    int mprime;        /* AOSO subpattern length m' = floor(min(L',cap)/k)    */
+    int positions;     /* filter positions m'' = k * m' (<= 64; <= 128 wide)    */
+    int entry_bytes;   /* bytes per mask-table entry: 1, 2, 4, 8 or 16        */
     uint64_t entries;  /* sigma_r^q                                           */
     uint64_t table_bytes;
     double est_candidate_rate; /* estimated candidate records per sampled q-gram,

@@ -27,9 +27,9 @@ def _torch():
 
 
 def make_params(q=0, sigma_r=0, k=0, map_kind=MAP_AUTO, map_shift=-1, table_place=TABLE_AUTO,
-                smag=0, chunk=0, kernel=KERNEL_AUTO, overlap=0):
+                smag=0, chunk=0, kernel=KERNEL_AUTO, overlap=0, wide=0):
     return Params(q, sigma_r, k, map_kind, map_shift, table_place, smag, chunk, kernel,
-                  overlap)
+                  overlap, wide)
 
 
 def jit_compile(P, sigma, **kw):

@@ -24,7 +24,7 @@ class Params(ctypes.Structure):
     _fields_ = [("q", ctypes.c_int), ("sigma_r", ctypes.c_int), ("k", ctypes.c_int),
                 ("map_kind", ctypes.c_int), ("map_shift", ctypes.c_int),
                 ("table_place", ctypes.c_int), ("smag", ctypes.c_int), ("chunk", ctypes.c_int),
-                ("kernel", ctypes.c_int), ("overlap", ctypes.c_int)]
+                ("kernel", ctypes.c_int), ("overlap", ctypes.c_int), ("wide", ctypes.c_int)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}

@@ -377,8 +377,8 @@ static mpm_handle* build_handle(const uint8_t* P, size_t r, size_t m, int sigma,
         set_error(rc);
         return nullptr;
     }
-    if (h->plan.p.overlap) {
-        // overlapping q-grams run in the generic kernel only
+    if (h->plan.p.overlap || h->plan.p.wide) {
+        // overlapping q-grams and two-word state run in the generic kernel only
         if (h->plan.p.smag || h->plan.p.kernel == MPM_KERNEL_SPECIALISED ||
             h->plan.p.kernel == MPM_KERNEL_SPLIT) {
             delete h;
@@ -781,7 +781,7 @@ int mpm_jit_compile(const uint8_t* P, size_t r, size_t m, int sigma, const mpm_p
     mpm::Plan plan;
     int rc = mpm::make_plan(P, r, m, sigma, params, &plan);
     if (rc) return set_error(rc);
-    if (plan.p.overlap) return set_error(MPM_ENOTSUP);  // generic kernel only
+    if (plan.p.overlap || plan.p.wide) return set_error(MPM_ENOTSUP);  // generic kernel only
     mpm::FilterDev f{};
     f.table_bytes = (uint32_t)((plan.info.table_bytes + 15) & ~uint64_t(15));
     f.entry_bytes = plan.info.entry_bytes;

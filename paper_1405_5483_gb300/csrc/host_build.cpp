@@ -88,12 +88,13 @@ struct Lengths {
 };
 
 // L' = the q-gram pattern length: floor((m-q+1)/q) non-overlapping q-grams
-// (common to the q shifts), or m-q+1 overlapping ones.
-Lengths lengths(size_t m, int q, int k, bool overlap) {
+// (common to the q shifts), or m-q+1 overlapping ones; the filter keeps at
+// most maxpos of them (64 for one word of Shift-Or state, 128 for two).
+Lengths lengths(size_t m, int q, int k, bool overlap, int maxpos) {
     Lengths x;
     long L = overlap ? ((long)m - q + 1) : ((long)m - q + 1) / q;
     x.L = (int)std::max(0L, L);
-    x.Lf = std::min(x.L, kMaxPositions);
+    x.Lf = std::min(x.L, maxpos);
     x.mprime = k >= 1 ? x.Lf / k : 0;
     x.positions = k * x.mprime;
     return x;
@@ -103,7 +104,8 @@ int entry_bytes_for(int positions) {
     if (positions <= 8) return 1;
     if (positions <= 16) return 2;
     if (positions <= 32) return 4;
-    return 8;
+    if (positions <= 64) return 8;
+    return 16;
 }
 
 // Probability, under the pattern-set symbol frequencies mapped by mu, that a
@@ -294,7 +296,9 @@ int make_plan(const uint8_t* P, size_t r, size_t m, int sigma, const mpm_params*
     if (req.table_place < 0 || req.table_place > MPM_TABLE_GLOBAL) return MPM_EINVAL;
     if (req.smag < 0 || req.smag > 1 || req.chunk < 0) return MPM_EINVAL;
     if (req.overlap < 0 || req.overlap > 1) return MPM_EINVAL;
+    if (req.wide < 0 || req.wide > 1) return MPM_EINVAL;
     const bool ov = req.overlap == 1;
+    const int maxpos = req.wide ? 2 * kMaxPositions : kMaxPositions;
     if (req.kernel < MPM_KERNEL_AUTO || req.kernel > MPM_KERNEL_SPLIT) return MPM_EINVAL;
 
     uint64_t h[256];
@@ -325,7 +329,7 @@ int make_plan(const uint8_t* P, size_t r, size_t m, int sigma, const mpm_params*
             for (int k = 1; k <= std::min(L1.Lf, kMaxK); k++) ks.push_back(k);
         }
         for (int k : ks) {
-            Lengths Lk = lengths(m, q, k, ov);
+            Lengths Lk = lengths(m, q, k, ov, maxpos);
             if (Lk.mprime < 1) continue;
             const int eb = entry_bytes_for(Lk.positions);
             const uint64_t tb = entries * (uint64_t)eb;
@@ -384,7 +388,7 @@ int make_plan(const uint8_t* P, size_t r, size_t m, int sigma, const mpm_params*
             for (int q = 2; q <= qmax; q++) qs.push_back(q);
         }
         for (int q : qs) {
-            Lengths L1 = lengths(m, q, 1, ov);
+            Lengths L1 = lengths(m, q, 1, ov, maxpos);
             if (L1.L < 1) continue;
             const GramStats g = gram_stats(P, r, m, q, h, L1.Lf, ov);
             for (int sr : bins) {
@@ -421,7 +425,7 @@ int make_plan(const uint8_t* P, size_t r, size_t m, int sigma, const mpm_params*
         }
         for (int q : qs) {
             if (q * ell > 30) continue;
-            Lengths L1 = lengths(m, q, 1, ov);
+            Lengths L1 = lengths(m, q, 1, ov, maxpos);
             if (L1.L < 1) continue;
             const uint64_t entries = 1ull << (q * ell);
             if (!req.q && entries * 8 > kAutoTableBytes * 8 && q * ell > 26) continue;

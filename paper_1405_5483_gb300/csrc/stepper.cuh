@@ -20,9 +20,43 @@ enum ScanMode : int {
     kQHash = 4    // raw-byte window, whole q-gram hashed to a bin (q <= 5)
 };
 
+// Two 64-bit words of Shift-Or state, and a mask table entry of 16 bytes
+// (bits 0..63 in lo, 64..127 in hi: the entry's bytes little-endian), for
+// filters of up to 128 positions (Section 3.2: ceil((m/q)/w) words, w = 64).
+struct U128 {
+    uint64_t lo, hi;
+    U128() = default;
+    __host__ __device__ constexpr U128(uint64_t v) : lo(v), hi(0) {}
+    __host__ __device__ constexpr U128(uint64_t l, uint64_t h) : lo(l), hi(h) {}
+    __host__ __device__ explicit operator uint32_t() const { return (uint32_t)lo; }
+};
+__device__ __forceinline__ U128 operator~(const U128& a) { return U128(~a.lo, ~a.hi); }
+__device__ __forceinline__ U128 operator|(const U128& a, const U128& b) {
+    return U128(a.lo | b.lo, a.hi | b.hi);
+}
+__device__ __forceinline__ U128 operator<<(const U128& a, int s) {
+    if (s == 0) return a;
+    if (s >= 64) return U128(0, a.lo << (s - 64));
+    return U128(a.lo << s, (a.hi << s) | (a.lo >> (64 - s)));
+}
+__device__ __forceinline__ U128 operator>>(const U128& a, int s) {
+    if (s == 0) return a;
+    if (s >= 64) return U128(a.hi >> (s - 64), 0);
+    return U128((a.lo >> s) | (a.hi << (64 - s)), a.hi >> s);
+}
+
+template <typename ET>
+struct StateOf {  // the Shift-Or state type for table entries of type ET
+    using type = typename std::conditional<sizeof(ET) == 8, uint64_t, uint32_t>::type;
+};
+template <>
+struct StateOf<U128> {
+    using type = U128;
+};
+
 template <int MODE, typename ET>
 struct Stepper {
-    using DT = typename std::conditional<sizeof(ET) == 8, uint64_t, uint32_t>::type;
+    using DT = typename StateOf<ET>::type;
     const ET* tab;
     const uint8_t* smu;
     int q, k, ell, shift, raw_base;

@@ -154,6 +154,42 @@ def test_host_tables_overlapping_qgrams_equal_oracle(mpm, seed):
     assert np.array_equal(got, otab.astype(np.uint64))
 
 
+def _wide_positions(table, entry_bytes, positions):
+    # entries as Python integers: up to 16 little-endian bytes each
+    t = table.reshape(-1, entry_bytes)
+    mask = (1 << positions) - 1
+    return [int.from_bytes(bytes(row), "little") & mask for row in t]
+
+
+@pytest.mark.parametrize("seed", range(12))
+def test_host_tables_two_word_state_equal_oracle(mpm, seed):
+    rng = np.random.default_rng(700 + seed)
+    sigma = int(rng.choice([4, 20]))
+    r = int(rng.integers(1, 40))
+    m = int(rng.choice([80, 130, 200, 260]))
+    q = int(rng.integers(1, 3))
+    sr = 4
+    k = int(rng.integers(1, 5))
+    overlap = int(rng.integers(0, 2))
+    P = (rng.integers(0, sigma, size=(r, m)) + 65).astype(np.uint8)
+    kw = dict(q=q, sigma_r=sr, k=k, map_kind=2, wide=1, overlap=overlap)
+    mu, table, info = mpm.host_tables(P, sigma, **kw)
+    Lc = (m - q + 1) if overlap else (m - q + 1) // q
+    assert info["positions"] == k * (min(Lc, 128) // k)
+    p = dict(q=q, sigma_r=sr, k=k, map_kind=2, map_shift=info["map_shift"], overlap=overlap)
+    fp = F.make_params(P, q, sr, k, "greedy", overlap=bool(overlap), max_positions=128)
+    cls = F.pattern_classes(P, fp)
+    otab = F.mask_table(cls, fp)
+    assert np.array_equal(mu, fp.mu) and info["positions"] == len(cls)
+    got = _wide_positions(table, info["entry_bytes"], len(cls))
+    assert got == [int(x) for x in otab]
+    if info["positions"] > 64:
+        assert info["entry_bytes"] == 16
+    # without wide, the same request keeps 64 positions at most
+    _, info64 = mpm.plan(P, sigma, q=q, sigma_r=sr, k=k, map_kind=2, overlap=overlap)
+    assert info64["positions"] <= 64
+
+
 def test_overlap_refusals(mpm):
     P = np.frombuffer(b"ACGTACGTACGTACGT", np.uint8).reshape(1, 16)
     rc, _ = mpm.jit_compile(P, 4, q=3, sigma_r=4, k=1, map_kind=2, overlap=1)
