@@ -152,47 +152,66 @@ def cpu_baseline(case, sample_bytes):
                       "(%.2f s, %d occurrences)" % (n >> 20, case.r, threads, dt, pos.size)}
 
 
-def run_reference_batch(args):
+class OracleBatchSample:
     """The oracle on the batch workload: one Aho-Corasick automaton per
-    pattern set, each text searched with its set's automaton, over a bounded
-    sample of the texts (in text order) per step."""
-    from oracle import native
+    pattern set, each text searched with its set's automaton, over the first
+    texts (in text order) up to `budget` bytes."""
+
+    def __init__(self, b, budget):
+        from oracle import native
+        self.b = b
+        self.threads = os.cpu_count() or 1
+        self.picked, self.total = [], 0
+        for t, T in enumerate(b.texts):
+            if self.total >= budget:
+                break
+            self.picked.append(t)
+            self.total += T.size
+        sets = sorted(set(int(b.set_of_text[t]) for t in self.picked))
+        self.acs = {s: native.AhoCorasick(b.sets[s]) for s in sets}
+
+    def step(self):
+        z = 0
+        for t in self.picked:
+            pos, _ = self.acs[int(self.b.set_of_text[t])].search(self.b.texts[t],
+                                                                  threads=self.threads)
+            z += pos.size
+        return z
+
+    def describe(self):
+        return ("the first %d texts (%d MiB), each with its set's Aho-Corasick automaton over "
+                "%d threads" % (len(self.picked), self.total >> 20, self.threads))
+
+    def close(self):
+        for ac in self.acs.values():
+            ac.close()
+
+
+def run_reference_batch(args):
+    """The oracle on the batch workload over a bounded sample of the texts
+    per step."""
     from paper_1405_5483_gb300 import workloads as W
     b = W.config4()
-    threads = os.cpu_count() or 1
     budget = max(4 << 20, min(args.ref_sample_mib << 20, (2 << 30) // max(1, args.steps)))
-    picked, total = [], 0
-    for t, T in enumerate(b.texts):
-        if total >= budget:
-            break
-        picked.append(t)
-        total += T.size
-    acs = {s: native.AhoCorasick(b.sets[s]) for s in sorted(set(int(b.set_of_text[t])
-                                                               for t in picked))}
-
-    def step():
-        for t in picked:
-            acs[int(b.set_of_text[t])].search(b.texts[t], threads=threads)
-
+    o = OracleBatchSample(b, budget)
     for _ in range(args.warmup):
-        step()
+        o.step()
     t0 = time.perf_counter()
     for _ in range(args.steps):
-        step()
+        o.step()
     dt = time.perf_counter() - t0
-    value = total * args.steps / dt / 1e9
+    value = o.total * args.steps / dt / 1e9
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": "GB/s",
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": dt * 1e3 / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "u8", "data": "synthetic",
-        "config": {"workload": "batch-4096", "texts": len(picked), "bytes": total},
-        "cpu_baseline": {"value": value, "unit": "GB/s", "cores": threads, "kind": "oracle",
-                         "sample": "the first %d texts (%d MiB), each with its set's "
-                                   "Aho-Corasick automaton over %d threads"
-                                   % (len(picked), total >> 20, threads)},
+        "config": {"workload": "batch-4096", "texts": len(o.picked), "bytes": o.total},
+        "cpu_baseline": {"value": value, "unit": "GB/s", "cores": o.threads, "kind": "oracle",
+                         "sample": o.describe()},
         "e2e": {"value": value, "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
+    o.close()
     print(json.dumps(line))
 
 
@@ -250,7 +269,16 @@ def run_batch(args, rank):
     t0 = time.perf_counter()
     b = W.config4()
     gen_s = time.perf_counter() - t0
-    texts = [torch.from_numpy(t).to(dev) for t in b.texts]
+    # all texts in one device buffer (each at a 256-byte boundary), so that
+    # the end-to-end run moves them with one host-to-device copy
+    offs = np.zeros(len(b.texts) + 1, np.int64)
+    for i, t in enumerate(b.texts):
+        offs[i + 1] = (offs[i] + t.size + 255) & ~255
+    flat = np.zeros(int(offs[-1]), np.uint8)
+    for i, t in enumerate(b.texts):
+        flat[offs[i]: offs[i] + t.size] = t
+    dflat = torch.from_numpy(flat).to(dev)
+    texts = [dflat[int(offs[i]): int(offs[i]) + t.size] for i, t in enumerate(b.texts)]
     total = b.total_bytes
     # plain per-request form
     plain = [mpm.Matcher(P, sigma=b.sigma) for P in b.sets]
@@ -312,9 +340,16 @@ def run_batch(args, rank):
     learn_s = time.perf_counter() - t0
     BL = build(learned)
     exact_learned = bool(np.array_equal(result(BL), want))
-    learned_ms = timed(BL, "batch_timed")
+    with ClockSampler(dev.index) as clk:
+        learned_ms = timed(BL, "batch_timed")
     st = BL.stats
     launches = int(st["launches"]) * args.steps
+    # the scan kernel alone: events on either side of it inside the graph
+    scans = []
+    for _ in range(10):
+        BL.run()
+        scans.append(BL.stats["scan_ms"])
+    scan_ms = statistics.median(scans)
     BL.close()
     # batched + tuned: the exhaustive tuner on a sample of each set's texts
     t0 = time.perf_counter()
@@ -345,8 +380,40 @@ def run_batch(args, rank):
     e1.record()
     torch.cuda.synchronize()
     plain_ms = e0.elapsed_time(e1) / plain_steps
+
+    # end to end: the texts from pinned host memory (one copy), the batched
+    # run with the learned parameters, and its occurrence triples read back
+    # to the host
+    hflat = torch.empty(flat.size, dtype=torch.uint8, pin_memory=True)
+    hflat.numpy()[:] = flat
+    BL = build(learned)
+    BL.run()
+    e2e_steps = max(2, min(args.steps, 5))
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        dflat.copy_(hflat, non_blocking=True)
+        torch.cuda.synchronize()  # the batch runs on its own stream
+        got = [x.cpu() for x in BL.run()]
+    e2e_s = time.perf_counter() - t0
+    e2e_z = int(got[0].numel())
+    BL.close()
+    del hflat
     value = total / (learned_ms * 1e-3) / 1e9
     peak, peak_kind = peaks()
+    cpu = None
+    if not args.no_cpu_baseline:
+        o = OracleBatchSample(b, args.cpu_sample_mib << 20)
+        t0 = time.perf_counter()
+        oz = o.step()
+        dt = time.perf_counter() - t0
+        cpu = {"value": o.total / dt / 1e9, "unit": "GB/s", "cores": o.threads,
+               "kind": "oracle", "sample": o.describe() + " (%.2f s, %d occurrences)" % (dt, oz)}
+        o.close()
+    # the dominant kernel (batch_scan_kernel): algorithmic bytes per launch =
+    # every text byte once (candidate records stay in shared memory; the
+    # occurrence records it writes are a few hundred KB)
+    achieved = total / (scan_ms * 1e-3) / 1e9 if scan_ms > 0 else None
     line = {
         "metric": METRIC, "value": value, "unit": "GB/s", "n_gpus": 1, "steps": args.steps,
         "warmup": max(3, args.warmup), "ms_per_step": learned_ms, "higher_is_better": True,
@@ -369,6 +436,18 @@ def run_batch(args, rank):
         "bit_exact_vs_plain": exact_learned and exact_tuned, "occurrences": int(st["z"]),
         "candidates_per_step": int(st["candidates"]),
         "gpu_launches": launches,
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak if achieved else None,
+                     "traffic": recorded_traffic("batch-4096", {}, "batch_scan_kernel",
+                                                 batch_kernel_rev()),
+                     "kernel": "batch_scan_kernel", "peak_kind": peak_kind,
+                     "scan_ms": scan_ms,
+                     "note": "issue-bound (integer ALU and latency), not HBM-bound"},
+        "e2e": {"value": total * e2e_steps / e2e_s / 1e9, "unit": "GB/s",
+                "h2d_bytes_per_step": int(flat.size),
+                "d2h_bytes_per_step": 16 + 12 * e2e_z},
+        "clocks": clk.summary(),
+        "cpu_baseline": cpu,
         "setup_seconds": {"generate": round(gen_s, 1), "learned_choice": round(learn_s, 1),
                           "tune": round(tune_s, 1)},
     }
@@ -581,40 +660,52 @@ def parse_params(text):
     return out
 
 
-def kernel_rev():
-    """A hash of the specialised scan kernel's source and launch geometry, to
-    tie DRAM counters recorded under profiles/ to the code that made them."""
+def source_rev(files):
+    """A hash of kernel sources, to tie DRAM counters recorded under
+    profiles/ to the code that made them."""
     import hashlib
     h = hashlib.sha1()
-    for f in ("keyhash.h", "scan_jit_args.h", "ptx_common.cuh", "window_check.cuh",
-              "scan_jit.cuh", "jit.cpp"):
+    for f in files:
         with open(os.path.join(ROOT, "paper_1405_5483_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:12]
 
 
-def recorded_traffic(workload, params):
-    """DRAM bytes per launch of the scan kernel from the ncu summary of this
-    workload, when it was taken on the current kernel with these parameters.
-    The summary lists `kernel_rev` once and one `record` line (JSON with
-    params and traffic_bytes_per_launch) per captured parameter set."""
-    path = os.path.join(ROOT, "profiles", "mpm_scan_jit_%s.md" % workload)
+def kernel_rev():
+    """The specialised scan kernel's source and launch geometry."""
+    return source_rev(("keyhash.h", "scan_jit_args.h", "ptx_common.cuh", "window_check.cuh",
+                       "scan_jit.cuh", "jit.cpp"))
+
+
+def batch_kernel_rev():
+    """The batched kernel's source and its host side (units, launch)."""
+    return source_rev(("batch.cu", "stepper.cuh", "device_common.cuh", "window_check.cuh",
+                       "keyhash.h"))
+
+
+def recorded_traffic(workload, params, profile="mpm_scan_jit", rev=None):
+    """DRAM bytes per launch of the dominant kernel from the ncu summary of
+    this workload, when it was taken on the current kernel with these
+    parameters.  The summary lists `kernel_rev` once and one `record` line
+    (JSON with params and traffic_bytes_per_launch) per captured parameter
+    set."""
+    path = os.path.join(ROOT, "profiles", "%s_%s.md" % (profile, workload))
     if not os.path.exists(path):
         return None
-    rev, records = None, []
+    found, records = None, []
     for line in open(path):
         if not line.startswith("- `"):
             continue
         key, rest = line[3:].split("`", 1)
         val = rest.split(":", 1)[1].strip().strip("`") if ":" in rest else ""
         if key == "kernel_rev":
-            rev = val
+            found = val
         elif key == "record":
             try:
                 records.append(json.loads(val))
             except ValueError:
                 pass
-    if rev != kernel_rev():
+    if found != (rev if rev is not None else kernel_rev()):
         return None
     for rec in records:
         if all(params.get(k) == v for k, v in rec.get("params", {}).items()):

@@ -355,7 +355,9 @@ typedef struct {
     uint32_t launches;    /* kernels per run                                */
     float ms;             /* device time of the last run (events on the
                              batch stream around the graph launch)           */
-    float reserved;
+    float scan_ms;        /* device time of the last run's scan kernel alone
+                             (event records on either side of it, kept as
+                             nodes of the graph); 0 when unavailable          */
 } mpm_batch_stats;
 
 mpm_batch *mpm_batch_create(mpm_handle *const *sets, int nsets, const uint8_t *const *texts,

@@ -86,7 +86,7 @@ class BatchStats(ctypes.Structure):
     _fields_ = [("bytes", ctypes.c_uint64), ("candidates", ctypes.c_uint64),
                 ("z", ctypes.c_uint64), ("tiles", ctypes.c_uint32),
                 ("launches", ctypes.c_uint32), ("ms", ctypes.c_float),
-                ("reserved", ctypes.c_float)]
+                ("scan_ms", ctypes.c_float)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}

@@ -359,7 +359,8 @@ struct mpm_batch {
     bool use_graph = true;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
-    cudaEvent_t ev[2] = {nullptr, nullptr};
+    cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};  // run start/end, scan start/end
+    bool scan_events = true;  // ev[2..3] bracket the scan kernel (inside the graph too)
     uint64_t bytes = 0;
     mpm_batch_stats stats{};
 };
@@ -418,13 +419,22 @@ int alloc_buffers(mpm_batch* b, uint32_t cap) {
     return MPM_OK;
 }
 
+// An event record that is also kept when the stream is being captured (as
+// an event-record node of the graph, so that replays time the scan too).
+bool record_event(cudaEvent_t e, cudaStream_t s, bool capturing) {
+    return (capturing ? cudaEventRecordWithFlags(e, s, cudaEventRecordExternal)
+                      : cudaEventRecord(e, s)) == cudaSuccess;
+}
+
 // Counter reset, scan, sort, split and count read-back on the batch stream.
-int enqueue_batch(mpm_batch* b) {
+int enqueue_batch(mpm_batch* b, bool capturing = false) {
     cudaStream_t s = b->stream;
     if (cudaMemsetAsync(b->d_counters, 0, 16, s) != cudaSuccess) return MPM_ECUDA;
+    if (b->scan_events && !record_event(b->ev[2], s, capturing)) return MPM_ECUDA;
     mpm::batch_scan_kernel<<<b->num_sms, mpm::kBatchThreads, mpm::kBatchSmem, s>>>(
         b->d_sets, b->d_texts, b->d_tiles, b->d_units, b->nunits, b->d_occ, b->cap,
         b->d_counters);
+    if (b->scan_events && !record_event(b->ev[3], s, capturing)) return MPM_ECUDA;
     int l = mpm::launch_sort_dev(b->d_occ, b->d_tmp, b->d_hist, b->cap, b->d_counters + mpm::kBOcc,
                                  b->shifts, b->nshifts, b->num_sms, &b->sorted, s);
     if (l < 0) return MPM_ECUDA;
@@ -436,12 +446,10 @@ int enqueue_batch(mpm_batch* b) {
     return cudaPeekAtLastError() == cudaSuccess ? MPM_OK : MPM_ECUDA;
 }
 
-int capture(mpm_batch* b) {
-    drop_graph(b);
-    if (!b->use_graph) return MPM_OK;
+int capture_once(mpm_batch* b) {
     if (cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess)
         return MPM_ECUDA;
-    int rc = enqueue_batch(b);
+    int rc = enqueue_batch(b, true);
     cudaGraph_t g = nullptr;
     const cudaError_t e = cudaStreamEndCapture(b->stream, &g);
     if (rc || e != cudaSuccess || !g) {
@@ -450,7 +458,21 @@ int capture(mpm_batch* b) {
         return rc ? rc : MPM_ECUDA;
     }
     b->graph = g;
-    if (cudaGraphInstantiate(&b->exec, g, 0) != cudaSuccess) {
+    return MPM_OK;
+}
+
+int capture(mpm_batch* b) {
+    drop_graph(b);
+    if (!b->use_graph) return MPM_OK;
+    int rc = capture_once(b);
+    if (rc == MPM_ECUDA && b->scan_events) {
+        // a graph without the scan's event-record nodes: runs are still
+        // timed as a whole, the scan alone is not
+        b->scan_events = false;
+        rc = capture_once(b);
+    }
+    if (rc) return rc;
+    if (cudaGraphInstantiate(&b->exec, b->graph, 0) != cudaSuccess) {
         cudaGetLastError();
         drop_graph(b);
         return MPM_ECUDA;
@@ -523,6 +545,7 @@ mpm_batch* mpm_batch_create(mpm_handle* const* sets, int nsets, const uint8_t* c
                   cudaSuccess &&
               cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking) == cudaSuccess &&
               cudaEventCreate(&b->ev[0]) == cudaSuccess && cudaEventCreate(&b->ev[1]) == cudaSuccess &&
+              cudaEventCreate(&b->ev[2]) == cudaSuccess && cudaEventCreate(&b->ev[3]) == cudaSuccess &&
               cudaMalloc(&b->d_counters, 16) == cudaSuccess &&
               cudaMallocHost(&b->h_counters, 16) == cudaSuccess;
     // per-set descriptors pointing at the handles' device tables
@@ -711,9 +734,13 @@ int mpm_batch_run(mpm_batch* b, uint32_t* out_tid, uint32_t* out_pos, uint32_t* 
                 return set_error(MPM_ENOMEM);
             continue;
         }
-        float ms = 0.f;
+        float ms = 0.f, scan_ms = 0.f;
         cudaEventElapsedTime(&ms, b->ev[0], b->ev[1]);
+        if (!b->scan_events || cudaEventElapsedTime(&scan_ms, b->ev[2], b->ev[3]) != cudaSuccess)
+            scan_ms = 0.f;
+        cudaGetLastError();
         b->stats.ms = ms;
+        b->stats.scan_ms = scan_ms;
         b->stats.candidates = b->h_counters[mpm::kBCand];
         b->stats.z = zz;
         *z = zz;

@@ -95,6 +95,9 @@ def test_batch_matches_oracle_graph_and_plain(mpm, native):
             assert np.array_equal(got, want)
         st = b.stats
         assert st["z"] == want.shape[0] and st["bytes"] == sum(t.size for t in texts)
+        # the scan kernel's own time, from the events around it (graph nodes
+        # when replayed from the graph), lies inside the whole run's
+        assert 0.0 < st["scan_ms"] <= st["ms"]
         b.close()
 
 
