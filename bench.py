@@ -37,6 +37,12 @@ WORKLOADS = {
     "protein-256MiB-varlen": ("config2_varlen", 20,
                               "protein-like text 256 MiB, r=1000 patterns of lengths 16..64, "
                               "half planted (filter on the 16-byte prefixes)"),
+    # large pattern sets on uniform DNA: the verification-heavy regime
+    "dna-1GiB-r100k": ("config3", 4, "uniform DNA text 1 GiB, r=100,000, m=32, 10% planted"),
+    "dna-1GiB-r10k-m16": ("config3", 4, "uniform DNA text 1 GiB, r=10,000, m=16, 10% planted",
+                          {"r": 10_000, "m": 16}),
+    "dna-1GiB-r10k-m64": ("config3", 4, "uniform DNA text 1 GiB, r=10,000, m=64, 10% planted",
+                          {"r": 10_000, "m": 64}),
 }
 
 
@@ -132,8 +138,9 @@ class ClockSampler:
 
 def make_case(name):
     from paper_1405_5483_gb300 import workloads as W
-    gen, sigma, desc = WORKLOADS[name]
-    return getattr(W, gen)(), sigma, desc
+    gen, sigma, desc = WORKLOADS[name][:3]
+    kwargs = WORKLOADS[name][3] if len(WORKLOADS[name]) > 3 else {}
+    return getattr(W, gen)(**kwargs), sigma, desc
 
 
 def cpu_baseline(case, sample_bytes):

@@ -385,7 +385,8 @@ typedef struct {
     int max_sets;        /* at most this many sets are timed, lowest estimated
                             candidate rate first; 0 = 64                            */
     double max_rate;     /* sets whose estimated candidate records per sampled
-                            q-gram exceed this are not timed; 0 = 0.05              */
+                            q-gram exceed this are not timed, unless no set stays
+                            under it (then the lowest-rate sets are); 0 = 0.05      */
     int max_positions;   /* only sets with at most this many filter positions
                             (32 for mpm_batch); 0 = 64                              */
     int grid;            /* 0: the tuner's grid above; 1: every point of the cost
@@ -412,7 +413,10 @@ typedef struct {
  * pattern symbols distinct, low-order bits, for sigma' up to the pattern
  * alphabet; q-gram hashing into 2^10 .. 2^16 bins), q <= max_q and
  * k <= max_k is planned; sets whose estimated
- * candidate rate exceeds max_rate are dropped, the rest (at most max_sets)
+ * candidate rate exceeds max_rate are dropped (when that would drop every
+ * set, the max_sets sets of lowest rate are kept), the rest (at most max_sets,
+ * plus the planner's automatic choice, which is always timed unless
+ * max_table_kib excludes its table)
  * are built and timed on the sample T[0..n) (device or host memory) with
  * each kernel selected in opts->kernels.  *best receives the fastest set;
  * entries (may be NULL) receive up to cap timed sets in the order they were

@@ -115,6 +115,7 @@ extern "C" int mpm_autotune(const uint8_t* P, size_t r, size_t m, int sigma, con
     while (top < distinct && top < 256) top <<= 1;
 
     std::vector<Candidate> cands;
+    std::vector<Candidate> above_rate;  // timed only when no set passes max_rate
     if (o.grid < 0 || o.grid > 1) return set_error(MPM_EINVAL);
     if (o.grid == 1) {
         // exactly the cost model's grid (max_q, max_k, max_sets and max_rate unused)
@@ -143,12 +144,11 @@ extern "C" int mpm_autotune(const uint8_t* P, size_t r, size_t m, int sigma, con
             if (pl.p.k > max_k) continue;
             if (pl.info.table_bytes > max_table) continue;
             if (pl.info.positions > max_positions) continue;
-            if (pl.info.est_candidate_rate > max_rate) continue;
             Candidate c;
             c.plan = pl;
             c.p = pl.p;
             c.key = pl.info.est_candidate_rate / (double)(pl.p.q * pl.p.k);
-            cands.push_back(c);
+            (pl.info.est_candidate_rate > max_rate ? above_rate : cands).push_back(c);
         }
     };
     for (int sr = 2; o.grid == 0 && sr <= top; sr <<= 1) {
@@ -169,10 +169,40 @@ extern "C" int mpm_autotune(const uint8_t* P, size_t r, size_t m, int sigma, con
     // q-gram hashing: whole q-grams into 2^10 .. 2^16 bins
     for (int bits = 10; o.grid == 0 && bits <= 16; bits++)
         for (int q = 1; q <= std::min(max_q, 8); q++) add_all_k(MPM_MAP_QHASH, 1 << bits, q);
-    if (o.grid == 0) {
+    if (o.grid == 0 && cands.empty()) {
+        // every set sends more windows to verification than max_rate (large
+        // pattern sets): time the lowest-rate ones
+        std::stable_sort(above_rate.begin(), above_rate.end(),
+                         [](const Candidate& a, const Candidate& b) {
+                             return a.plan.info.est_candidate_rate <
+                                    b.plan.info.est_candidate_rate;
+                         });
+        cands.swap(above_rate);
+    } else if (o.grid == 0) {
         std::stable_sort(cands.begin(), cands.end(),
                          [](const Candidate& a, const Candidate& b) { return a.key < b.key; });
-        if (cands.size() > max_sets) cands.resize(max_sets);
+    }
+    if (o.grid == 0 && cands.size() > max_sets) cands.resize(max_sets);
+    if (o.grid == 0) {
+        // the planner's own choice (mpm_build with automatic parameters) is
+        // always timed too, whatever its q or table size, unless the caller
+        // bounded the table
+        mpm::Plan pa;
+        if (mpm::make_plan(P, r, m, sigma_eff, nullptr, &pa) == MPM_OK &&
+            pa.info.positions <= max_positions &&
+            (o.max_table_kib <= 0 || pa.info.table_bytes <= max_table)) {
+            bool dup = false;
+            for (const auto& c : cands)
+                dup = dup || (c.p.q == pa.p.q && c.p.sigma_r == pa.p.sigma_r && c.p.k == pa.p.k &&
+                              c.p.map_kind == pa.p.map_kind && c.p.map_shift == pa.p.map_shift);
+            if (!dup) {
+                Candidate c;
+                c.plan = pa;
+                c.p = pa.p;
+                c.key = 0.0;
+                cands.insert(cands.begin(), c);
+            }
+        }
     }
     if (cands.empty()) return set_error(MPM_EINVAL);
 

@@ -317,6 +317,22 @@ def test_autotune_picks_a_set_that_is_exact(mpm, native):
     check_search(mpm, native, c.T, c.P, 20, **best)
 
 
+def test_autotune_times_large_sets_above_the_rate_limit(mpm, native):
+    # r = 20 000 DNA patterns of m = 16: every filter the tuner plans sends
+    # more than 5 % of its sampled q-grams to verification, so it times the
+    # lowest-rate sets, and the planner's own choice, instead of refusing
+    c = W.dna_case(2 << 20, 20_000, 16, 2000)
+    auto = mpm.plan(c.P, 4)[0]
+    best, sets = mpm.autotune(c.P, 4, dev(c.T), kernels=3, max_sets=6, reps=1)
+    ok = [e for e in sets if e["status"] == 0]
+    assert ok
+    assert min(e["info"]["est_candidate_rate"] for e in sets) > 0.05
+    assert any(all(e["params"][k] == auto[k] for k in ("q", "sigma_r", "k", "map_kind"))
+               for e in sets)
+    assert len({e["z"] for e in ok}) == 1
+    check_search(mpm, native, c.T, c.P, 4, **best)
+
+
 def test_specialised_kernel_refuses_periods_it_cannot_stage(mpm):
     # k*q = 21: a stage holding whole periods would be lcm(21, 16) = 336 bytes
     c = W.english_case(1 << 14, 40, 64, 20)
