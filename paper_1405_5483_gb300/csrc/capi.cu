@@ -30,6 +30,10 @@ namespace {
 
 using mpm::set_error;
 
+// Largest key bitmap of a handle (1 MiB): about 1 % of the windows of a
+// 10^5-pattern set pass it and probe the pattern groups.
+constexpr uint32_t kVerifyKeyBits = 1u << 23;
+
 template <typename T>
 int grow(T** p, size_t* cap, size_t want) {
     if (*cap >= want && *p) return MPM_OK;
@@ -82,6 +86,7 @@ void release(mpm_handle* h) {
     cudaFree(h->d_pat);
     cudaFree(h->d_pat_off);
     cudaFree(h->d_pid);
+    cudaFree(h->d_keys);
     cudaFree(h->d_cand);
     cudaFree(h->d_occ);
     cudaFree(h->d_occ_tmp);
@@ -154,6 +159,8 @@ mpm::VerifyArgs verify_args(const mpm_handle* h, const uint8_t* dT, uint32_t n,
     v.pid = h->d_pid;
     v.pat_off = h->d_pat_off;
     v.key_bytes = h->host.key_bytes;
+    v.keys = h->d_keys;
+    v.key_mask = h->key_bits - 1;
     v.occ = occ;
     v.occ_cap = occ_cap;
     v.counters = counters;
@@ -411,7 +418,17 @@ static mpm_handle* build_handle(const uint8_t* P, size_t r, size_t m, int sigma,
         set_error(MPM_ECUDA);
         return nullptr;
     }
+    std::vector<uint32_t> keys;
+    try {
+        keys = mpm::key_bitmap(h->host, kVerifyKeyBits);
+    } catch (const std::bad_alloc&) {
+        delete h;
+        set_error(MPM_ENOMEM);
+        return nullptr;
+    }
+    h->key_bits = (uint32_t)keys.size() * 32;
     bool ok = cudaMalloc(&h->d_mu, 256) == cudaSuccess &&
+              cudaMalloc(&h->d_keys, keys.size() * 4) == cudaSuccess &&
               cudaMalloc(&h->d_table, h->table_bytes_padded) == cudaSuccess &&
               cudaMalloc(&h->d_slots, h->host.slots.size() * sizeof(mpm::Slot)) == cudaSuccess &&
               cudaMalloc(&h->d_pat, h->host.sorted_pat.size()) == cudaSuccess &&
@@ -424,6 +441,8 @@ static mpm_handle* build_handle(const uint8_t* P, size_t r, size_t m, int sigma,
               cudaHostAlloc(&h->h_snap, mpm::kNumCounters * 4, cudaHostAllocMapped) == cudaSuccess &&
               cudaHostGetDevicePointer(&h->d_snap, h->h_snap, 0) == cudaSuccess;
     ok = ok && cudaMemcpy(h->d_mu, h->host.mu, 256, cudaMemcpyHostToDevice) == cudaSuccess &&
+         cudaMemcpy(h->d_keys, keys.data(), keys.size() * 4, cudaMemcpyHostToDevice) ==
+             cudaSuccess &&
          cudaMemcpy(h->d_table, h->host.table.data(), h->table_bytes_padded,
                     cudaMemcpyHostToDevice) == cudaSuccess &&
          cudaMemcpy(h->d_slots, h->host.slots.data(), h->host.slots.size() * sizeof(mpm::Slot),

@@ -19,6 +19,8 @@ struct mpm_handle {
     uint8_t* d_pat = nullptr;
     uint32_t* d_pat_off = nullptr;  // row starts when the patterns differ in length
     uint32_t* d_pid = nullptr;
+    uint32_t* d_keys = nullptr;     // key bitmap of the pattern groups
+    uint32_t key_bits = 0;
 
     // scratch, grown on demand
     uint64_t* d_cand = nullptr;

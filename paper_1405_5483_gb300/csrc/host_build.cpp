@@ -558,6 +558,20 @@ int make_verify_tables_var(const uint8_t* cat, const size_t* off, size_t r, size
     return MPM_OK;
 }
 
+std::vector<uint32_t> key_bitmap(const HostTables& t, uint32_t max_bits) {
+    uint64_t groups = 0;
+    for (const auto& sl : t.slots) groups += sl.count ? 1 : 0;
+    uint32_t bits = 1u << 10;
+    while (bits < max_bits && bits < 64ull * groups) bits <<= 1;
+    std::vector<uint32_t> bm(bits / 32, 0u);
+    for (const auto& sl : t.slots) {
+        if (!sl.count) continue;
+        const uint32_t bit = (uint32_t)key_hash(sl.lo, sl.hi) & (bits - 1);
+        bm[bit / 32] |= 1u << (bit % 32);
+    }
+    return bm;
+}
+
 }  // namespace mpm
 
 // ------------------------------------------------------- host-only C ABI

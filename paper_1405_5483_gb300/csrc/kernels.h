@@ -58,6 +58,8 @@ struct VerifyArgs {
     const uint32_t* pid;  // pattern id of each sorted row
     const uint32_t* pat_off;  // row starts when the patterns differ in length, else null
     int key_bytes;
+    const uint32_t* keys;     // key bitmap of the pattern groups (key_mask + 1 bits)
+    uint32_t key_mask;
     uint64_t* occ;        // (pos << 32) | pid
     uint32_t occ_cap;
     uint32_t* counters;

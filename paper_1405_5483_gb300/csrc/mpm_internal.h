@@ -58,5 +58,9 @@ int make_verify_tables(const uint8_t* P, size_t r, size_t m, HostTables* out);
 // shortest mmin bytes long; keys are their first min(mmin, 16) bytes.
 int make_verify_tables_var(const uint8_t* cat, const size_t* off, size_t r, size_t mmin,
                            HostTables* out);
+// Bitmap of the pattern groups' key hashes (bit key_hash & (bits - 1)): 64
+// bits per group, a power of two between 2^10 and max_bits.  A window whose
+// key hash hits a clear bit has no pattern group to probe.
+std::vector<uint32_t> key_bitmap(const HostTables& t, uint32_t max_bits);
 
 }  // namespace mpm

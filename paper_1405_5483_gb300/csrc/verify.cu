@@ -5,10 +5,13 @@
 // A candidate record (fired << 32) | h stands, for every set bit j of fired,
 // for the window of q-grams starting at h0 = h - (m'-1)k - j, i.e. for the
 // text starts i = h0*q - s, s = 0..q-1 (each start has exactly one (h0, s)).
-// One thread takes one (record, s) pair.  A start i is looked up by the key
-// of its first min(m, 16) bytes in an open-addressing table of pattern
-// groups; the patterns of a matching group are compared byte by byte beyond
-// the key and every equal pattern id is appended as (i << 32) | pid.
+// One thread takes one record and walks its q starts in ascending order: the
+// key (first min(m, 16) bytes) of the first start is read from the text,
+// each next key drops a byte and takes in the byte after it.  A key whose
+// hash hits a clear bit of the key bitmap has no pattern group; the others
+// are looked up in the open-addressing table of pattern groups, the patterns
+// of a matching group compared byte by byte beyond the key, and every equal
+// pattern id appended as (i << 32) | pid.
 #include "device_common.cuh"
 #include "kernels.h"
 #include "window_check.cuh"
@@ -18,15 +21,18 @@ namespace mpm {
 namespace {
 
 __global__ void __launch_bounds__(256) verify_kernel(const VerifyArgs A) {
+    if (A.n < A.m) return;
     const uint32_t count = min(A.counters[kCandCount], A.cand_cap);
-    const uint64_t total = (uint64_t)count * A.q;
-    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
     const int64_t lead = (int64_t)(A.mprime - 1) * A.k;
+    const int64_t q = A.q;
+    const int64_t last = (int64_t)(A.n - A.m);  // the last start of a whole window
+    const uint32_t kb = (uint32_t)A.key_bytes;   // 1 .. 16
+    const uint32_t top = 8 * ((kb - 1) & 7);     // bit offset of a key's last byte
     WindowCtx wc;
     wc.T = A.T;
     wc.n = A.n;
     wc.m = A.m;
-    wc.key_bytes = (unsigned int)A.key_bytes;
+    wc.key_bytes = kb;
     wc.slot_mask = A.slot_mask;
     wc.occ_cap = A.occ_cap;
     wc.slots = A.slots;
@@ -37,10 +43,8 @@ __global__ void __launch_bounds__(256) verify_kernel(const VerifyArgs A) {
     wc.occ_count = &A.counters[kOccCount];
     wc.tag = 0;
     wc.pos_shift = 32;
-    for (uint64_t idx = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
-         idx += stride) {
-        const uint32_t c = (uint32_t)(idx / A.q);
-        const int s = (int)(idx % A.q);
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t c = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; c < count; c += stride) {
         const uint64_t rec = A.cand[c];
         const int64_t h = (int64_t)(uint32_t)rec;
         uint32_t fired = (uint32_t)(rec >> 32);
@@ -48,9 +52,28 @@ __global__ void __launch_bounds__(256) verify_kernel(const VerifyArgs A) {
             const int j = __ffs(fired) - 1;
             fired &= fired - 1;
             const int64_t h0 = h - lead - j;
-            const int64_t i = h0 * A.q - s;
-            if (i < 0 || i + (int64_t)A.m > (int64_t)A.n) continue;
-            check_window(wc, (uint32_t)i);
+            const int64_t first = max(h0 * q - (q - 1), (int64_t)0);
+            const int64_t end = min(h0 * q, last);
+            if (first > end) continue;
+            uint32_t i = (uint32_t)first;
+            unsigned long long lo, hi;
+            window_key(wc, i, &lo, &hi);
+            for (;;) {
+                const unsigned long long hs = key_hash(lo, hi);
+                const uint32_t bit = (uint32_t)hs & A.key_mask;
+                if ((__ldg(A.keys + (bit >> 5)) >> (bit & 31)) & 1u)
+                    probe_window(wc, i, lo, hi, hs);
+                if ((int64_t)i >= end) break;
+                // i + kb <= i + m - 1 < n: the byte after the key is in the text
+                const unsigned long long nb = __ldg(A.T + i + kb);
+                lo = (lo >> 8) | (hi << 56);
+                hi >>= 8;
+                if (kb <= 8)
+                    lo |= nb << top;
+                else
+                    hi |= nb << top;
+                i++;
+            }
         }
     }
 }
