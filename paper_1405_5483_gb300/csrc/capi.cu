@@ -30,10 +30,6 @@ namespace {
 
 using mpm::set_error;
 
-// Largest key bitmap of a handle (1 MiB): about 1 % of the windows of a
-// 10^5-pattern set pass it and probe the pattern groups.
-constexpr uint32_t kVerifyKeyBits = 1u << 23;
-
 template <typename T>
 int grow(T** p, size_t* cap, size_t want) {
     if (*cap >= want && *p) return MPM_OK;
@@ -420,7 +416,7 @@ static mpm_handle* build_handle(const uint8_t* P, size_t r, size_t m, int sigma,
     }
     std::vector<uint32_t> keys;
     try {
-        keys = mpm::key_bitmap(h->host, kVerifyKeyBits);
+        keys = mpm::key_bitmap(h->host, mpm::kVerifyKeyBitsMax);
     } catch (const std::bad_alloc&) {
         delete h;
         set_error(MPM_ENOMEM);

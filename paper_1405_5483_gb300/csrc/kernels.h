@@ -46,6 +46,9 @@ struct ScanArgs {
     uint32_t* counters;
 };
 
+// Largest key bitmap the verification kernel keeps in shared memory (64 KiB).
+constexpr uint32_t kVerifyKeyBitsMax = 1u << 19;
+
 struct VerifyArgs {
     const uint8_t* T;
     uint32_t n, m;
@@ -58,8 +61,8 @@ struct VerifyArgs {
     const uint32_t* pid;  // pattern id of each sorted row
     const uint32_t* pat_off;  // row starts when the patterns differ in length, else null
     int key_bytes;
-    const uint32_t* keys;     // key bitmap of the pattern groups (key_mask + 1 bits)
-    uint32_t key_mask;
+    const uint32_t* keys;     // key bitmap of the pattern groups (key_mask + 1 bits,
+    uint32_t key_mask;        // a power of two in 2^10 .. kVerifyKeyBitsMax)
     uint64_t* occ;        // (pos << 32) | pid
     uint32_t occ_cap;
     uint32_t* counters;

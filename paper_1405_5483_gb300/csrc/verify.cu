@@ -8,7 +8,9 @@
 // One thread takes one record and walks its q starts in ascending order: the
 // key (first min(m, 16) bytes) of the first start is read from the text,
 // each next key drops a byte and takes in the byte after it.  A key whose
-// hash hits a clear bit of the key bitmap has no pattern group; the others
+// hash hits a clear bit of the key bitmap (copied into shared memory by
+// every block: random bit tests there cost a few bank conflicts, where in L1
+// each lane's test is a cache line of its own) has no pattern group; the others
 // are looked up in the open-addressing table of pattern groups, the patterns
 // of a matching group compared byte by byte beyond the key, and every equal
 // pattern id appended as (i << 32) | pid.
@@ -20,8 +22,15 @@ namespace mpm {
 
 namespace {
 
-__global__ void __launch_bounds__(256) verify_kernel(const VerifyArgs A) {
+constexpr int kVerifyThreads = 1024;
+
+__global__ void __launch_bounds__(kVerifyThreads, 2) verify_kernel(const VerifyArgs A) {
+    extern __shared__ __align__(16) uint32_t s_keys[];
     if (A.n < A.m) return;
+    // the key bitmap: (key_mask + 1) / 8 bytes, a multiple of 128
+    for (uint32_t w = threadIdx.x; w < (A.key_mask + 1) / 128; w += blockDim.x)
+        reinterpret_cast<uint4*>(s_keys)[w] = __ldg(reinterpret_cast<const uint4*>(A.keys) + w);
+    __syncthreads();
     const uint32_t count = min(A.counters[kCandCount], A.cand_cap);
     const int64_t lead = (int64_t)(A.mprime - 1) * A.k;
     const int64_t q = A.q;
@@ -61,7 +70,7 @@ __global__ void __launch_bounds__(256) verify_kernel(const VerifyArgs A) {
             for (;;) {
                 const unsigned long long hs = key_hash(lo, hi);
                 const uint32_t bit = (uint32_t)hs & A.key_mask;
-                if ((__ldg(A.keys + (bit >> 5)) >> (bit & 31)) & 1u)
+                if ((s_keys[bit >> 5] >> (bit & 31)) & 1u)
                     probe_window(wc, i, lo, hi, hs);
                 if ((int64_t)i >= end) break;
                 // i + kb <= i + m - 1 < n: the byte after the key is in the text
@@ -81,7 +90,13 @@ __global__ void __launch_bounds__(256) verify_kernel(const VerifyArgs A) {
 }  // namespace
 
 int launch_verify(const VerifyArgs& a, int num_sms, cudaStream_t s) {
-    verify_kernel<<<num_sms * 8, 256, 0, s>>>(a);
+    static const bool sized = cudaFuncSetAttribute(verify_kernel,
+                                                   cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                   kVerifyKeyBitsMax / 8) == cudaSuccess;
+    const uint32_t bits = a.key_mask + 1;
+    if (!sized || !a.keys || bits < 1024 || bits > kVerifyKeyBitsMax || (bits & (bits - 1)))
+        return -1;
+    verify_kernel<<<num_sms * 2, kVerifyThreads, bits / 8, s>>>(a);
     return cudaPeekAtLastError() == cudaSuccess ? 1 : -1;
 }
 
