@@ -24,7 +24,7 @@ enum Counter : int {
 struct FilterDev {
     const void* table;        // mask table, global memory
     uint32_t table_bytes;     // padded to a multiple of 16
-    int entry_bytes;          // 1, 2, 4 or 8
+    int entry_bytes;          // 1, 2, 4, 8, or 16 (two words of state)
     int smem_table;           // copy the table into shared memory
     const uint8_t* mu;        // 256-entry byte -> reduced symbol map
     int map_kind, q, k, ell, shift, mprime, positions;
