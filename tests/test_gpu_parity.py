@@ -296,6 +296,48 @@ def test_full_size_dna_scaled(mpm, native):
     assert z >= 50
 
 
+def _pipelined_equals(mpm, native, T, P, sigma, params, searches=3):
+    """The benchmark's timed form: searches issued back to back with
+    mpm_search_async on one handle, each writing its own status row and
+    output buffers, then checked against the oracle."""
+    m = mpm.Matcher(P, sigma=sigma, **params)
+    Td = dev(T)
+    cap = max(1 << 16, 8 * P.shape[0])
+    outs = [(torch.empty(cap, dtype=torch.int32, device="cuda"),
+             torch.empty(cap, dtype=torch.int32, device="cuda")) for _ in range(searches)]
+    status = torch.zeros((searches, 4), dtype=torch.int32, device="cuda")
+    for i in range(searches):
+        m.search_async(Td, outs[i][0], outs[i][1], status[i])
+    m.sync()
+    wp, wi = native.aho_corasick(T, P, threads=_threads())
+    rows = status.cpu().numpy()
+    assert np.all(rows[:, 3] == 1) and np.all(rows[:, 2] == 0), rows
+    assert np.all(rows[:, 1] == wp.size), (rows, wp.size)
+    for pos, pid in outs:
+        assert np.array_equal(as_u32(pos[: wp.size]), wp)
+        assert np.array_equal(as_u32(pid[: wp.size]), wi)
+    return m
+
+
+@pytest.mark.parametrize("q", [4, 5])
+def test_full_size_protein_in_the_benchmarked_configuration(mpm, native, q):
+    # the parameter sets the tuner picks for the benchmark's workload (q-gram
+    # hashing into 2^16 bins, k = 1, the specialised kernel that verifies by
+    # itself), through the pipelined calls the benchmark times
+    c = W.config2()
+    m = _pipelined_equals(mpm, native, c.T, c.P, 20,
+                          dict(q=q, sigma_r=1 << 16, k=1, map_kind=4, kernel=2))
+    assert m.stats["specialised"] == 1
+
+
+def test_full_size_dna_in_the_benchmarked_configuration(mpm, native):
+    # 1 GiB DNA as the benchmark's dna-1GiB workload runs it: q = 8 over the
+    # low bits, k = 1, the specialised scan writing candidate records and the
+    # separate verification kernel
+    c = W.config1_scaled()
+    _pipelined_equals(mpm, native, c.T, c.P, 4, dict(q=8, sigma_r=4, k=1, map_kind=3, kernel=3))
+
+
 @pytest.mark.parametrize("r,mlen", [(100_000, 32), (10_000, 16), (10_000, 64)])
 def test_full_size_dna_large_sets(mpm, native, r, mlen):
     c = W.config3(r=r, m=mlen)
