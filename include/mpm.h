@@ -40,7 +40,7 @@ extern "C" {
 #define MPM_ECUDA      3  /* a CUDA call failed (no device, launch error ...) */
 #define MPM_ECAPACITY  4  /* output capacity too small; *z = required count  */
 #define MPM_ETIMEOUT   5  /* a bounded device wait gave up; results invalid  */
-#define MPM_ENOTSUP    6  /* combination not supported by this build         */
+#define MPM_ENOTSUP    6  /* parameter combination the library does not run  */
 #define MPM_ESCRATCH   7  /* mpm_search_noalloc: its fixed scratch is too small */
 
 /* ----------------------------------------------------- parameter choices */

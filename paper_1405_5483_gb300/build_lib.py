@@ -3,7 +3,7 @@
 Every translation unit is compiled in parallel with nvcc, then linked into
 paper_1405_5483_gb300/_build/libmpm.so with the CUDA runtime linked
 statically, so the library loads on a machine without a GPU (for symbol
-checks) and needs only the driver when it runs.
+checks) and needs only the NVIDIA kernel driver when it runs.
 """
 import concurrent.futures
 import os
