@@ -121,8 +121,9 @@ typedef struct {
     int entry_bytes;   /* bytes per mask-table entry: 1, 2, 4, 8 or 16        */
     uint64_t entries;  /* sigma_r^q                                           */
     uint64_t table_bytes;
-    double est_candidate_rate; /* estimated candidate records per sampled q-gram,
-                                  from the pattern-set symbol frequencies       */
+    double est_candidate_rate; /* expected candidate windows (fired subpatterns)
+                                  per sampled q-gram in i.i.d. text with the
+                                  pattern set's symbol frequencies, at most 1  */
 } mpm_table_info;
 
 /* Counters of the last mpm_search / mpm_scan on a handle. */

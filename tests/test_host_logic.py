@@ -241,3 +241,41 @@ def test_specialised_scan_compiles(mpm, alpha, mlen, kw):
     if rc == mpm.MPM_ENOTSUP and "NVRTC not found" in log:
         pytest.skip("NVRTC is not installed here")
     assert rc == mpm.MPM_OK, log
+
+
+RATE_CASES = [
+    ("dna", 100, 16, dict(q=4, sigma_r=4, k=1, map_kind=3)),
+    ("dna", 100, 16, dict(q=6, sigma_r=4, k=1, map_kind=3)),
+    ("dna", 300, 32, dict(q=5, sigma_r=4, k=2, map_kind=3)),
+    ("protein", 200, 32, dict(q=2, sigma_r=16, k=2, map_kind=1)),
+    ("protein", 1000, 16, dict(q=3, sigma_r=1 << 10, k=1, map_kind=4)),
+    ("english", 100, 12, dict(q=3, sigma_r=16, k=1, map_kind=2)),
+    ("english", 400, 16, dict(q=2, sigma_r=32, k=2, map_kind=2)),
+]
+
+
+@pytest.mark.parametrize("alpha,r,mlen,kw", RATE_CASES)
+def test_planner_rate_is_the_oracle_filters_window_rate(mpm, alpha, r, mlen, kw):
+    """The planner's estimated candidate rate (the tuner orders and prunes by
+    it, the batched kernel weighs work units by it) is the expected number of
+    candidate windows per sampled q-gram: on 1 MiB of i.i.d. text from the
+    patterns' own source, with no pattern planted, the oracle's AOSO scan
+    sends that many windows to verification (within 10 % plus three standard
+    deviations of the count, or at least 0.9 where the estimate is capped
+    at 1)."""
+    from paper_1405_5483_gb300 import workloads as W
+    make = {"dna": W.dna_case, "protein": W.protein_case, "english": W.english_case}[alpha]
+    c = make(1 << 20, r, mlen, 0, cfg=40 + r % 7)
+    p, info = mpm.plan(c.P, c.sigma, **kw)
+    kind = {1: "rank", 2: "greedy", 3: "lowbits", 4: "qhash"}[p["map_kind"]]
+    fp = F.make_params(c.P, p["q"], p["sigma_r"], p["k"], kind, shift=p["map_shift"])
+    cls = F.pattern_classes(c.P, fp)
+    codes = F.text_codes(c.T, fp)
+    windows = len(F.aoso_scan(codes, F.mask_table(cls, fp), fp, len(cls)))
+    steps = len(range(p["k"] - 1, len(codes), p["k"]))
+    rate, est = windows / steps, info["est_candidate_rate"]
+    assert windows > 500
+    if est >= 1.0:
+        assert rate >= 0.9
+    else:
+        assert abs(rate - est) <= 0.1 * est + 3 * np.sqrt(windows) / steps, (rate, est)
