@@ -90,11 +90,13 @@ __global__ void __launch_bounds__(kVerifyThreads, 2) verify_kernel(const VerifyA
 }  // namespace
 
 int launch_verify(const VerifyArgs& a, int num_sms, cudaStream_t s) {
-    static const bool sized = cudaFuncSetAttribute(verify_kernel,
-                                                   cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                   kVerifyKeyBitsMax / 8) == cudaSuccess;
     const uint32_t bits = a.key_mask + 1;
-    if (!sized || !a.keys || bits < 1024 || bits > kVerifyKeyBitsMax || (bits & (bits - 1)))
+    if (!a.keys || bits < 1024 || bits > kVerifyKeyBitsMax || (bits & (bits - 1))) return -1;
+    // above the default 48 KiB of dynamic shared memory (set on the current
+    // device, at every such launch)
+    if (bits / 8 > 48 * 1024 &&
+        cudaFuncSetAttribute(verify_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)(bits / 8)) != cudaSuccess)
         return -1;
     verify_kernel<<<num_sms * 2, kVerifyThreads, bits / 8, s>>>(a);
     return cudaPeekAtLastError() == cudaSuccess ? 1 : -1;
