@@ -531,6 +531,28 @@ def main():
             dist.barrier()
         torch.cuda.synchronize()
 
+    # a text that fits in L2 would be timed warm: then L2 is flushed (a write
+    # of twice its size) before every timed search, outside the search's events
+    l2 = int(getattr(torch.cuda.get_device_properties(dev), "L2_cache_size", 0) or 129 * 10**6)
+    flush = torch.empty(2 * l2, dtype=torch.uint8, device=dev) if case.n < l2 else None
+
+    def timed_flushed(k, search):
+        """k searches, each after an L2 flush, each timed alone; the sum."""
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+               for _ in range(k)]
+        barrier()
+        for i, (a, b) in enumerate(evs):
+            flush.zero_()
+            a.record(stream)
+            search(i)
+            b.record(stream)
+        barrier()
+        return sum(a.elapsed_time(b) for a, b in evs)
+
+    def pipelined_step(i):
+        m.search_async(T, out_pos, out_pid, status[i])
+        m.join()  # its closing sort belongs to the step
+
     def timed_pipelined():
         """Searches issued back to back (mpm_search_async), each writing its
         own status row; the stream never waits for the host."""
@@ -538,6 +560,11 @@ def main():
             m.search_async(T, out_pos, out_pid, status[0])
         m.sync()
         m.reset_stats()
+        if flush is not None:
+            with ClockSampler(local) as clk:
+                ms = timed_flushed(steps, pipelined_step)
+            m.sync()
+            return ms, clk
         ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         with ClockSampler(local) as clk:
             barrier()
@@ -554,6 +581,8 @@ def main():
         """The same searches, one synchronous mpm_search call each."""
         for _ in range(max(3, args.warmup)):
             m.search_into(T, out_pos, out_pid)
+        if flush is not None:
+            return timed_flushed(k, lambda i: m.search_into(T, out_pos, out_pid))
         ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         barrier()
         ev0.record(stream)
@@ -626,7 +655,9 @@ def main():
             "scaling": "weak", "vs_baseline": None, "dtype": "u8", "data": "synthetic",
             "config": {"workload": args.workload, "description": desc, "n": case.n,
                        "r": case.r, "m": case.m, "params": m.params, "tuning": tuning,
-                       "l2": "inputs larger than L2 (no flush)",
+                       "l2": ("inputs larger than L2 (no flush)" if flush is None else
+                              "text smaller than L2: L2 flushed (a %d-byte write) before "
+                              "every timed search, outside its events" % (2 * l2)),
                        "parallelism": "replicas" if world > 1 else "single GPU"},
             "hbm_frac_of_%s_peak" % peak_kind: value / peak,
             "form": ("pipelined: mpm_search_async back to back, every step's status checked "
