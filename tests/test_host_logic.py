@@ -227,6 +227,13 @@ JIT_GRID = [
     ("protein", 32, dict(q=4, sigma_r=1 << 16, k=1, map_kind=4)),
     ("protein", 32, dict(q=6, sigma_r=1 << 14, k=2, map_kind=4)),
     ("english", 64, dict(q=8, sigma_r=1 << 12, k=3, map_kind=4)),
+    # the benchmarked filters: protein q 5 hashed into 2^16 bins (verifying
+    # variant), DNA q 8 low bits (split), q 11 k 2 (m = 64), q 13 (a 64 MiB
+    # table in global memory)
+    ("protein", 32, dict(q=5, sigma_r=1 << 16, k=1, map_kind=4, kernel=2)),
+    ("dna", 16, dict(q=8, sigma_r=4, k=1, map_kind=3, kernel=3)),
+    ("dna", 64, dict(q=11, sigma_r=4, k=2, map_kind=3, kernel=2)),
+    ("dna", 32, dict(q=13, sigma_r=4, k=1, map_kind=3, kernel=3)),
 ]
 
 
