@@ -898,6 +898,8 @@ constexpr size_t kNaMaxCand = MPM_NOALLOC_MAX_CANDIDATES;
 constexpr size_t kNaMaxOcc = MPM_NOALLOC_MAX_OCCURRENCES;
 constexpr size_t kNaBytes = MPM_NOALLOC_SCRATCH_BYTES;
 static_assert(kNaBytes == kNaCounterBytes + 8 * (kNaMaxCand + kNaMaxOcc), "scratch layout");
+// more occurrences than this would need the radix sort's temporary buffers
+static_assert(kNaMaxOcc <= mpm::kSortSmallMax, "occurrence limit within the one-block sort");
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNaBytes];
 
@@ -942,10 +944,17 @@ extern "C" int mpm_search_noalloc(mpm_handle* h, const uint8_t* T, size_t n, uin
     uint64_t* occ = cand + kNaMaxCand;
 
     const size_t out_capacity = *z;
+    // as in mpm_search: closing sorts of pipelined searches still running on
+    // the side stream may write the same outputs, so later work waits for
+    // them; their pending timings belong to the statistics reset below
+    rc = join_sorts(h);
+    if (rc) return set_error(rc);
+    rc = harvest_timing(h, true);
+    if (rc) return set_error(rc);
     h->stats = mpm_stats{};
     h->stats.n = n;
     h->stats.sampled = (n / (uint32_t)h->plan.p.q) / (uint32_t)h->plan.p.k;
-    h->stats.specialised = fused_search(h) ? 1u : 0u;
+    h->stats.specialised = (h->jit || h->jit_cand) && !h->plan.p.smag ? 1u : 0u;
     if (n < h->plan.m) {
         *z = 0;
         return set_error(MPM_OK);

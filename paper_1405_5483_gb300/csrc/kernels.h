@@ -132,6 +132,9 @@ int launch_rank_sort(const uint64_t* keys, uint32_t* counters, uint32_t out_cap,
 
 // Sorts z keys (in d_keys, device count unknown to the kernels: z is passed)
 // and writes out_pos/out_pid.  tmp must hold z keys; returns launches or -1.
+// Up to kSortSmallMax keys the sort runs in one block's shared memory and
+// touches neither tmp nor hist (both may then be null).
+constexpr uint32_t kSortSmallMax = 8192;
 int launch_sort_output(uint64_t* d_keys, uint64_t* d_tmp, uint32_t* d_hist, size_t hist_cap,
                        uint32_t z, uint32_t key_bits, uint32_t* out_pos, uint32_t* out_pid,
                        cudaStream_t s);

@@ -22,7 +22,7 @@ namespace mpm {
 
 namespace {
 
-constexpr int kSmallSort = 8192;
+constexpr int kSmallSort = (int)kSortSmallMax;
 constexpr int kRadixThreads = 256;
 constexpr int kRadixWarps = kRadixThreads / 32;
 constexpr int kRadixTile = 4096;  // keys per block

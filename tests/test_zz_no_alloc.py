@@ -43,12 +43,20 @@ def _noalloc(mpm, matcher, T, cap):
     return rc, z.value, out_pos, out_pid
 
 
-def test_noalloc_equals_search_on_two_calls_in_a_row(mpm):
+# The automatic choice (the specialised scan that verifies its candidates
+# itself), the generic kernel and the split specialised scan: the last two
+# keep candidate records in the shared array and verify them in a second
+# kernel.
+KERNELS = [("auto", {}), ("generic", {"kernel": 1}), ("split", {"kernel": 3})]
+
+
+@pytest.mark.parametrize("name,kw", KERNELS, ids=[k for k, _ in KERNELS])
+def test_noalloc_equals_search_on_two_calls_in_a_row(mpm, name, kw):
     from paper_1405_5483_gb300 import workloads as W
     cases = [W.dna_case(1 << 20, 100, 16, 50), W.protein_case((1 << 22) + 13, 300, 32, 150)]
     built = []
     for c in cases:
-        m = mpm.Matcher(c.P, sigma=c.sigma)
+        m = mpm.Matcher(c.P, sigma=c.sigma, **kw)
         T = torch.from_numpy(c.T).cuda()
         ref_pos, ref_pid = m.search(T)
         torch.cuda.synchronize()
@@ -74,3 +82,51 @@ def test_noalloc_rejects_more_occurrences_than_its_scratch_holds(mpm):
     # the regular search still handles it
     pos, _ = m.search(T)
     assert pos.numel() == z
+
+
+def test_noalloc_rejects_more_candidates_than_its_scratch_holds(mpm):
+    from paper_1405_5483_gb300._native import MPM_ESCRATCH, NOALLOC_MAX_CANDIDATES
+    # every q-gram of an all-A text matches the filter of AAAAAAAAAAAAAAAC
+    # (q = 2: seven positions, each accepting "AA"), so every sampled q-gram
+    # is a candidate record while no window is an occurrence
+    n = 4 * NOALLOC_MAX_CANDIDATES
+    T = torch.full((n,), 65, dtype=torch.uint8, device="cuda")
+    P = np.frombuffer(b"AAAAAAAAAAAAAAAC", np.uint8).reshape(1, 16)
+    for kernel in (1, 3):
+        m = mpm.Matcher(P, sigma=4, q=2, k=1, sigma_r=4, map_kind=mpm.MAP_RANK, kernel=kernel)
+        rc, z, _, _ = _noalloc(mpm, m, T, 4096)
+        assert rc == MPM_ESCRATCH
+        assert z == 0
+        assert m.stats["candidates"] > NOALLOC_MAX_CANDIDATES
+        # the regular search finds the same (empty) list
+        pos, _ = m.search(T)
+        assert pos.numel() == 0
+
+
+def test_noalloc_after_pipelined_search_into_the_same_outputs(mpm):
+    """A pipelined search's closing sort runs on a side stream; a following
+    allocation-free search into the same outputs is ordered after it."""
+    from paper_1405_5483_gb300 import workloads as W
+    c = W.protein_case(1 << 24, 1000, 32, 500)
+    m = mpm.Matcher(c.P, sigma=c.sigma)
+    T1 = torch.from_numpy(c.T).cuda()
+    # the first quarter of the text: a different, shorter occurrence list
+    T2 = T1[: 1 << 22].clone()
+    ref_pos, ref_pid = m.search(T2)
+    ref_pos, ref_pid = ref_pos.cpu().numpy(), ref_pid.cpu().numpy()
+    cap = 4096
+    out_pos = torch.full((cap,), -1, dtype=torch.int32, device="cuda")
+    out_pid = torch.full((cap,), -1, dtype=torch.int32, device="cuda")
+    status = torch.zeros(4, dtype=torch.int32, device="cuda")
+    lib = mpm.lib()
+    for _ in range(3):
+        m.search_async(T1, out_pos, out_pid, status)
+        z = ctypes.c_size_t(cap)
+        rc = lib.mpm_search_noalloc(m._h, T2.data_ptr(), T2.numel(), out_pos.data_ptr(),
+                                    out_pid.data_ptr(), ctypes.byref(z))
+        assert rc == mpm.MPM_OK, lib.mpm_strerror(rc)
+        m.sync()
+        zz = z.value
+        assert zz == ref_pos.size
+        assert np.array_equal(out_pos[:zz].cpu().numpy(), ref_pos)
+        assert np.array_equal(out_pid[:zz].cpu().numpy(), ref_pid)
