@@ -512,7 +512,7 @@ def main():
         # patterns of different lengths: the filter's parameters are tuned on
         # their common-length prefixes
         params, sets = mpm.autotune(case.prefix_matrix(), sigma, sample, kernels=3,
-                                    max_sets=args.tune_sets)
+                                    max_sets=args.tune_sets, overlap=1)
         tuning = {"sample_bytes": int(sample.numel()), "sets_timed": len(sets),
                   "seconds": round(time.perf_counter() - t0, 2)}
     m = mpm.Matcher(case.P, sigma=sigma, **params)

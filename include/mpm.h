@@ -79,15 +79,16 @@ extern "C" {
  *   kernel   MPM_KERNEL_*: the scan kernel compiled at build time for
  *            these parameters (NVRTC, sm_103a), or the precompiled generic
  *            one; AUTO takes the specialised kernel when it compiles.  The
- *            specialised kernel needs lcm(k*q, 16) <= 256 (an explicit
- *            request outside that fails with MPM_ENOTSUP); the generic one
+ *            specialised kernel needs lcm(P, 16) <= 256, P = k*q text bytes
+ *            per sampled q-gram (k with overlap = 1; an explicit request
+ *            outside that fails with MPM_ENOTSUP); the generic one
  *            hashes q-grams of at most 5 bytes (MPM_ENOTSUP from the search
  *            otherwise).
  *   overlap  0: MAG's non-overlapping q-grams of all q shifts; 1: the
  *            overlapping q-grams of Section 2 (P_i[j..j+q-1], j < m-q+1, no
  *            shifts; the text's q-gram at every byte, every k-th one read),
- *            L' = m - q + 1.  Runs in the generic kernel (AUTO resolves to
- *            it; SPECIALISED, SPLIT, SMAG and mpm_batch answer MPM_ENOTSUP).
+ *            L' = m - q + 1.  Runs in the specialised kernels and the
+ *            generic one; SMAG and mpm_batch answer MPM_ENOTSUP.
  *   wide     0: at most 64 filter positions (one 64-bit word of Shift-Or
  *            state); 1: at most 128 (two words, Section 3.2's ceil((m/q)/w)
  *            words; mask table entries of 16 bytes above 64 positions).  Runs
@@ -394,6 +395,10 @@ typedef struct {
                             model's grid (mpm_model_grid)                          */
     int max_table_kib;   /* only sets whose mask table has at most this many KiB;
                             0 = 16384                                               */
+    int overlap;         /* 0: MAG's non-overlapping q-grams only; 1: those and
+                            the overlapping q-grams of Section 2, each family
+                            ranked on its own and given half of max_sets; 2: the
+                            overlapping ones only (tuner grid only)                */
 } mpm_tune_opts;
 
 typedef struct {
@@ -413,7 +418,8 @@ typedef struct {
  * mapping and sigma' (equal-weight greedy bins and, where they keep the
  * pattern symbols distinct, low-order bits, for sigma' up to the pattern
  * alphabet; q-gram hashing into 2^10 .. 2^16 bins), q <= max_q and
- * k <= max_k is planned; sets whose estimated
+ * k <= max_k is planned, with non-overlapping and/or overlapping q-grams as
+ * opts->overlap asks; sets whose estimated
  * candidate rate exceeds max_rate are dropped (when that would drop every
  * set, the max_sets sets of lowest rate are kept), the rest (at most max_sets,
  * plus the planner's automatic choice, which is always timed unless

@@ -79,14 +79,15 @@ def host_tables(P, sigma, **kw):
 
 
 def autotune(P, sigma, T, max_q=0, max_k=0, reps=0, kernels=0, max_sets=0, max_rate=0.0,
-             max_positions=0, grid=0, max_table_kib=0):
+             max_positions=0, grid=0, max_table_kib=0, overlap=0):
     """Exhaustive parameter search timed on the sample text T (CUDA tensor or
-    numpy).  grid=1 times every point of the cost model's grid.  Returns
+    numpy).  grid=1 times every point of the cost model's grid; overlap=1
+    also times overlapping-q-gram filters (2: only those).  Returns
     (best params dict, list of timed sets)."""
     from ._native import TuneEntry, TuneOpts
     P = _patterns(P)
     opts = TuneOpts(max_q, max_k, reps, kernels, max_sets, max_rate, max_positions, grid,
-                    max_table_kib)
+                    max_table_kib, overlap)
     cap = 4096
     entries = (TuneEntry * cap)()
     best = Params()

@@ -54,7 +54,8 @@ class TuneOpts(ctypes.Structure):
     _fields_ = [("max_q", ctypes.c_int), ("max_k", ctypes.c_int), ("reps", ctypes.c_int),
                 ("kernels", ctypes.c_int), ("max_sets", ctypes.c_int),
                 ("max_rate", ctypes.c_double), ("max_positions", ctypes.c_int),
-                ("grid", ctypes.c_int), ("max_table_kib", ctypes.c_int)]
+                ("grid", ctypes.c_int), ("max_table_kib", ctypes.c_int),
+                ("overlap", ctypes.c_int)]
 
 
 MODEL_INPUTS, MODEL_HIDDEN, MODEL_PARAMS = 8, 64, 4801

@@ -380,8 +380,8 @@ static mpm_handle* build_handle(const uint8_t* P, size_t r, size_t m, int sigma,
         set_error(rc);
         return nullptr;
     }
-    if (h->plan.p.overlap || h->plan.p.wide) {
-        // overlapping q-grams and two-word state run in the generic kernel only
+    if (h->plan.p.wide) {
+        // two words of state run in the generic kernels only
         if (h->plan.p.smag || h->plan.p.kernel == MPM_KERNEL_SPECIALISED ||
             h->plan.p.kernel == MPM_KERNEL_SPLIT) {
             delete h;
@@ -389,6 +389,12 @@ static mpm_handle* build_handle(const uint8_t* P, size_t r, size_t m, int sigma,
             return nullptr;
         }
         h->plan.p.kernel = MPM_KERNEL_GENERIC;
+    }
+    if (h->plan.p.overlap && h->plan.p.smag) {
+        // SMAG encodes the text's non-overlapping q-grams only
+        delete h;
+        set_error(MPM_ENOTSUP);
+        return nullptr;
     }
     // host tables
     try {
@@ -796,7 +802,7 @@ int mpm_jit_compile(const uint8_t* P, size_t r, size_t m, int sigma, const mpm_p
     mpm::Plan plan;
     int rc = mpm::make_plan(P, r, m, sigma, params, &plan);
     if (rc) return set_error(rc);
-    if (plan.p.overlap || plan.p.wide) return set_error(MPM_ENOTSUP);  // generic kernel only
+    if (plan.p.wide) return set_error(MPM_ENOTSUP);  // generic kernels only
     mpm::FilterDev f{};
     f.table_bytes = (uint32_t)((plan.info.table_bytes + 15) & ~uint64_t(15));
     f.entry_bytes = plan.info.entry_bytes;
@@ -808,6 +814,7 @@ int mpm_jit_compile(const uint8_t* P, size_t r, size_t m, int sigma, const mpm_p
     f.shift = plan.p.map_shift;
     f.mprime = plan.info.mprime;
     f.positions = plan.info.positions;
+    f.overlap = plan.p.overlap;
     // both variants: the one mpm_search runs and the candidate one of mpm_scan
     std::string text;
     rc = mpm::jit_compile_only(f, true, &text);

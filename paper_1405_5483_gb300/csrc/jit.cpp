@@ -127,7 +127,7 @@ constexpr size_t kSmemLimit = 227 * 1024;
 
 // Compile-time constants of one specialisation and its launch geometry.
 struct JitSpec {
-    int q, k, mp, ell, shift, mode, eb, smem, table_bytes, C, S, warps, verify, ecap;
+    int q, k, mp, ell, shift, mode, eb, smem, table_bytes, C, S, warps, verify, ecap, ov;
     size_t smem_bytes;
 
     std::string defines() const {
@@ -135,9 +135,10 @@ struct JitSpec {
         std::snprintf(buf, sizeof(buf),
                       "-DMPM_Q=%d -DMPM_K=%d -DMPM_MP=%d -DMPM_ELL=%d -DMPM_SHIFT=%d "
                       "-DMPM_MODE=%d -DMPM_EB=%d -DMPM_SMEM=%d -DMPM_TABLE_BYTES=%du "
-                      "-DMPM_C=%d -DMPM_S=%d -DMPM_WARPS=%d -DMPM_VERIFY=%d -DMPM_EMIT_CAP=%d",
+                      "-DMPM_C=%d -DMPM_S=%d -DMPM_WARPS=%d -DMPM_VERIFY=%d -DMPM_EMIT_CAP=%d "
+                      "-DMPM_OV=%d",
                       q, k, mp, ell, shift, mode, eb, smem, table_bytes, C, S, warps, verify,
-                      ecap);
+                      ecap, ov);
         return buf;
     }
 };
@@ -163,16 +164,21 @@ bool jit_spec(const FilterDev& f, bool verify, JitSpec* out) {
     s.eb = f.entry_bytes;
     s.smem = f.smem_table ? 1 : 0;
     s.table_bytes = f.smem_table ? (int)f.table_bytes : 0;
-    const uint32_t P = (uint32_t)(f.k * f.q);
+    s.ov = f.overlap ? 1 : 0;
+    if (f.entry_bytes > 8) return false;  // two words of state: generic kernels only
+    // bytes per sampled q-gram: k q non-overlapping, k overlapping
+    const uint32_t P = (uint32_t)(s.ov ? f.k : f.k * f.q);
     const uint32_t base = lcm_u(P, 16);
     if (base > 256) return false;
     // stage rows of at least 80 bytes (48-byte rows measured up to 3x slower
     // on GB300); odd multiples of base keep C/16 odd, which keeps the 16-byte
     // shared loads of a quarter warp on distinct banks
-    // (and at most 64 report bits per stage: C / P * k <= 64)
+    // (and, non-overlapping, at most 64 report bits per stage: C / P * k <= 64;
+    // the overlapping stage finds its report bits again only when one fired)
+    auto bits_ok = [&](uint32_t c) { return s.ov || c / P * (uint32_t)f.k <= 64; };
     uint32_t C = base;
     const uint32_t step = ((base / 16) % 2 == 1) ? 2 * base : base;
-    while (C < 80 && C + step <= 256 && (C + step) / P * (uint32_t)f.k <= 64) C += step;
+    while (C < 80 && C + step <= 256 && bits_ok(C + step)) C += step;
     s.warps = 16;
     // overrides for tuning the geometry: MPM_JIT_C (stage bytes, a multiple
     // of lcm(k q, 16) up to 256) and MPM_JIT_WARPS (4..32)
@@ -184,7 +190,7 @@ bool jit_spec(const FilterDev& f, bool verify, JitSpec* out) {
         const int w = std::atoi(e);
         if (w >= 4 && w <= 32) s.warps = w;
     }
-    if ((C / P) * (uint32_t)f.k > 64) return false;
+    if (!bits_ok(C)) return false;
     s.C = (int)C;
     for (;;) {
         const size_t fixed =
@@ -369,10 +375,13 @@ int launch_scan_jit(const ScanArgs& A, const VerifyArgs* V, const JitKernel* K, 
     const JitSpec& s = K->spec;
     const uint32_t n = A.n;
     const uint32_t C = (uint32_t)s.C;
-    const uint32_t P = (uint32_t)(s.k * s.q);
+    const uint32_t P = (uint32_t)(s.ov ? s.k : s.k * s.q);
     const uint32_t blocks = (uint32_t)(num_sms * K->blocks_per_sm);
     const uint32_t GW = blocks * (uint32_t)s.warps;
-    const uint32_t warm = ((uint32_t)((s.mp - 1) * s.q * s.k) + C - 1) / C * C;
+    // bytes of the samples before a row (overlapping: and a sample's first
+    // q-1 bytes), in whole stages
+    const uint32_t wb = (uint32_t)((s.mp - 1) * (int)P + (s.ov ? s.q - 1 : 0));
+    const uint32_t warm = (wb + C - 1) / C * C;
     const uint32_t row_warps = GW > 1 ? GW - 1 : 1;
     uint64_t Lst = chunk > 0 ? (uint64_t)chunk : ((uint64_t)n + 32ull * row_warps - 1) / (32ull * row_warps);
     Lst = (Lst + C - 1) / C * C;

@@ -18,6 +18,10 @@
 //   MPM_VERIFY        1: verify the candidates in the kernel and append
 //                     occurrences; 0: append the candidate records
 //   MPM_EMIT_CAP      records a warp buffers in shared memory
+//   MPM_OV            0: MAG's non-overlapping q-grams of all q shifts;
+//                     1: the overlapping q-grams of Section 2 (the text's
+//                     q-gram at every byte, every k-th read, a window at its
+//                     own start)
 //
 // Layout and flow.  Rows of Lst bytes (a multiple of C, starting on a
 // multiple of k*q) are owned by threads; a warp streams its 32 rows through
@@ -35,6 +39,16 @@
 // compared byte by byte (Section 3.2), while the text is still in L2.  The
 // bytes after the last full row are scanned by the last lanes of the grid
 // with plain loads while the other warps stream rows.
+//
+// Overlapping q-grams (MPM_OV).  The sampled q-grams start at the bytes
+// h = k-1 (mod k), one every k bytes, so a stage of C bytes (a multiple of k)
+// holds C/k of them at fixed offsets: those whose last byte lies in the
+// stage, their first bytes possibly in the TW words before it, which a lane
+// keeps in registers from its previous stage.  The hot loop only folds the
+// lookups into D and ANDs every D into one word; only when a report bit of
+// that word is zero for some lane (rare: this filter is chosen for its low
+// candidate rate) does the warp run the stage again from the saved D to find
+// which samples fired.
 
 typedef unsigned char u8;
 typedef unsigned short u16;
@@ -54,12 +68,19 @@ struct Cond<false, X, Y> {
 };
 
 constexpr int Q = MPM_Q, K = MPM_K, MP = MPM_MP, ELL = MPM_ELL, SHIFT = MPM_SHIFT;
-constexpr int P = Q * K;
+constexpr bool OV = MPM_OV != 0;
+constexpr int P = OV ? K : Q * K;  // text bytes per sampled q-gram
+constexpr int VQ = OV ? 1 : Q;     // text starts a window stands for
 constexpr int C = MPM_C;
 constexpr int NS = C / P;
 constexpr int S = MPM_S;
 constexpr int WARPS = MPM_WARPS;
-constexpr int WB = (MP - 1) * P;  // bytes of the samples that precede a row
+// overlapping q-grams: words before a stage that hold the first bytes of its
+// samples, and the offset of the last byte of its first sample
+constexpr int TW = OV ? (Q + 2) / 4 : 0;
+constexpr int E0 = OV ? (K + Q - 2) % K : 0;
+// bytes of the samples that precede a row
+constexpr int WB = OV ? (MP - 1) * K + Q - 1 : (MP - 1) * P;
 constexpr int WSTAGES = (WB + C - 1) / C;
 constexpr int RSH = (MP - 1) * K;
 constexpr u32 KMASK = K >= 32 ? 0xFFFFFFFFu : ((1u << K) - 1u);
@@ -77,14 +98,18 @@ typedef u32 ET;
 typedef u64 ET;
 #endif
 typedef Cond<(MPM_EB == 8), u64, u32>::T DT;
-typedef Cond<(NS * K > 32), u64, u32>::T FT;
+typedef Cond<(OV || NS * K > 32), u64, u32>::T FT;
+// overlapping q-grams: samples per 64-bit word of report bits, and words
+constexpr int SPW = 64 / K;
+constexpr int FW = (NS + SPW - 1) / SPW;
 
 enum { kCandCountJ = 0, kOccCountJ = 1, kErrorFlagJ = 2 };
 constexpr u32 ECAP = MPM_EMIT_CAP;
 static_assert(ECAP >= 64, "emit buffer");
 
 static_assert(C % 16 == 0 && C % P == 0, "stage bytes");
-static_assert(NS * K <= 64, "fired mask");
+static_assert(OV || NS * K <= 64, "fired mask");
+static_assert(!OV || 4 * TW >= Q - 1, "tail words");
 
 // Reduced symbols of the four bytes of a word, first byte most significant.
 __device__ __forceinline__ u32 pack_word(u32 x) {
@@ -156,8 +181,42 @@ __device__ __forceinline__ void run_stage(const u32* w, DT& D, FT& fm, const ET*
     }
 }
 
+// Overlapping q-grams: the NS samples of a stage, the q-gram of sample u
+// starting at byte TW*4 + E0 - (q-1) + u*k of x (the TW words before the
+// stage, then its C/4 words; rx: their reduced symbols for the low-bit map).
+// Every D is ANDed into acc, so a zero report bit of acc means that some
+// sample of the stage fired.
+__device__ __forceinline__ void run_stage_ov(const u32* x, const u32* rx, DT& D, DT& acc,
+                                             const ET* tab, const u8* smu) {
+#pragma unroll
+    for (int u = 0; u < NS; u++) {
+        const u32 c = code_at(x, rx, smu, TW * 4 + E0 - (Q - 1) + u * K);
+        D = (D << K) | (DT)tab[c];
+        acc &= D;
+    }
+}
+
+// The same stage again from D0, with the report bits of sample u in word
+// u / SPW of fm, bits (u % SPW) k ..; hs0 = h - (m'-1)k of sample 0 (h its
+// start byte): a window h - (m'-1)k - j before the text start is dropped.
+__device__ __forceinline__ void fired_stage_ov(const u32* x, const u32* rx, DT D, FT* fm,
+                                               i64 hs0, const ET* tab, const u8* smu) {
+#pragma unroll
+    for (int w = 0; w < FW; w++) fm[w] = 0;
+#pragma unroll
+    for (int u = 0; u < NS; u++) {
+        const u32 c = code_at(x, rx, smu, TW * 4 + E0 - (Q - 1) + u * K);
+        D = (D << K) | (DT)tab[c];
+        u32 f = (u32)(~D >> RSH) & KMASK;
+        const i64 hs = hs0 + (i64)u * K;
+        if (hs < K - 1) f &= hs < 0 ? 0u : ((1u << (u32)(hs + 1)) - 1u);
+        fm[u / SPW] |= (FT)f << ((u % SPW) * K);
+    }
+}
+
 // The windows of one record (sampled q-gram h, report bits `fired`) at
-// shift s: window h0 = h - (m'-1)k - j stands for the text start h0*q - s.
+// shift s: window h0 = h - (m'-1)k - j stands for the text start h0*q - s
+// (overlapping q-grams: h is a byte, and the window starts at h0).
 __device__ __forceinline__ WindowCtx window_ctx(const JitScanArgs& A) {
     WindowCtx c;
     c.T = A.T;
@@ -182,7 +241,7 @@ __device__ __forceinline__ void verify_record(const JitScanArgs& A, u32 h, u32 f
     while (fired) {
         const int j = __ffs((int)fired) - 1;
         fired &= fired - 1;
-        const i64 i = ((i64)h - RSH - j) * Q - s;
+        const i64 i = ((i64)h - RSH - j) * VQ - s;
         if (i < 0 || i + (i64)A.m > (i64)A.n) continue;
         check_window(c, (u32)i);
     }
@@ -200,10 +259,10 @@ __device__ __forceinline__ void flush(Emitter& E, const JitScanArgs& A) {
     const int lane = threadIdx.x & 31;
 #if MPM_VERIFY
     if (lane == 0) atomicAdd(&A.counters[kCandCountJ], E.n);
-    const u32 items = E.n * (u32)Q;
+    const u32 items = E.n * (u32)VQ;
     for (u32 t = lane; t < items; t += 32) {
-        const u64 rec = E.buf[t / Q];
-        verify_record(A, (u32)rec, (u32)(rec >> 32), (int)(t % Q));
+        const u64 rec = E.buf[t / VQ];
+        verify_record(A, (u32)rec, (u32)(rec >> 32), (int)(t % VQ));
     }
 #else
     u32 base = 0;
@@ -217,8 +276,8 @@ __device__ __forceinline__ void flush(Emitter& E, const JitScanArgs& A) {
 }
 
 // Buffers the records of one stage: for every lane, every sample u with
-// report bits, ((bits) << 32) | (h0 + u*k + k-1).
-__device__ __forceinline__ void emit_stage(FT fm, u32 h0, Emitter& E, const JitScanArgs& A) {
+// report bits, ((bits) << 32) | (h1 + u*k), h1 the stage's first sample.
+__device__ __forceinline__ void emit_stage(FT fm, u32 h1, Emitter& E, const JitScanArgs& A) {
     while (true) {
         const bool has = fm != 0;
         const u32 bal = __ballot_sync(0xFFFFFFFFu, has);
@@ -229,7 +288,7 @@ __device__ __forceinline__ void emit_stage(FT fm, u32 h0, Emitter& E, const JitS
             const int u = bit / K;
             const u32 fired = (u32)(fm >> (u * K)) & KMASK;
             fm &= ~((FT)KMASK << (u * K));
-            const u32 h = h0 + (u32)(u * K + (K - 1));
+            const u32 h = h1 + (u32)(u * K);
             E.buf[E.n + __popc(bal & lanemask_lt())] = ((u64)fired << 32) | h;
         }
         E.n += __popc(bal);
@@ -316,6 +375,43 @@ extern "C" __global__ void __launch_bounds__(MPM_WARPS * 32, 1)
             const bool valid = row < A.R;
             const u32 row_start = row * A.Lst;
             DT D = ~(DT)0;
+#if MPM_OV
+            // x: the TW words before the stage, then the stage's C/4 words;
+            // rx: their reduced symbols (low-bit map).  Row 0 starts from
+            // zero words: the samples that would start before the text only
+            // reach windows before it, which fired_stage_ov drops.
+            u32 x[TW + C / 4], rx[TW + C / 4];
+#pragma unroll
+            for (int i = 0; i < TW; i++) x[i] = rx[i] = 0u;
+            if (WB > 0 && valid && row_start > 0) {
+                // the samples before the row: whole stages ending at row_start
+                // (the first stage's own first samples may read zero words:
+                // they come more than m'-1 samples before the row)
+                const u8* wp = A.T + row_start - (u32)(WSTAGES * C);
+#pragma unroll 1
+                for (int ws = 0; ws < WSTAGES; ws++) {
+#pragma unroll
+                    for (int i = 0; i < C / 16; i++) {
+                        const uint4 v = ldg_v4(wp + ws * C + 16 * i);
+                        x[TW + 4 * i] = v.x;
+                        x[TW + 4 * i + 1] = v.y;
+                        x[TW + 4 * i + 2] = v.z;
+                        x[TW + 4 * i + 3] = v.w;
+                    }
+                    if (MPM_MODE == 0) {
+#pragma unroll
+                        for (int i = TW; i < TW + C / 4; i++) rx[i] = pack_word(x[i]);
+                    }
+                    DT acc = ~(DT)0;
+                    run_stage_ov(x, rx, D, acc, tab, s_mu);
+#pragma unroll
+                    for (int i = 0; i < TW; i++) {
+                        x[i] = x[C / 4 + i];
+                        rx[i] = rx[C / 4 + i];
+                    }
+                }
+            }
+#else
             FT fm = 0;
             if (WB > 0 && valid && row_start > 0) {
                 // the samples before the row: whole stages ending at row_start
@@ -335,6 +431,7 @@ extern "C" __global__ void __launch_bounds__(MPM_WARPS * 32, 1)
                 }
             }
             const u32 h_row = row_start / (u32)Q;
+#endif
             for (u32 st = 0; st < nst; st++, it++) {
                 const u32 slot = it % S;
                 const bool ok = mbar_wait_bounded(smem_addr(&bars[slot]), (it / S) & 1u);
@@ -348,8 +445,25 @@ extern "C" __global__ void __launch_bounds__(MPM_WARPS * 32, 1)
                     __syncwarp();
                     return;
                 }
-                u32 w[C / 4];
                 const u32 base = smem_addr(stage + slot * SLOT + lane * C);
+#if MPM_OV
+#pragma unroll
+                for (int i = 0; i < C / 16; i++) {
+                    const uint4 v = lds128(base + 16 * i);
+                    x[TW + 4 * i] = v.x;
+                    x[TW + 4 * i + 1] = v.y;
+                    x[TW + 4 * i + 2] = v.z;
+                    x[TW + 4 * i + 3] = v.w;
+                }
+                if (MPM_MODE == 0) {
+#pragma unroll
+                    for (int i = TW; i < TW + C / 4; i++) rx[i] = pack_word(x[i]);
+                }
+                const DT D0 = D;
+                DT acc = ~(DT)0;
+                run_stage_ov(x, rx, D, acc, tab, s_mu);
+#else
+                u32 w[C / 4];
 #pragma unroll
                 for (int i = 0; i < C / 16; i++) {
                     const uint4 v = lds128(base + 16 * i);
@@ -360,6 +474,7 @@ extern "C" __global__ void __launch_bounds__(MPM_WARPS * 32, 1)
                 }
                 fm = 0;
                 run_stage<true>(w, D, fm, tab, s_mu);
+#endif
                 // the slot's words are consumed: refill it
                 __syncwarp();
                 if (lane == 0 && it + S < total) {
@@ -369,8 +484,30 @@ extern "C" __global__ void __launch_bounds__(MPM_WARPS * 32, 1)
                     tma_load_2d(smem_addr(stage + slot * SLOT), &tmap, (int)((j % nst) * C),
                                 (int)((gw + (j / nst) * RW) * 32), bar);
                 }
+#if MPM_OV
+                const bool any = valid && (((u32)(~acc >> RSH) & KMASK) != 0u);
+                if (__any_sync(0xFFFFFFFFu, any)) {
+                    // some lane fired: which samples, from the saved D
+                    const i64 h1 = (i64)row_start + (i64)st * C + (E0 - (Q - 1));
+                    FT fmw[FW];
+                    fired_stage_ov(x, rx, D0, fmw, h1 - RSH, tab, s_mu);
+#pragma unroll
+                    for (int w = 0; w < FW; w++) {
+                        const FT f = valid ? fmw[w] : (FT)0;
+                        if (__any_sync(0xFFFFFFFFu, f != 0))
+                            emit_stage(f, (u32)(h1 + (i64)w * SPW * K), E, A);
+                    }
+                }
+#pragma unroll
+                for (int i = 0; i < TW; i++) {
+                    x[i] = x[C / 4 + i];
+                    rx[i] = rx[C / 4 + i];
+                }
+#else
                 if (!valid) fm = 0;
-                if (__any_sync(0xFFFFFFFFu, fm != 0)) emit_stage(fm, h_row + st * (u32)(C / Q), E, A);
+                if (__any_sync(0xFFFFFFFFu, fm != 0))
+                    emit_stage(fm, h_row + st * (u32)(C / Q) + (u32)(K - 1), E, A);
+#endif
             }
         }
         flush(E, A);
@@ -383,6 +520,33 @@ extern "C" __global__ void __launch_bounds__(MPM_WARPS * 32, 1)
         const u32 a = A.pa + s * A.Ls;
         const u32 b = min(A.n, a + A.Ls);
         DT D = ~(DT)0;
+#if MPM_OV
+        // the samples whose last byte lies in [a, b): starts from a - (q-1),
+        // at h = k-1 (mod k); the m'-1 samples before them warm D up, and
+        // samples starting before the text do not exist (D stays all ones)
+        i64 h = (i64)a - (Q - 1);
+        h += (((i64)(K - 1) - h) % K + K) % K;
+        for (int t = MP - 1; t >= 1; t--) {
+            const i64 hw = h - (i64)t * K;
+            if (hw < 0) continue;
+            D = (D << K) | (DT)tab[code_bytes(A.T, (u32)hw, s_mu)];
+        }
+        for (; h + Q <= (i64)b; h += K) {
+            if (h < 0) continue;
+            D = (D << K) | (DT)tab[code_bytes(A.T, (u32)h, s_mu)];
+            const u32 fired = (u32)(~D >> RSH) & KMASK;
+            if (fired) {
+                // rare: handled by the lane alone
+                const u32 idx = atomicAdd(&A.counters[kCandCountJ], 1u);
+#if MPM_VERIFY
+                (void)idx;
+                verify_record(A, (u32)h, fired, 0);
+#else
+                if (idx < A.cap) A.cand[idx] = ((u64)fired << 32) | (u32)h;
+#endif
+            }
+        }
+#else
         // the m'-1 samples that end at a, a-P, ...; those starting before
         // the text are virtual and leave D at all ones
         for (int j = MP - 2; j >= 0; j--) {
@@ -405,6 +569,7 @@ extern "C" __global__ void __launch_bounds__(MPM_WARPS * 32, 1)
 #endif
             }
         }
+#endif
     }
 }
 

@@ -31,6 +31,7 @@ mpm::FilterDev filter_of(const mpm::Plan& plan) {
     f.shift = plan.p.map_shift;
     f.mprime = plan.info.mprime;
     f.positions = plan.info.positions;
+    f.overlap = plan.p.overlap;
     return f;
 }
 
@@ -117,6 +118,7 @@ extern "C" int mpm_autotune(const uint8_t* P, size_t r, size_t m, int sigma, con
     std::vector<Candidate> cands;
     std::vector<Candidate> above_rate;  // timed only when no set passes max_rate
     if (o.grid < 0 || o.grid > 1) return set_error(MPM_EINVAL);
+    if (o.overlap < 0 || o.overlap > 2) return set_error(MPM_EINVAL);
     if (o.grid == 1) {
         // exactly the cost model's grid (max_q, max_k, max_sets and max_rate unused)
         std::vector<mpm::Plan> plans;
@@ -130,25 +132,37 @@ extern "C" int mpm_autotune(const uint8_t* P, size_t r, size_t m, int sigma, con
             cands.push_back(c);
         }
     }
+    // the overlapping-q-gram family (Section 2) is ranked apart: its sets
+    // send far fewer windows to verification per byte but read k bytes per
+    // sampled q-gram instead of k q, so one ranking would starve the other
+    std::vector<Candidate> cands_ov, above_ov;
+    const bool want_nov = o.grid == 1 || o.overlap != 2;
+    const bool want_ov = o.grid == 0 && o.overlap != 0;
     // one planning pass per (mapping, sigma', q) scores every k at once
     auto add_all_k = [&](int kind, int sr, int q) {
-        mpm_params p{};
-        p.q = q;
-        p.sigma_r = sr;
-        p.map_kind = kind;
-        p.map_shift = -1;
-        mpm::Plan best_k;
-        std::vector<mpm::Plan> all;
-        if (mpm::make_plan(P, r, m, sigma_eff, &p, &best_k, &all) != MPM_OK) return;
-        for (const auto& pl : all) {
-            if (pl.p.k > max_k) continue;
-            if (pl.info.table_bytes > max_table) continue;
-            if (pl.info.positions > max_positions) continue;
-            Candidate c;
-            c.plan = pl;
-            c.p = pl.p;
-            c.key = pl.info.est_candidate_rate / (double)(pl.p.q * pl.p.k);
-            (pl.info.est_candidate_rate > max_rate ? above_rate : cands).push_back(c);
+        for (int ov = 0; ov <= 1; ov++) {
+            if (!(ov ? want_ov : want_nov)) continue;
+            mpm_params p{};
+            p.q = q;
+            p.sigma_r = sr;
+            p.map_kind = kind;
+            p.map_shift = -1;
+            p.overlap = ov;
+            mpm::Plan best_k;
+            std::vector<mpm::Plan> all;
+            if (mpm::make_plan(P, r, m, sigma_eff, &p, &best_k, &all) != MPM_OK) continue;
+            for (const auto& pl : all) {
+                if (pl.p.k > max_k) continue;
+                if (pl.info.table_bytes > max_table) continue;
+                if (pl.info.positions > max_positions) continue;
+                Candidate c;
+                c.plan = pl;
+                c.p = pl.p;
+                // candidate windows per text byte
+                c.key = pl.info.est_candidate_rate / (double)(ov ? pl.p.k : pl.p.q * pl.p.k);
+                const bool above = pl.info.est_candidate_rate > max_rate;
+                (ov ? (above ? above_ov : cands_ov) : (above ? above_rate : cands)).push_back(c);
+            }
         }
     };
     for (int sr = 2; o.grid == 0 && sr <= top; sr <<= 1) {
@@ -169,21 +183,34 @@ extern "C" int mpm_autotune(const uint8_t* P, size_t r, size_t m, int sigma, con
     // q-gram hashing: whole q-grams into 2^10 .. 2^16 bins
     for (int bits = 10; o.grid == 0 && bits <= 16; bits++)
         for (int q = 1; q <= std::min(max_q, 8); q++) add_all_k(MPM_MAP_QHASH, 1 << bits, q);
-    if (o.grid == 0 && cands.empty()) {
-        // every set sends more windows to verification than max_rate (large
-        // pattern sets): time the lowest-rate ones
-        std::stable_sort(above_rate.begin(), above_rate.end(),
-                         [](const Candidate& a, const Candidate& b) {
-                             return a.plan.info.est_candidate_rate <
-                                    b.plan.info.est_candidate_rate;
-                         });
-        cands.swap(above_rate);
-    } else if (o.grid == 0) {
-        std::stable_sort(cands.begin(), cands.end(),
-                         [](const Candidate& a, const Candidate& b) { return a.key < b.key; });
-    }
-    if (o.grid == 0 && cands.size() > max_sets) cands.resize(max_sets);
+    // each family: its sets under max_rate by windows per byte, or, when
+    // every set sends more windows to verification than max_rate (large
+    // pattern sets), its lowest-rate ones
+    auto rank = [](std::vector<Candidate>& in, std::vector<Candidate>& above) {
+        if (in.empty()) {
+            std::stable_sort(above.begin(), above.end(),
+                             [](const Candidate& a, const Candidate& b) {
+                                 return a.plan.info.est_candidate_rate <
+                                        b.plan.info.est_candidate_rate;
+                             });
+            in.swap(above);
+        } else {
+            std::stable_sort(in.begin(), in.end(),
+                             [](const Candidate& a, const Candidate& b) { return a.key < b.key; });
+        }
+    };
     if (o.grid == 0) {
+        rank(cands, above_rate);
+        rank(cands_ov, above_ov);
+        // half of max_sets for each family present; one family's unused
+        // share goes to the other
+        size_t n_ov = std::min(cands_ov.size(), cands.empty() ? max_sets : max_sets / 2);
+        size_t n_nov = std::min(cands.size(), max_sets - n_ov);
+        n_ov = std::min(cands_ov.size(), max_sets - n_nov);
+        cands.resize(n_nov);
+        cands.insert(cands.end(), cands_ov.begin(), cands_ov.begin() + n_ov);
+    }
+    if (o.grid == 0 && want_nov) {
         // the planner's own choice (mpm_build with automatic parameters) is
         // always timed too, whatever its q or table size, unless the caller
         // bounded the table
@@ -194,7 +221,8 @@ extern "C" int mpm_autotune(const uint8_t* P, size_t r, size_t m, int sigma, con
             bool dup = false;
             for (const auto& c : cands)
                 dup = dup || (c.p.q == pa.p.q && c.p.sigma_r == pa.p.sigma_r && c.p.k == pa.p.k &&
-                              c.p.map_kind == pa.p.map_kind && c.p.map_shift == pa.p.map_shift);
+                              c.p.map_kind == pa.p.map_kind && c.p.map_shift == pa.p.map_shift &&
+                              c.p.overlap == pa.p.overlap);
             if (!dup) {
                 Candidate c;
                 c.plan = pa;

@@ -1,6 +1,8 @@
 """GPU parity of the overlapping-q-gram filter (Section 2's first filter,
 `overlap = 1`): the scan's candidate windows equal the oracle's AOSO scan
-over the text's q-gram at every byte, and full searches equal Aho-Corasick."""
+over the text's q-gram at every byte, and full searches equal Aho-Corasick,
+in the generic kernel and in both variants of the specialised one (the one
+that verifies its candidates itself and the split one)."""
 import os
 
 import numpy as np
@@ -65,8 +67,14 @@ SCAN_CASES = [
 ]
 
 
+# mpm_scan runs the generic kernel or the specialised one that writes
+# candidate records
+SCAN_KERNELS = [1, 3]
+
+
+@pytest.mark.parametrize("kernel", SCAN_KERNELS, ids=["generic", "specialised"])
 @pytest.mark.parametrize("case", SCAN_CASES, ids=[str(c) for c in SCAN_CASES])
-def test_overlap_candidates_equal_oracle(mpm, case):
+def test_overlap_candidates_equal_oracle(mpm, case, kernel):
     sigma, m, q, sr, k, kind = case
     rng = np.random.default_rng(sum(case))
     base = 65 if sigma <= 20 else 33
@@ -76,21 +84,24 @@ def test_overlap_candidates_equal_oracle(mpm, case):
     for i in range(20):
         o = int(rng.integers(0, n - m + 1))
         P[i] = T[o:o + m]
-    kw = dict(q=q, sigma_r=sr, k=k, map_kind=kind, overlap=1)
+    kw = dict(q=q, sigma_r=sr, k=k, map_kind=kind, overlap=1, kernel=kernel)
     if kind == 3:
         kw["map_shift"] = 0 if sigma > 4 else 1
     M = mpm.Matcher(P, sigma=sigma, **kw)
     p, info = M.params, M.info
-    assert p["overlap"] == 1 and p["kernel"] == mpm.KERNEL_GENERIC
+    assert p["overlap"] == 1 and p["kernel"] == kernel
     got = windows_of(M.scan(dev(T)), k, info["mprime"])
+    if kernel != 1:
+        assert M.stats["specialised"] == 1
     fp = F.make_params(P, q, sr, k, KIND[kind], shift=p["map_shift"], overlap=True)
     cls = F.pattern_classes(P, fp)
     want = F.aoso_scan(F.text_codes(T, fp), F.mask_table(cls, fp), fp, len(cls))
     assert np.array_equal(got, np.array(want, np.int64))
 
 
+@pytest.mark.parametrize("kernel", [1, 2, 3], ids=["generic", "verifying", "split"])
 @pytest.mark.parametrize("case", SCAN_CASES[::2], ids=[str(c) for c in SCAN_CASES[::2]])
-def test_overlap_search_equals_aho_corasick(mpm, native, case):
+def test_overlap_search_equals_aho_corasick(mpm, native, case, kernel):
     sigma, m, q, sr, k, kind = case
     rng = np.random.default_rng(7 + sum(case))
     base = 65 if sigma <= 20 else 33
@@ -100,7 +111,7 @@ def test_overlap_search_equals_aho_corasick(mpm, native, case):
     for i in range(150):
         o = int(rng.integers(0, n - m + 1))
         P[i] = T[o:o + m]
-    kw = dict(q=q, sigma_r=sr, k=k, map_kind=kind, overlap=1)
+    kw = dict(q=q, sigma_r=sr, k=k, map_kind=kind, overlap=1, kernel=kernel)
     M = mpm.Matcher(P, sigma=sigma, **kw)
     pos, pid = M.search(dev(T))
     want = native.aho_corasick(T, P, threads=8)
@@ -128,15 +139,46 @@ def test_overlap_edges(mpm, native):
         for kw in (dict(q=9, sigma_r=4, k=1, map_kind=2),     # q = m: L' = 1
                    dict(q=2, sigma_r=4, k=8, map_kind=2),     # k = L'
                    dict(q=3, sigma_r=1 << 12, k=3, map_kind=4)):
-            M = mpm.Matcher(P, sigma=4, overlap=1, **kw)
-            pos, pid = M.search(T)   # host text and outputs
-            want = native.aho_corasick(T, P)
-            assert np.array_equal(pos, want[0]) and np.array_equal(pid, want[1]), (n, kw)
+            for kernel in (1, 2, 3):
+                M = mpm.Matcher(P, sigma=4, overlap=1, kernel=kernel, **kw)
+                pos, pid = M.search(T)   # host text and outputs
+                want = native.aho_corasick(T, P)
+                assert np.array_equal(pos, want[0]) and np.array_equal(pid, want[1]), \
+                    (n, kw, kernel)
+
+
+def test_overlap_rows_and_tail_edges(mpm, native):
+    """Texts of a few specialised-kernel rows: occurrences planted at row and
+    stage starts, across row boundaries and at both text ends, for filters
+    whose first bytes come from 0, 1 and 2 words before a stage."""
+    rng = np.random.default_rng(5)
+    for q, k, m in ((1, 4, 12), (5, 2, 16), (8, 4, 16), (8, 3, 20)):
+        P = (rng.integers(0, 4, (30, m)) + 65).astype(np.uint8)
+        for n in (4 * 1024 * 1024 + 77, 2 * 1024 * 1024):
+            T = (rng.integers(0, 4, n) + 65).astype(np.uint8)
+            T[:m] = P[0]
+            T[n - m:] = P[1]
+            for at in list(range(80, n - m, n // 37))[:36]:
+                # every place of a stage row: ends and middle
+                for d in (-m // 2, 0, 3):
+                    o = at + d
+                    if 0 <= o <= n - m:
+                        T[o:o + m] = P[int(rng.integers(0, 30))]
+            want = native.aho_corasick(T, P, threads=8)
+            for kernel in (2, 3):
+                M = mpm.Matcher(P, sigma=4, q=q, sigma_r=4, k=k, map_kind=3, map_shift=1,
+                                overlap=1, kernel=kernel)
+                pos, pid = M.search(dev(T))
+                assert np.array_equal(as_u32(pos), want[0]), (q, k, m, n, kernel)
+                assert np.array_equal(as_u32(pid), want[1]), (q, k, m, n, kernel)
+                # unaligned text: every byte through the plain-load path
+                pos, pid = M.search(dev(np.concatenate([np.zeros(1, np.uint8), T]))[1:])
+                assert np.array_equal(as_u32(pos), want[0]), (q, k, m, n, kernel, "unaligned")
 
 
 def test_overlap_refused_where_unsupported(mpm):
     P = np.frombuffer(b"ACGTACGTACGTACGT", np.uint8).reshape(1, 16)
-    for kw in (dict(kernel=mpm.KERNEL_SPECIALISED), dict(kernel=mpm.KERNEL_SPLIT), dict(smag=1)):
+    for kw in (dict(smag=1),):
         with pytest.raises(mpm.MpmError) as e:
             mpm.Matcher(P, sigma=4, q=3, sigma_r=4, k=1, map_kind=2, overlap=1, **kw)
         assert e.value.code == mpm.MPM_ENOTSUP
@@ -146,9 +188,13 @@ def test_overlap_refused_where_unsupported(mpm):
 
 
 def test_overlap_full_size_dna(mpm, native):
-    """1 GiB uniform DNA, r = 100, m = 16 (config 1's patterns at scale)."""
+    """1 GiB uniform DNA, r = 100, m = 16 (config 1's patterns at scale):
+    the generic kernel and the specialised one."""
     case = W.config1_scaled()
-    M = mpm.Matcher(case.P, sigma=4, q=8, sigma_r=4, k=1, map_kind=3, map_shift=1, overlap=1)
-    pos, pid = M.search(dev(case.T))
+    T = dev(case.T)
     want = native.aho_corasick(case.T, case.P, threads=max(1, min(32, os.cpu_count() or 1)))
-    assert np.array_equal(as_u32(pos), want[0]) and np.array_equal(as_u32(pid), want[1])
+    for kw in (dict(q=8, k=1, kernel=1), dict(q=8, k=4, kernel=2), dict(q=8, k=2, kernel=3)):
+        M = mpm.Matcher(case.P, sigma=4, sigma_r=4, map_kind=3, map_shift=1, overlap=1, **kw)
+        pos, pid = M.search(T)
+        assert np.array_equal(as_u32(pos), want[0]) and np.array_equal(as_u32(pid), want[1]), kw
+        M.close()

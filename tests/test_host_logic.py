@@ -192,7 +192,8 @@ def test_host_tables_two_word_state_equal_oracle(mpm, seed):
 
 def test_overlap_refusals(mpm):
     P = np.frombuffer(b"ACGTACGTACGTACGT", np.uint8).reshape(1, 16)
-    rc, _ = mpm.jit_compile(P, 4, q=3, sigma_r=4, k=1, map_kind=2, overlap=1)
+    # two words of state stay in the generic kernels
+    rc, _ = mpm.jit_compile(P, 4, q=1, sigma_r=4, k=1, map_kind=2, wide=1)
     assert rc == mpm.MPM_ENOTSUP
     # the planner keeps q-gram hashing to the generic kernel's 5 bytes
     p, _ = mpm.plan(P, 4, map_kind=4, sigma_r=1 << 12, overlap=1)
@@ -234,6 +235,15 @@ JIT_GRID = [
     ("dna", 16, dict(q=8, sigma_r=4, k=1, map_kind=3, kernel=3)),
     ("dna", 64, dict(q=11, sigma_r=4, k=2, map_kind=3, kernel=2)),
     ("dna", 32, dict(q=13, sigma_r=4, k=1, map_kind=3, kernel=3)),
+    # overlapping q-grams (Section 2): every mapping, tail words of 0, 1 and 2,
+    # stages of 80 and 144 bytes, both variants
+    ("dna", 16, dict(q=8, sigma_r=4, k=4, map_kind=3, map_shift=1, overlap=1, kernel=2)),
+    ("dna", 16, dict(q=8, sigma_r=4, k=2, map_kind=3, map_shift=1, overlap=1, kernel=3)),
+    ("dna", 16, dict(q=6, sigma_r=4, k=3, map_kind=3, map_shift=1, overlap=1, kernel=2)),
+    ("dna", 32, dict(q=1, sigma_r=4, k=8, map_kind=1, overlap=1, kernel=3)),
+    ("protein", 32, dict(q=5, sigma_r=1 << 16, k=1, map_kind=4, overlap=1, kernel=2)),
+    ("protein", 32, dict(q=3, sigma_r=16, k=6, map_kind=2, overlap=1, kernel=3)),
+    ("english", 64, dict(q=4, sigma_r=8, k=16, map_kind=1, overlap=1, kernel=2)),
 ]
 
 
