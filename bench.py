@@ -1,11 +1,18 @@
 """Benchmark: text GB/s of exact multiple pattern matching (MAG) on GB300.
 
-One step = one mpm_search over the whole text: the fused encode + AOSO
-Shift-Or scan, verification, the occurrence count read-back and the sort of
-the occurrence list.  The default workload is the protein-like one: a
-256 MiB text over 20 symbols (Zipf s = 0.8), r = 1000 patterns of length
-m = 32, half planted.  The text is larger than the 129 MB L2, so no flush is
-needed between steps.
+One step = one search over the whole text: the fused encode + AOSO Shift-Or
+scan, verification, the occurrence count and the sort of the occurrence
+list.  The default workload is uniform DNA at 1 GiB with r = 100 patterns of
+length m = 16, half planted (the 1 MiB DNA configuration's distribution and
+pattern shape at a text larger than the 129 MB L2, so no flush is needed
+between steps); the filter's parameters come from the autotuner, which
+times MAG's non-overlapping q-grams and Section 2's overlapping ones.
+
+The default run (one GPU) adds the other configurations to the same line
+under "other_configs", each in a bounded form: the 1 MiB DNA search as
+stated (L2 flushed before every search), the protein-like workload, the
+large pattern sets, the batch of 4096 texts (batched + learned against the
+plain per-request form) and the cost model's regret timed live.
 
 Prints one JSON line.  --impl reference times the oracle (textbook
 Aho-Corasick in C, threaded) on the host cores instead.
@@ -258,14 +265,15 @@ def run_reference(args, rank):
     print(json.dumps(line))
 
 
-def run_batch(args, rank):
+def run_batch(args, rank, steps=None, fast=False):
     """Config 4: 4096 texts (1 KiB - 4 MiB, printable Zipf text) against 64
-    pattern sets.  Plain form: one mpm_search per text with the automatic
-    parameters.  Batched forms: one persistent launch replayed from a CUDA
-    graph, with each set's parameters proposed by the learned cost model (the
-    headline) or picked by the exhaustive autotuner timing the batched kernel
-    on a sample of the set's texts.  All forms produce the same occurrences,
-    checked."""
+    pattern sets.  Plain form: one mpm_search per text, each set's
+    parameters tuned by the autotuner on a sample of its texts.  Batched
+    forms: one persistent launch replayed from a CUDA graph, with each set's
+    parameters proposed by the learned cost model (the headline) or picked by
+    the exhaustive autotuner timing the batched kernel on a sample of the
+    set's texts.  All forms produce the same occurrences, checked.  Returns
+    the JSON line (fast: smaller tuning budgets)."""
     import torch
     import paper_1405_5483_gb300 as mpm
     from paper_1405_5483_gb300 import _native as mpm_native
@@ -287,8 +295,21 @@ def run_batch(args, rank):
     dflat = torch.from_numpy(flat).to(dev)
     texts = [dflat[int(offs[i]): int(offs[i]) + t.size] for i, t in enumerate(b.texts)]
     total = b.total_bytes
-    # plain per-request form
-    plain = [mpm.Matcher(P, sigma=b.sigma) for P in b.sets]
+    steps = max(1, steps or args.steps)
+    # plain per-request form: each set's parameters tuned (mpm_search timed)
+    # on up to 16 MiB of its texts
+    t0 = time.perf_counter()
+    plain = []
+    for sidx, P in enumerate(b.sets):
+        mine = [texts[t] for t in np.flatnonzero(b.set_of_text == sidx)]
+        sample = torch.cat(mine)[: 16 << 20] if mine else texts[0]
+        try:
+            best, _ = mpm.autotune(P, b.sigma, sample, kernels=3, overlap=1,
+                                   max_sets=8 if fast else 24, reps=2)
+        except mpm.MpmError:
+            best = {}
+        plain.append(mpm.Matcher(P, sigma=b.sigma, **best))
+    plain_tune_s = time.perf_counter() - t0
     cap = 1 << 20
     out_pos = torch.empty(cap, dtype=torch.int32, device=dev)
     out_pid = torch.empty(cap, dtype=torch.int32, device=dev)
@@ -304,13 +325,8 @@ def run_batch(args, rank):
         return np.concatenate(res) if res else np.zeros((0, 3), np.uint32)
 
     def build(params):
-        sets = []
-        for P, p in zip(b.sets, params):
-            m = mpm.Matcher(P, sigma=b.sigma, **p)
-            if m.info["positions"] > 32:
-                m = mpm.Matcher(P, sigma=b.sigma, map_kind=2, sigma_r=16, q=4, k=1)
-            sets.append(m)
-        return mpm.Batch(sets, texts, b.set_of_text)
+        return mpm.Batch([CM.batch_matcher(P, b.sigma, p) for P, p in zip(b.sets, params)],
+                         texts, b.set_of_text)
 
     def timed(B, label):
         for _ in range(max(3, args.warmup)):
@@ -319,12 +335,12 @@ def run_batch(args, rank):
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         torch.cuda.nvtx.range_push(label)
         e0.record()
-        for _ in range(args.steps):
+        for _ in range(steps):
             B.run()
         e1.record()
         torch.cuda.synchronize()
         torch.cuda.nvtx.range_pop()
-        return e0.elapsed_time(e1) / args.steps
+        return e0.elapsed_time(e1) / steps
 
     def result(B):
         return np.stack([x.cpu().numpy().view(np.uint32) for x in B.run()], axis=1)
@@ -333,24 +349,15 @@ def run_batch(args, rank):
     # batched + learned: the committed cost model proposes each set's parameters
     t0 = time.perf_counter()
     model = CM.Model.load()
-    learned = []
-    for sidx, P in enumerate(b.sets):
-        mine = np.flatnonzero(b.set_of_text == sidx)
-        if mine.size == 0:
-            learned.append({})
-            continue
-        ent = CM.entropy_bits(np.concatenate([b.texts[i][:1 << 16] for i in mine]))
-        n = int(np.clip(np.mean([b.texts[i].size for i in mine]), 1 << 20, 1 << 23))
-        # mask tables that the batched kernel keeps in shared memory
-        learned.append(model.choose(P, b.sigma, ent, n,
-                                    max_table_bytes=mpm_native.BATCH_SMEM_TABLE_BYTES)[0])
+    # mask tables that the batched kernel keeps in shared memory
+    learned = CM.learned_batch_params(b, model, mpm_native.BATCH_SMEM_TABLE_BYTES)
     learn_s = time.perf_counter() - t0
     BL = build(learned)
     exact_learned = bool(np.array_equal(result(BL), want))
     with ClockSampler(dev.index) as clk:
         learned_ms = timed(BL, "batch_timed")
     st = BL.stats
-    launches = int(st["launches"]) * args.steps
+    launches = int(st["launches"]) * steps
     # the scan kernel alone: events on either side of it inside the graph
     scans = []
     for _ in range(10):
@@ -366,7 +373,7 @@ def run_batch(args, rank):
         sample = torch.cat(mine)[: 16 << 20] if mine else texts[0]
         try:
             best, _ = mpm.autotune(P, b.sigma, sample, kernels=8, max_positions=32,
-                                   max_sets=24, reps=2,
+                                   max_sets=12 if fast else 24, reps=2,
                                    max_table_kib=mpm_native.BATCH_SMEM_TABLE_BYTES >> 10)
         except mpm.MpmError:
             best = {}
@@ -377,7 +384,7 @@ def run_batch(args, rank):
     tuned_ms = timed(BT, "batch_tuned")
     BT.close()
 
-    plain_steps = max(1, min(3, args.steps))
+    plain_steps = max(1, min(3, steps))
     plain_pass()
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -395,7 +402,7 @@ def run_batch(args, rank):
     hflat.numpy()[:] = flat
     BL = build(learned)
     BL.run()
-    e2e_steps = max(2, min(args.steps, 5))
+    e2e_steps = max(2, min(steps, 5))
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     for _ in range(e2e_steps):
@@ -409,7 +416,7 @@ def run_batch(args, rank):
     value = total / (learned_ms * 1e-3) / 1e9
     peak, peak_kind = peaks()
     cpu = None
-    if not args.no_cpu_baseline:
+    if not args.no_cpu_baseline and not fast:
         o = OracleBatchSample(b, args.cpu_sample_mib << 20)
         t0 = time.perf_counter()
         oz = o.step()
@@ -422,7 +429,7 @@ def run_batch(args, rank):
     # occurrence records it writes are a few hundred KB)
     achieved = total / (scan_ms * 1e-3) / 1e9 if scan_ms > 0 else None
     line = {
-        "metric": METRIC, "value": value, "unit": "GB/s", "n_gpus": 1, "steps": args.steps,
+        "metric": METRIC, "value": value, "unit": "GB/s", "n_gpus": 1, "steps": steps,
         "warmup": max(3, args.warmup), "ms_per_step": learned_ms, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "u8", "data": "synthetic",
         "config": {"workload": "batch-4096", "texts": len(texts), "sets": len(b.sets),
@@ -433,7 +440,9 @@ def run_batch(args, rank):
         "hbm_frac_of_%s_peak" % peak_kind: value / peak,
         "plain_per_request": {"value": total / (plain_ms * 1e-3) / 1e9, "unit": "GB/s",
                               "ms_per_step": plain_ms,
-                              "form": "one mpm_search per text, automatic parameters"},
+                              "form": "one mpm_search per text, each set's parameters "
+                                      "from the autotuner (mpm_search timed on up to 16 MiB "
+                                      "of its texts)"},
         "batched_tuned": {"value": total / (tuned_ms * 1e-3) / 1e9, "unit": "GB/s",
                           "ms_per_step": tuned_ms,
                           "form": "batched, parameters from the exhaustive autotuner "
@@ -456,65 +465,45 @@ def run_batch(args, rank):
         "clocks": clk.summary(),
         "cpu_baseline": cpu,
         "setup_seconds": {"generate": round(gen_s, 1), "learned_choice": round(learn_s, 1),
-                          "tune": round(tune_s, 1)},
+                          "tune": round(tune_s, 1), "tune_plain": round(plain_tune_s, 1)},
     }
-    if rank == 0:
-        print(json.dumps(line))
+    for mm in plain:
+        mm.close()
+    del dflat, texts
+    torch.cuda.empty_cache()
+    return line
 
 
-def main():
-    ap = argparse.ArgumentParser()
-    ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=500)
-    ap.add_argument("--warmup", type=int, default=3)
-    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="protein-256MiB",
-                    choices=sorted(WORKLOADS) + ["batch-4096"])
-    ap.add_argument("--cpu-sample-mib", type=int, default=256)
-    ap.add_argument("--ref-sample-mib", type=int, default=64)
-    ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--no-tune", action="store_true")
-    ap.add_argument("--tune-sample-mib", type=int, default=256)
-    ap.add_argument("--params", default="", help="JSON filter parameters; skips tuning")
-    ap.add_argument("--tune-sets", type=int, default=48)
-    args = ap.parse_args()
-
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-
-    if args.impl == "reference":
-        run_reference(args, rank)
-        return
-    if args.workload == "batch-4096":
-        run_batch(args, rank)
-        return
-
+def search_line(args, name, dev, world=1, params=None, tune_sets=None, steps=None,
+                e2e=True, cpu=True):
+    """One workload through the single-text API (mpm_build, mpm_search_async /
+    mpm_search): parameters from the autotuner (both q-gram families) unless
+    given, pipelined searches timed back to back (a text that fits in L2:
+    each search after an L2 flush), the synchronous form beside them, the end
+    to end run from pinned host memory and the oracle's CPU baseline.
+    Returns the JSON line's keys; every rank returns its own timings, the
+    maximum over ranks is taken here."""
     import torch
     import torch.distributed as dist
-    if world > 1:
-        dist.init_process_group("nccl")
-    torch.cuda.set_device(local)
-    dev = torch.device("cuda", local)
-
     import paper_1405_5483_gb300 as mpm
 
-    case, sigma, desc = make_case(args.workload)
+    case, sigma, desc = make_case(name)
     T = torch.from_numpy(case.T).to(dev)
     tuning = None
-    params = {}
-    if args.params:
-        params = parse_params(args.params)
-    elif not args.no_tune:
-        # exhaustive autotuner on a sample of the text; not timed, like the build
-        sample = T[: min(case.n, args.tune_sample_mib << 20)]
-        t0 = time.perf_counter()
-        # patterns of different lengths: the filter's parameters are tuned on
-        # their common-length prefixes
-        params, sets = mpm.autotune(case.prefix_matrix(), sigma, sample, kernels=3,
-                                    max_sets=args.tune_sets, overlap=1)
-        tuning = {"sample_bytes": int(sample.numel()), "sets_timed": len(sets),
-                  "seconds": round(time.perf_counter() - t0, 2)}
+    if params is None:
+        params = {}
+        if args.params:
+            params = parse_params(args.params)
+        elif not args.no_tune:
+            # exhaustive autotuner on a sample of the text; not timed, like the build
+            sample = T[: min(case.n, args.tune_sample_mib << 20)]
+            t0 = time.perf_counter()
+            # patterns of different lengths: the filter's parameters are tuned on
+            # their common-length prefixes
+            params, sets = mpm.autotune(case.prefix_matrix(), sigma, sample, kernels=3,
+                                        max_sets=tune_sets or args.tune_sets, overlap=1)
+            tuning = {"sample_bytes": int(sample.numel()), "sets_timed": len(sets),
+                      "seconds": round(time.perf_counter() - t0, 2)}
     m = mpm.Matcher(case.P, sigma=sigma, **params)
     m.set_timing(True)
     cap = max(1 << 16, 8 * case.r)
@@ -523,7 +512,7 @@ def main():
     stream = torch.cuda.current_stream()
     # one synchronous search sizes the handle's buffers and gives the count
     z = m.search_into(T, out_pos, out_pid)
-    steps = max(1, args.steps)
+    steps = max(1, steps or args.steps)
     status = torch.zeros((steps, 4), dtype=torch.int32, device=dev)
 
     def barrier():
@@ -561,12 +550,12 @@ def main():
         m.sync()
         m.reset_stats()
         if flush is not None:
-            with ClockSampler(local) as clk:
+            with ClockSampler(dev.index) as clk:
                 ms = timed_flushed(steps, pipelined_step)
             m.sync()
             return ms, clk
         ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        with ClockSampler(local) as clk:
+        with ClockSampler(dev.index) as clk:
             barrier()
             ev0.record(stream)
             for i in range(steps):
@@ -604,9 +593,9 @@ def main():
     sync_steps = min(steps, 100)
     sync_ms = timed_sync(sync_steps)
     if not pipelined_ok:
-        # a workload the pipelined call cannot finish by itself (more than
-        # 4096 occurrences): the synchronous form is the step
-        with ClockSampler(local) as clk:
+        # a search the pipelined call does not finish by itself: the
+        # synchronous form is the step
+        with ClockSampler(dev.index) as clk:
             elapsed_ms = timed_sync(steps)
         st = m.stats
         scan_avg, verify_avg = st["ms_scan"], st["ms_verify"]
@@ -616,71 +605,216 @@ def main():
         t = torch.tensor([elapsed_ms, sync_ms], device=dev)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         elapsed_ms, sync_ms = float(t[0].item()), float(t[1].item())
-    total_bytes = case.n * steps * world
-    value = total_bytes / (elapsed_ms * 1e-3) / 1e9
+    value = case.n * steps * world / (elapsed_ms * 1e-3) / 1e9
     peak, peak_kind = peaks()
 
-    # end to end through the public API with host buffers: pinned host text,
-    # host outputs, copies inside the timed region
-    hT = torch.from_numpy(case.T).pin_memory()
-    hpos = np.empty(cap, np.uint32)
-    hpid = np.empty(cap, np.uint32)
-    e2e_steps = max(2, min(args.steps, 5))
-    m.search_into(hT, hpos, hpid)
-    torch.cuda.synchronize()
-    barrier()
-    t0 = time.perf_counter()
-    for _ in range(e2e_steps):
-        ze = m.search_into(hT, hpos, hpid)
-    torch.cuda.synchronize()
-    e2e_s = time.perf_counter() - t0
-    e2e_value = case.n * e2e_steps * world / e2e_s / 1e9
+    e2e_line = None
+    if e2e:
+        # end to end through the public API with host buffers: pinned host
+        # text, host outputs, copies inside the timed region
+        hT = torch.from_numpy(case.T).pin_memory()
+        hpos = np.empty(cap, np.uint32)
+        hpid = np.empty(cap, np.uint32)
+        e2e_steps = max(2, min(args.steps, 5))
+        m.search_into(hT, hpos, hpid)
+        torch.cuda.synchronize()
+        barrier()
+        t0 = time.perf_counter()
+        for _ in range(e2e_steps):
+            ze = m.search_into(hT, hpos, hpid)
+        torch.cuda.synchronize()
+        e2e_s = time.perf_counter() - t0
+        e2e_line = {"value": case.n * e2e_steps * world / e2e_s / 1e9, "unit": "GB/s",
+                    "h2d_bytes_per_step": case.n, "d2h_bytes_per_step": 16 + 8 * ze}
+        del hT
 
     # the dominant kernel: the scan.  Algorithmic bytes per launch = the
     # text read once plus, when the scan writes candidate records to HBM (the
     # split and generic kernels), 8 bytes per record.
-    fused = bool(m.params["kernel"] == mpm.KERNEL_SPECIALISED)
+    p = m.params
+    fused = bool(p["kernel"] == mpm.KERNEL_SPECIALISED)
     algo_bytes = case.n + (0 if fused else 8 * candidates)
     achieved = algo_bytes / (scan_avg * 1e-3) / 1e9
-    traffic = recorded_traffic(args.workload, m.params)
+    if st["specialised"]:
+        kname = "mpm_scan_jit (specialised%s)" % (", overlapping q-grams" if p["overlap"] else "")
+    else:
+        kname = ("scan_overlap_kernel (generic, overlapping q-grams)" if p["overlap"]
+                 else "scan_tma_kernel (generic)")
+    line = {
+        "metric": METRIC, "value": value, "unit": "GB/s", "n_gpus": world,
+        "steps": steps, "warmup": max(3, args.warmup),
+        "ms_per_step": elapsed_ms / steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "u8", "data": "synthetic",
+        "config": {"workload": name, "description": desc, "n": case.n,
+                   "r": case.r, "m": case.m, "params": p, "tuning": tuning,
+                   "l2": ("inputs larger than L2 (no flush)" if flush is None else
+                          "text smaller than L2: L2 flushed (a %d-byte write) before "
+                          "every timed search, outside its events" % (2 * l2)),
+                   "parallelism": "replicas" if world > 1 else "single GPU"},
+        "hbm_frac_of_%s_peak" % peak_kind: value / peak,
+        "form": ("pipelined: mpm_search_async back to back, every step's status checked "
+                 "(complete, z as the synchronous search)" if pipelined_ok else
+                 "synchronous mpm_search per step"),
+        "sync_per_call": {"value": case.n * sync_steps * world / (sync_ms * 1e-3) / 1e9,
+                          "unit": "GB/s", "ms_per_step": sync_ms / sync_steps,
+                          "form": "one synchronous mpm_search per step"},
+        "occurrences": z,
+        "candidates_per_step": candidates,
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": recorded_traffic(name, p),
+                     "kernel": kname, "peak_kind": peak_kind, "scan_ms": scan_avg,
+                     "verify_ms": verify_avg},
+        "e2e": e2e_line,
+        "gpu_launches": launches,
+        "clocks": clk.summary(),
+        "cpu_baseline": None,
+    }
+    if cpu and not args.no_cpu_baseline and world == 1:
+        line["cpu_baseline"] = cpu_baseline(case, args.cpu_sample_mib << 20)
+    m.close()
+    del T, out_pos, out_pid, status, flush
+    torch.cuda.empty_cache()
+    return line
 
+
+def run_regret(args, dev, nsets=50):
+    """Config 5 measured live: for each of the first nsets held-out pattern
+    sets of the cost model's data (config-4-shaped, never trained on), every
+    point of the model's grid is timed with the batched kernel (the
+    autotuner's grid mode: the whole GPU busy, the set's text repeated to at
+    least 128 MiB, median device time); the model's choice is the grid point
+    of least predicted time, its regret t(choice) / t(best) - 1 in the same
+    timing; the library's default parameters are timed the same way."""
+    import torch
+    import paper_1405_5483_gb300 as mpm
+    from paper_1405_5483_gb300 import cost_model as CM
+    from paper_1405_5483_gb300 import workloads as W
+    model = CM.Model.load()
+    regrets, gains, points = [], [], 0
+    t0 = time.perf_counter()
+    for idx in list(CM.HELDOUT_SETS)[:nsets]:
+        case = W.config5_set(idx)
+        T = torch.from_numpy(case.T).to(dev)
+        ent = CM.entropy_bits(case.T)
+        _, entries = mpm.autotune(case.P, case.sigma, T, kernels=8, grid=1, max_positions=32,
+                                  reps=3)
+        ok = [e for e in entries if e["status"] == 0 and e["ms"] > 0]
+        if not ok:
+            continue
+        points += len(ok)
+        ms = np.array([e["ms"] for e in ok])
+        pred = model.predict(CM.features(case.sigma, ent, case.m, case.r, case.n,
+                                         [e["params"] for e in ok]))
+        pick = float(ms[int(np.argmin(pred))])
+        regrets.append(pick / float(ms.min()) - 1.0)
+        dp = CM.default_params(case.P, case.sigma)
+        if dp:
+            gains.append(CM.time_batched(case.P, case.sigma, T, dp, reps=3) / pick)
+        del T
+    regrets = np.array(regrets)
+    return {
+        "sets": int(regrets.size), "grid_points_timed": points,
+        "mean_regret": float(regrets.mean()) if regrets.size else None,
+        "median_regret": float(np.median(regrets)) if regrets.size else None,
+        "p90_regret": float(np.quantile(regrets, 0.9)) if regrets.size else None,
+        "geomean_speedup_over_default":
+            float(np.exp(np.mean(np.log(gains)))) if gains else None,
+        "form": "held-out cost-model sets %d.. (config-4 shape), every grid point timed live "
+                "with the batched kernel; regret of the model's least-predicted point "
+                "against the best timed point" % CM.HELDOUT_SETS.start,
+        "target": "mean regret <= 0.05",
+        "timing_seconds": round(time.perf_counter() - t0, 1),
+    }
+
+
+# The configurations measured, each in a bounded form, beside the headline
+# workload in the default run (one GPU): config 1 as stated, the protein
+# workload, the large pattern sets, the batch and the cost model's regret.
+OTHER_CONFIGS = ("dna-1MiB", "protein-256MiB", "dna-1GiB-r100k", "dna-1GiB-r10k-m16",
+                 "dna-1GiB-r10k-m64", "batch-4096", "learned-regret")
+
+
+def summary_of(line):
+    """The keys of a workload's line that the default run repeats for it."""
+    keep = ("value", "unit", "ms_per_step", "steps", "hbm_frac_of_measured_peak",
+            "hbm_frac_of_fallback_peak", "form", "occurrences", "candidates_per_step",
+            "roofline", "sync_per_call", "plain_per_request", "batched_tuned",
+            "batched_over_plain", "learned_over_tuned", "bit_exact_vs_plain", "clocks",
+            "gpu_launches", "setup_seconds")
+    out = {k: line[k] for k in keep if k in line}
+    out["config"] = line.get("config")
+    return out
+
+
+def other_configs(args, dev):
+    """The other configurations, each timed as its own workload with fewer
+    steps and a smaller tuning budget; a failure is recorded, not raised."""
+    import torch
+    sub = argparse.Namespace(**vars(args))
+    sub.params = ""
+    out = {}
+    for name in OTHER_CONFIGS:
+        t0 = time.perf_counter()
+        try:
+            if name == "batch-4096":
+                res = summary_of(run_batch(sub, 0, steps=min(args.steps, 10), fast=True))
+            elif name == "learned-regret":
+                res = run_regret(sub, dev, nsets=args.regret_sets)
+            else:
+                res = summary_of(search_line(sub, name, dev, tune_sets=16,
+                                             steps=min(args.steps, 20), e2e=False, cpu=False))
+        except Exception as e:  # recorded in the line
+            res = {"error": ("%s: %s" % (type(e).__name__, e))[:400]}
+        res["seconds"] = round(time.perf_counter() - t0, 1)
+        out[name] = res
+        torch.cuda.empty_cache()
+    return out
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=500)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="dna-1GiB",
+                    choices=sorted(WORKLOADS) + ["batch-4096"])
+    ap.add_argument("--main-only", action="store_true",
+                    help="skip the other configurations of the default run")
+    ap.add_argument("--cpu-sample-mib", type=int, default=256)
+    ap.add_argument("--ref-sample-mib", type=int, default=64)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-tune", action="store_true")
+    ap.add_argument("--tune-sample-mib", type=int, default=256)
+    ap.add_argument("--params", default="", help="JSON filter parameters; skips tuning")
+    ap.add_argument("--tune-sets", type=int, default=48)
+    ap.add_argument("--regret-sets", type=int, default=50)
+    args = ap.parse_args()
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+
+    if args.impl == "reference":
+        run_reference(args, rank)
+        return
+    if args.workload == "batch-4096":
+        line = run_batch(args, rank)
+        if rank == 0:
+            print(json.dumps(line))
+        return
+
+    import torch
+    import torch.distributed as dist
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    line = search_line(args, args.workload, dev, world=world)
+    default_run = (args.workload == "dna-1GiB" and not args.params and not args.main_only)
+    if rank == 0 and world == 1 and default_run:
+        line["other_configs"] = other_configs(args, dev)
     if rank == 0:
-        cpu = None
-        if not args.no_cpu_baseline and world == 1:
-            cpu = cpu_baseline(case, args.cpu_sample_mib << 20)
-        line = {
-            "metric": METRIC, "value": value, "unit": "GB/s", "n_gpus": world,
-            "steps": steps, "warmup": max(3, args.warmup),
-            "ms_per_step": elapsed_ms / steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "u8", "data": "synthetic",
-            "config": {"workload": args.workload, "description": desc, "n": case.n,
-                       "r": case.r, "m": case.m, "params": m.params, "tuning": tuning,
-                       "l2": ("inputs larger than L2 (no flush)" if flush is None else
-                              "text smaller than L2: L2 flushed (a %d-byte write) before "
-                              "every timed search, outside its events" % (2 * l2)),
-                       "parallelism": "replicas" if world > 1 else "single GPU"},
-            "hbm_frac_of_%s_peak" % peak_kind: value / peak,
-            "form": ("pipelined: mpm_search_async back to back, every step's status checked "
-                     "(complete, z as the synchronous search)" if pipelined_ok else
-                     "synchronous mpm_search per step"),
-            "sync_per_call": {"value": case.n * sync_steps * world / (sync_ms * 1e-3) / 1e9,
-                              "unit": "GB/s", "ms_per_step": sync_ms / sync_steps,
-                              "form": "one synchronous mpm_search per step"},
-            "occurrences": z,
-            "candidates_per_step": candidates,
-            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                         "frac": achieved / peak, "traffic": traffic,
-                         "kernel": ("mpm_scan_jit (specialised)" if st["specialised"]
-                                    else "scan_overlap_kernel (generic, overlapping q-grams)"
-                                    if m.params.get("overlap") else "scan_tma_kernel (generic)"),
-                         "peak_kind": peak_kind, "scan_ms": scan_avg,
-                         "verify_ms": verify_avg},
-            "e2e": {"value": e2e_value, "unit": "GB/s", "h2d_bytes_per_step": case.n,
-                    "d2h_bytes_per_step": 16 + 8 * ze},
-            "gpu_launches": launches,
-            "clocks": clk.summary(),
-            "cpu_baseline": cpu,
-        }
         print(json.dumps(line))
     if world > 1:
         dist.destroy_process_group()
@@ -711,14 +845,14 @@ def source_rev(files):
 
 def kernel_rev():
     """The specialised scan kernel's source and launch geometry."""
-    return source_rev(("keyhash.h", "scan_jit_args.h", "ptx_common.cuh", "window_check.cuh",
-                       "scan_jit.cuh", "jit.cpp"))
+    return source_rev(("keyhash.h", "multiword.h", "scan_jit_args.h", "ptx_common.cuh",
+                       "window_check.cuh", "scan_jit.cuh", "jit.cpp"))
 
 
 def batch_kernel_rev():
     """The batched kernel's source and its host side (units, launch)."""
-    return source_rev(("batch.cu", "stepper.cuh", "device_common.cuh", "window_check.cuh",
-                       "keyhash.h"))
+    return source_rev(("batch.cu", "stepper.cuh", "multiword.h", "device_common.cuh",
+                       "window_check.cuh", "keyhash.h"))
 
 
 def recorded_traffic(workload, params, profile="mpm_scan_jit", rev=None):

@@ -90,10 +90,11 @@ extern "C" {
  *            L' = m - q + 1.  Runs in the specialised kernels and the
  *            generic one; SMAG and mpm_batch answer MPM_ENOTSUP.
  *   wide     0: at most 64 filter positions (one 64-bit word of Shift-Or
- *            state); 1: at most 128 (two words, Section 3.2's ceil((m/q)/w)
- *            words; mask table entries of 16 bytes above 64 positions).  Runs
- *            in the generic kernel (AUTO resolves to it; SPECIALISED, SPLIT
- *            and SMAG answer MPM_ENOTSUP).
+ *            state); w = 1, 2, 3: at most 64 (w + 1) positions, the state
+ *            then ceil(positions / 64) words (Section 3.2's ceil((m/q)/w)
+ *            words, w = 64) and mask table entries of 8 bytes per word above
+ *            64 positions.  Runs in the specialised kernels and the generic
+ *            one; SMAG answers MPM_ENOTSUP above 64 positions.
  */
 #define MPM_KERNEL_AUTO        0
 #define MPM_KERNEL_GENERIC     1
@@ -118,8 +119,8 @@ typedef struct {
 typedef struct {
     int L;             /* common q-gram length of the q shifted patterns, L'  */
     int mprime;        /* AOSO subpattern length m' = floor(min(L',cap)/k)    */
-    int positions;     /* filter positions m'' = k * m' (<= 64; <= 128 wide)    */
-    int entry_bytes;   /* bytes per mask-table entry: 1, 2, 4, 8 or 16        */
+    int positions;     /* filter positions m'' = k * m' (<= 64 (wide + 1))      */
+    int entry_bytes;   /* bytes per mask-table entry: 1, 2, 4, 8, 16, 24, 32  */
     uint64_t entries;  /* sigma_r^q                                           */
     uint64_t table_bytes;
     double est_candidate_rate; /* expected candidate windows (fired subpatterns)
@@ -219,15 +220,18 @@ int mpm_set_timing(mpm_handle *h, int on);
 
 /*
  * Pipelined search: enqueues the whole search of T[0..n) (scan, verification
- * and the sort of up to 4096 occurrences) on the handle's stream and returns
- * without waiting, so successive searches keep the GPU busy.  T, out_pos and
+ * and the sort of the occurrences) on the handle's stream and returns
+ * without waiting, so successive searches keep the GPU busy.  The sort is a
+ * rank sort for up to 4096 occurrences; when cap is above 4096 a radix sort
+ * that reads the count on the device follows it for larger counts (its
+ * kernels return at once when the count is at most 4096).  T, out_pos and
  * out_pid (cap entries each) are device pointers; status points to 4
  * uint32 in device memory or in mapped host memory (cudaHostAlloc with
  * cudaHostAllocMapped).  When the stream reaches the end of the call:
  * status[0] = candidate records, status[1] = z, status[2] = 0 or the error
  * of the device work (MPM_ETIMEOUT), status[3] = 1 when out_pos/out_pid hold
  * all z occurrences sorted by (pos, pid); status[3] = 0 when they could not
- * (z > cap, z > 4096, an internal buffer too small, or an error): then run
+ * (z > cap, an internal buffer too small, or an error): then run
  * mpm_search for this text, which grows what it needs.  Successive calls
  * alternate between two internal buffer sets: the scan runs on the handle's
  * stream and the closing sort on an internal stream after it, overlapping the

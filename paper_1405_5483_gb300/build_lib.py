@@ -22,8 +22,8 @@ SOURCES = ["host_build.cpp", "capi.cu", "scan.cu", "encode.cu", "verify.cu", "so
            "tune.cpp", "batch.cu", "mlp.cu"]
 # files concatenated, in this order, into the source of the scan kernel that
 # is compiled at run time
-JIT_PARTS = ["keyhash.h", "scan_jit_args.h", "ptx_common.cuh", "window_check.cuh",
-             "scan_jit.cuh"]
+JIT_PARTS = ["keyhash.h", "multiword.h", "scan_jit_args.h", "ptx_common.cuh",
+             "window_check.cuh", "scan_jit.cuh"]
 GEN = os.path.join(OUT, "gen")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 

@@ -212,6 +212,37 @@ class Model:
         return best.as_dict(), pred.value
 
 
+# ------------------------------------------------------- batched workloads
+
+def batch_matcher(P, sigma, params):
+    """A Matcher for one set of a batch: the given parameters, or, when they
+    exceed the batched kernel's 32 filter positions, 16 greedy bins with
+    q = 4 and k = 1."""
+    from . import Matcher
+    m = Matcher(P, sigma=sigma, **params)
+    if m.info["positions"] > 32:
+        m.close()
+        m = Matcher(P, sigma=sigma, map_kind=2, sigma_r=16, q=4, k=1)
+    return m
+
+
+def learned_batch_params(batch, model, max_table_bytes=_native.BATCH_SMEM_TABLE_BYTES):
+    """The model's parameters for every pattern set of a batch (workloads.Batch):
+    features from the set's texts (entropy of their first 64 KiB each, the
+    mean length held to [2^20, 2^23] as in the training data), grid points
+    whose mask table fits max_table_bytes.  A set without texts gets {}."""
+    out = []
+    for sidx, P in enumerate(batch.sets):
+        mine = np.flatnonzero(batch.set_of_text == sidx)
+        if mine.size == 0:
+            out.append({})
+            continue
+        ent = entropy_bits(np.concatenate([batch.texts[i][:1 << 16] for i in mine]))
+        n = int(np.clip(np.mean([batch.texts[i].size for i in mine]), 1 << 20, 1 << 23))
+        out.append(model.choose(P, batch.sigma, ent, n, max_table_bytes=max_table_bytes)[0])
+    return out
+
+
 # ---------------------------------------------------------- timing database
 
 def default_params(P, sigma):

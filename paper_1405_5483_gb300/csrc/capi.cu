@@ -100,6 +100,9 @@ void release(mpm_handle* h) {
     }
     cudaFree(h->d_cand1);
     cudaFree(h->d_occ1);
+    cudaFree(h->d_occ1_tmp);
+    cudaFree(h->d_ahist[0]);
+    cudaFree(h->d_ahist[1]);
     cudaFree(h->d_counters1);
     for (auto& trio : h->ring)
         for (auto& e : trio)
@@ -380,18 +383,9 @@ static mpm_handle* build_handle(const uint8_t* P, size_t r, size_t m, int sigma,
         set_error(rc);
         return nullptr;
     }
-    if (h->plan.p.wide) {
-        // two words of state run in the generic kernels only
-        if (h->plan.p.smag || h->plan.p.kernel == MPM_KERNEL_SPECIALISED ||
-            h->plan.p.kernel == MPM_KERNEL_SPLIT) {
-            delete h;
-            set_error(MPM_ENOTSUP);
-            return nullptr;
-        }
-        h->plan.p.kernel = MPM_KERNEL_GENERIC;
-    }
-    if (h->plan.p.overlap && h->plan.p.smag) {
-        // SMAG encodes the text's non-overlapping q-grams only
+    if (h->plan.p.smag && (h->plan.p.overlap || h->plan.info.entry_bytes > 8)) {
+        // SMAG encodes the text's non-overlapping q-grams and scans them with
+        // one word of state
         delete h;
         set_error(MPM_ENOTSUP);
         return nullptr;
@@ -751,18 +745,57 @@ int mpm_search_async(mpm_handle* h, const uint8_t* T, size_t n, uint32_t* out_po
             for (int i = 0; i < 3; i++) cudaEventRecord(ev[i], s);
         }
     }
-    // the closing sort on the side stream, after this scan
+    // the closing sort on the side stream, after this scan: the rank sort
+    // up to kRankSortMax occurrences; with room for more in the outputs, the
+    // device-count radix sort after it (its kernels return at once when the
+    // rank sort had them all) and the kernel that closes the search
     const uint32_t rank_cap = (uint32_t)std::min<size_t>(cap, mpm::kRankSortMax);
+    const bool radix = cap > mpm::kRankSortMax;
+    const uint32_t cand_lim = fused_search(h) ? 0xFFFFFFFFu : (uint32_t)cand_cap;
+    uint64_t* tmp = nullptr;
+    const uint32_t sort_cap = (uint32_t)std::min<size_t>(cap, occ_cap);
+    if (radix) {
+        if (b == 0) {
+            tmp = h->d_occ_tmp;  // grown with d_occ
+        } else {
+            if (grow(&h->d_occ1_tmp, &h->occ1_tmp_cap, occ_cap)) return set_error(MPM_ENOMEM);
+            tmp = h->d_occ1_tmp;
+        }
+        if (grow(&h->d_ahist[b], &h->ahist_cap[b], mpm::sort_dev_hist_entries(sort_cap)))
+            return set_error(MPM_ENOMEM);
+    }
     if (cudaEventRecord(h->scan_done[b], s) != cudaSuccess ||
         cudaStreamWaitEvent(h->side, h->scan_done[b], 0) != cudaSuccess ||
-        mpm::launch_rank_sort(occ, counters, rank_cap, out_pos, out_pid, dstatus,
-                              fused_search(h) ? 0xFFFFFFFFu : (uint32_t)cand_cap,
-                              (uint32_t)occ_cap, h->side) < 0 ||
-        cudaEventRecord(h->sort_done[b], h->side) != cudaSuccess) {
+        mpm::launch_rank_sort(occ, counters, rank_cap, out_pos, out_pid,
+                              radix ? nullptr : dstatus, cand_lim, (uint32_t)occ_cap,
+                              h->side) < 0) {
         cudaGetLastError();
         return set_error(MPM_ECUDA);
     }
     launches++;
+    if (radix) {
+        // digits of the key (pos << 32) | pid that can be non-zero
+        int shifts[8], ns = 0;
+        const int pid_bits = bits_for(h->plan.r > 1 ? h->plan.r - 1 : 1);
+        const int pos_bits = bits_for(n);
+        for (int v = 0; v < pid_bits; v += 8) shifts[ns++] = v;
+        for (int v = 0; v < pos_bits; v += 8) shifts[ns++] = 32 + v;
+        uint64_t* sorted = nullptr;
+        const int l = mpm::launch_sort_dev(occ, tmp, h->d_ahist[b], sort_cap,
+                                           counters + mpm::kOccCount, shifts, ns, h->num_sms,
+                                           &sorted, h->side, mpm::kRankSortMax);
+        if (l < 0 || mpm::launch_close_sorted(sorted, counters, (uint32_t)cap, out_pos, out_pid,
+                                              dstatus, cand_lim, (uint32_t)occ_cap,
+                                              mpm::kRankSortMax, h->num_sms, h->side) < 0) {
+            cudaGetLastError();
+            return set_error(MPM_ECUDA);
+        }
+        launches += l + 1;
+    }
+    if (cudaEventRecord(h->sort_done[b], h->side) != cudaSuccess) {
+        cudaGetLastError();
+        return set_error(MPM_ECUDA);
+    }
     h->sort_pending[b] = true;
     h->stats.launches += (uint32_t)launches;
     dirty = false;
@@ -802,7 +835,6 @@ int mpm_jit_compile(const uint8_t* P, size_t r, size_t m, int sigma, const mpm_p
     mpm::Plan plan;
     int rc = mpm::make_plan(P, r, m, sigma, params, &plan);
     if (rc) return set_error(rc);
-    if (plan.p.wide) return set_error(MPM_ENOTSUP);  // generic kernels only
     mpm::FilterDev f{};
     f.table_bytes = (uint32_t)((plan.info.table_bytes + 15) & ~uint64_t(15));
     f.entry_bytes = plan.info.entry_bytes;

@@ -61,6 +61,12 @@ struct mpm_handle {
     size_t cand1_cap = 0;
     uint64_t* d_occ1 = nullptr;
     size_t occ1_cap = 0;
+    // the device-count radix sort that closes pipelined searches with more
+    // than kRankSortMax outputs: key buffers for set 1 and a histogram each
+    uint64_t* d_occ1_tmp = nullptr;
+    size_t occ1_tmp_cap = 0;
+    uint32_t* d_ahist[2] = {nullptr, nullptr};
+    size_t ahist_cap[2] = {0, 0};
     uint32_t* d_counters1 = nullptr;
     bool counters1_dirty = false;
     int async_set = 0;

@@ -89,7 +89,7 @@ struct Lengths {
 
 // L' = the q-gram pattern length: floor((m-q+1)/q) non-overlapping q-grams
 // (common to the q shifts), or m-q+1 overlapping ones; the filter keeps at
-// most maxpos of them (64 for one word of Shift-Or state, 128 for two).
+// most maxpos of them (64 for each 64-bit word of Shift-Or state).
 Lengths lengths(size_t m, int q, int k, bool overlap, int maxpos) {
     Lengths x;
     long L = overlap ? ((long)m - q + 1) : ((long)m - q + 1) / q;
@@ -100,12 +100,13 @@ Lengths lengths(size_t m, int q, int k, bool overlap, int maxpos) {
     return x;
 }
 
+// Bytes of a mask-table entry: the smallest word that holds the positions,
+// above 64 positions ceil(positions / 64) words of 8 bytes (Section 3.2).
 int entry_bytes_for(int positions) {
     if (positions <= 8) return 1;
     if (positions <= 16) return 2;
     if (positions <= 32) return 4;
-    if (positions <= 64) return 8;
-    return 16;
+    return 8 * ((positions + 63) / 64);
 }
 
 // Probability, under the pattern-set symbol frequencies mapped by mu, that a
@@ -296,9 +297,9 @@ int make_plan(const uint8_t* P, size_t r, size_t m, int sigma, const mpm_params*
     if (req.table_place < 0 || req.table_place > MPM_TABLE_GLOBAL) return MPM_EINVAL;
     if (req.smag < 0 || req.smag > 1 || req.chunk < 0) return MPM_EINVAL;
     if (req.overlap < 0 || req.overlap > 1) return MPM_EINVAL;
-    if (req.wide < 0 || req.wide > 1) return MPM_EINVAL;
+    if (req.wide < 0 || req.wide > kMaxWords - 1) return MPM_EINVAL;
     const bool ov = req.overlap == 1;
-    const int maxpos = req.wide ? 2 * kMaxPositions : kMaxPositions;
+    const int maxpos = (req.wide + 1) * kMaxPositions;
     if (req.kernel < MPM_KERNEL_AUTO || req.kernel > MPM_KERNEL_SPLIT) return MPM_EINVAL;
 
     uint64_t h[256];

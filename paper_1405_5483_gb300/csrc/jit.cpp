@@ -165,7 +165,6 @@ bool jit_spec(const FilterDev& f, bool verify, JitSpec* out) {
     s.smem = f.smem_table ? 1 : 0;
     s.table_bytes = f.smem_table ? (int)f.table_bytes : 0;
     s.ov = f.overlap ? 1 : 0;
-    if (f.entry_bytes > 8) return false;  // two words of state: generic kernels only
     // bytes per sampled q-gram: k q non-overlapping, k overlapping
     const uint32_t P = (uint32_t)(s.ov ? f.k : f.k * f.q);
     const uint32_t base = lcm_u(P, 16);

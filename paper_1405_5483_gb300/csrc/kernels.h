@@ -24,7 +24,7 @@ enum Counter : int {
 struct FilterDev {
     const void* table;        // mask table, global memory
     uint32_t table_bytes;     // padded to a multiple of 16
-    int entry_bytes;          // 1, 2, 4, 8, or 16 (two words of state)
+    int entry_bytes;          // 1, 2, 4, 8; 16, 24, 32 (2 - 4 words of state)
     int smem_table;           // copy the table into shared memory
     const uint8_t* mu;        // 256-entry byte -> reduced symbol map
     int map_kind, q, k, ell, shift, mprime, positions;
@@ -121,11 +121,20 @@ constexpr uint32_t kRankSortMax = 4096;
 // `shifts`, with the count read on the device and fixed grids, so that it
 // can be captured in a CUDA graph.  tmp holds cap keys, hist
 // sort_dev_hist_entries(cap) entries; *sorted receives keys or tmp,
-// whichever holds the result.
+// whichever holds the result.  Every kernel returns at once when
+// *count <= skip (the rank sort has those).
 size_t sort_dev_hist_entries(uint32_t cap);
 int launch_sort_dev(uint64_t* keys, uint64_t* tmp, uint32_t* hist, uint32_t cap,
                     const uint32_t* count, const int* shifts, int nshifts, int num_sms,
-                    uint64_t** sorted, cudaStream_t s);
+                    uint64_t** sorted, cudaStream_t s, uint32_t skip = 0);
+// Closes a pipelined search after launch_sort_dev: when from < count <=
+// min(out_cap, occ_cap) the sorted keys are split into out_pos/out_pid;
+// always, the counters go to the snapshot (the fourth word 1 when the
+// outputs hold every occurrence) and are zeroed.
+int launch_close_sorted(const uint64_t* sorted, uint32_t* counters, uint32_t out_cap,
+                        uint32_t* out_pos, uint32_t* out_pid, uint32_t* snapshot,
+                        uint32_t cand_cap, uint32_t occ_cap, uint32_t from, int num_sms,
+                        cudaStream_t s);
 int launch_rank_sort(const uint64_t* keys, uint32_t* counters, uint32_t out_cap,
                      uint32_t* out_pos, uint32_t* out_pid, uint32_t* snapshot, uint32_t cand_cap,
                      uint32_t occ_cap, cudaStream_t s);

@@ -21,7 +21,8 @@ int set_error(int code);
 
 // Largest k (the sampling step) and filter width accepted by the kernels.
 constexpr int kMaxK = 32;
-constexpr int kMaxPositions = 64;
+constexpr int kMaxPositions = 64;  // per 64-bit word of Shift-Or state
+constexpr int kMaxWords = 4;       // words of state: wide = 0 .. kMaxWords - 1
 
 static_assert(sizeof(Slot) == 24, "slot layout");
 

@@ -425,7 +425,9 @@ int launch_mode(const ScanArgs& A, int num_sms, int chunk, cudaStream_t s) {
             case 2: return launch_overlap<MODE, uint16_t>(A, num_sms, chunk, s);
             case 4: return launch_overlap<MODE, uint32_t>(A, num_sms, chunk, s);
             case 8: return launch_overlap<MODE, uint64_t>(A, num_sms, chunk, s);
-            default: return launch_overlap<MODE, U128>(A, num_sms, chunk, s);
+            case 16: return launch_overlap<MODE, Words<2>>(A, num_sms, chunk, s);
+            case 24: return launch_overlap<MODE, Words<3>>(A, num_sms, chunk, s);
+            default: return launch_overlap<MODE, Words<4>>(A, num_sms, chunk, s);
         }
     }
     switch (A.f.entry_bytes) {
@@ -433,7 +435,9 @@ int launch_mode(const ScanArgs& A, int num_sms, int chunk, cudaStream_t s) {
         case 2: return launch_typed<MODE, uint16_t>(A, num_sms, chunk, s);
         case 4: return launch_typed<MODE, uint32_t>(A, num_sms, chunk, s);
         case 8: return launch_typed<MODE, uint64_t>(A, num_sms, chunk, s);
-        default: return launch_typed<MODE, U128>(A, num_sms, chunk, s);
+        case 16: return launch_typed<MODE, Words<2>>(A, num_sms, chunk, s);
+        case 24: return launch_typed<MODE, Words<3>>(A, num_sms, chunk, s);
+        default: return launch_typed<MODE, Words<4>>(A, num_sms, chunk, s);
     }
 }
 
@@ -454,7 +458,7 @@ int launch_scan(const ScanArgs& A, int num_sms, int chunk, cudaStream_t s) {
 
 int launch_scan_codes(const uint32_t* codes, uint32_t nq, const FilterDev& f, uint64_t* cand,
                       uint32_t cap, uint32_t* counters, cudaStream_t s) {
-    if (f.entry_bytes > 8) return -2;  // two-word state: the generic MAG scan only
+    if (f.entry_bytes > 8) return -2;  // several words of state: the MAG scans only
     const uint32_t nsamp = nq / (uint32_t)f.k;
     if (nsamp == 0) return 0;
     const uint32_t per = std::max<uint32_t>(64, nsamp / (1u << 18));

@@ -10,7 +10,8 @@
 //                     q-gram generation), 1: byte map mu through a table,
 //                     2: whole q-grams hashed to 2^MPM_ELL bins (Section 3.3,
 //                     alphabet mapping on the q-grams)
-//   MPM_EB            bytes per mask-table entry (1, 2, 4, 8)
+//   MPM_EB            bytes per mask-table entry (1, 2, 4, 8; 16, 24, 32 for
+//                     2 - 4 words of Shift-Or state, multiword.h)
 //   MPM_SMEM          1: mask table copied to shared memory
 //   MPM_TABLE_BYTES   mask-table bytes (padded to 16)
 //   MPM_C             bytes of a row per stage: a multiple of 16 and of k*q
@@ -94,10 +95,16 @@ typedef u8 ET;
 typedef u16 ET;
 #elif MPM_EB == 4
 typedef u32 ET;
-#else
+#elif MPM_EB == 8
 typedef u64 ET;
+#else
+typedef Words<MPM_EB / 8> ET;  // more than 64 positions: several words
 #endif
+#if MPM_EB > 8
+typedef Words<MPM_EB / 8> DT;
+#else
 typedef Cond<(MPM_EB == 8), u64, u32>::T DT;
+#endif
 typedef Cond<(OV || NS * K > 32), u64, u32>::T FT;
 // overlapping q-grams: samples per 64-bit word of report bits, and words
 constexpr int SPW = 64 / K;
@@ -177,7 +184,7 @@ __device__ __forceinline__ void run_stage(const u32* w, DT& D, FT& fm, const ET*
     for (int u = 0; u < NS; u++) {
         const u32 c = code_at(w, rw, smu, u * P + (K - 1) * Q);
         D = (D << K) | (DT)tab[c];
-        if (REPORT) fm |= ((FT)((u32)(~D >> RSH) & KMASK)) << (u * K);
+        if (REPORT) fm |= ((FT)(~bits_at(D, RSH) & KMASK)) << (u * K);
     }
 }
 
@@ -207,7 +214,7 @@ __device__ __forceinline__ void fired_stage_ov(const u32* x, const u32* rx, DT D
     for (int u = 0; u < NS; u++) {
         const u32 c = code_at(x, rx, smu, TW * 4 + E0 - (Q - 1) + u * K);
         D = (D << K) | (DT)tab[c];
-        u32 f = (u32)(~D >> RSH) & KMASK;
+        u32 f = ~bits_at(D, RSH) & KMASK;
         const i64 hs = hs0 + (i64)u * K;
         if (hs < K - 1) f &= hs < 0 ? 0u : ((1u << (u32)(hs + 1)) - 1u);
         fm[u / SPW] |= (FT)f << ((u % SPW) * K);
@@ -485,7 +492,7 @@ extern "C" __global__ void __launch_bounds__(MPM_WARPS * 32, 1)
                                 (int)((gw + (j / nst) * RW) * 32), bar);
                 }
 #if MPM_OV
-                const bool any = valid && (((u32)(~acc >> RSH) & KMASK) != 0u);
+                const bool any = valid && ((~bits_at(acc, RSH) & KMASK) != 0u);
                 if (__any_sync(0xFFFFFFFFu, any)) {
                     // some lane fired: which samples, from the saved D
                     const i64 h1 = (i64)row_start + (i64)st * C + (E0 - (Q - 1));
@@ -534,7 +541,7 @@ extern "C" __global__ void __launch_bounds__(MPM_WARPS * 32, 1)
         for (; h + Q <= (i64)b; h += K) {
             if (h < 0) continue;
             D = (D << K) | (DT)tab[code_bytes(A.T, (u32)h, s_mu)];
-            const u32 fired = (u32)(~D >> RSH) & KMASK;
+            const u32 fired = ~bits_at(D, RSH) & KMASK;
             if (fired) {
                 // rare: handled by the lane alone
                 const u32 idx = atomicAdd(&A.counters[kCandCountJ], 1u);
@@ -557,7 +564,7 @@ extern "C" __global__ void __launch_bounds__(MPM_WARPS * 32, 1)
         for (u32 e = a + P; e <= b; e += P) {
             const u32 st = e - Q;
             D = (D << K) | (DT)tab[code_bytes(A.T, st, s_mu)];
-            const u32 fired = (u32)(~D >> RSH) & KMASK;
+            const u32 fired = ~bits_at(D, RSH) & KMASK;
             if (fired) {
                 // rare: handled by the lane alone
                 const u32 idx = atomicAdd(&A.counters[kCandCountJ], 1u);

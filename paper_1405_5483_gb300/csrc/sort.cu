@@ -225,8 +225,9 @@ __device__ __forceinline__ uint32_t dev_tiles(const uint32_t* count, uint32_t ca
 
 __global__ void __launch_bounds__(kRadixThreads)
     dev_hist_kernel(const uint64_t* keys, const uint32_t* count, uint32_t cap, int shift,
-                    uint32_t* hist, uint32_t ntmax) {
+                    uint32_t* hist, uint32_t ntmax, uint32_t skip) {
     __shared__ uint32_t h[256];
+    if (*count <= skip) return;
     const uint32_t z = min(*count, cap);
     const uint32_t nt = dev_tiles(count, cap);
     for (uint32_t t = blockIdx.x; t < nt; t += gridDim.x) {
@@ -243,9 +244,11 @@ __global__ void __launch_bounds__(kRadixThreads)
 
 // Exclusive prefix sum, in (digit, tile) order, over the tiles in use.
 __global__ void __launch_bounds__(1024)
-    dev_scan_kernel(uint32_t* hist, const uint32_t* count, uint32_t cap, uint32_t ntmax) {
+    dev_scan_kernel(uint32_t* hist, const uint32_t* count, uint32_t cap, uint32_t ntmax,
+                    uint32_t skip) {
     __shared__ uint32_t warp_sums[32];
     __shared__ uint32_t carry;
+    if (*count <= skip) return;
     const uint32_t nt = dev_tiles(count, cap);
     const uint32_t len = 256 * nt;
     if (threadIdx.x == 0) carry = 0;
@@ -282,8 +285,9 @@ __global__ void __launch_bounds__(1024)
 
 __global__ void __launch_bounds__(kRadixThreads)
     dev_scatter_kernel(const uint64_t* in, uint64_t* out, const uint32_t* count, uint32_t cap,
-                       int shift, const uint32_t* offs, uint32_t ntmax) {
+                       int shift, const uint32_t* offs, uint32_t ntmax, uint32_t skip) {
     __shared__ uint32_t cnt[kRadixWarps][256];
+    if (*count <= skip) return;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const uint32_t z = min(*count, cap);
     const uint32_t nt = dev_tiles(count, cap);
@@ -326,7 +330,50 @@ __global__ void __launch_bounds__(kRadixThreads)
     }
 }
 
+// The end of a pipelined search whose keys were radix-sorted on the device
+// (more than `from` occurrences): the sorted keys split into the outputs,
+// and, as in rank_sort_kernel, the counters copied to the snapshot with the
+// completeness word and zeroed for the next search by the last block.
+__global__ void __launch_bounds__(256)
+    close_sorted_kernel(const uint64_t* sorted, uint32_t* counters, uint32_t out_cap,
+                        uint32_t* out_pos, uint32_t* out_pid, uint32_t* snapshot,
+                        uint32_t cand_cap, uint32_t occ_cap, uint32_t from) {
+    __shared__ uint32_t s_z;
+    if (threadIdx.x == 0) s_z = *(volatile uint32_t*)&counters[kOccCount];
+    __syncthreads();
+    const uint32_t z = s_z;
+    if (threadIdx.x == 0) {
+        __threadfence();
+        if (atomicAdd(&counters[kDoneCount], 1u) == gridDim.x - 1) {
+            __threadfence();
+            volatile uint32_t* c = counters;
+            const uint32_t cand = c[kCandCount], occ = c[kOccCount], err = c[kErrorFlag];
+            snapshot[kCandCount] = cand;
+            snapshot[kOccCount] = occ;
+            snapshot[kErrorFlag] = err;
+            snapshot[kDoneCount] =
+                (err == 0 && occ <= out_cap && occ <= occ_cap && cand <= cand_cap) ? 1u : 0u;
+            for (int i = 0; i < kNumCounters; i++) c[i] = 0;
+        }
+    }
+    if (z <= from || z > out_cap || z > occ_cap) return;
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < z; i += gridDim.x * blockDim.x) {
+        const uint64_t k = sorted[i];
+        out_pos[i] = (uint32_t)(k >> 32);
+        out_pid[i] = (uint32_t)k;
+    }
+}
+
 }  // namespace
+
+int launch_close_sorted(const uint64_t* sorted, uint32_t* counters, uint32_t out_cap,
+                        uint32_t* out_pos, uint32_t* out_pid, uint32_t* snapshot,
+                        uint32_t cand_cap, uint32_t occ_cap, uint32_t from, int num_sms,
+                        cudaStream_t s) {
+    close_sorted_kernel<<<num_sms, 256, 0, s>>>(sorted, counters, out_cap, out_pos, out_pid,
+                                                 snapshot, cand_cap, occ_cap, from);
+    return cudaPeekAtLastError() == cudaSuccess ? 1 : -1;
+}
 
 size_t sort_dev_hist_entries(uint32_t cap) {
     return 256 * (size_t)((cap + kDevTile - 1) / kDevTile + 1);
@@ -334,17 +381,18 @@ size_t sort_dev_hist_entries(uint32_t cap) {
 
 int launch_sort_dev(uint64_t* keys, uint64_t* tmp, uint32_t* hist, uint32_t cap,
                     const uint32_t* count, const int* shifts, int nshifts, int num_sms,
-                    uint64_t** sorted, cudaStream_t s) {
+                    uint64_t** sorted, cudaStream_t s, uint32_t skip) {
     const uint32_t ntmax = (cap + kDevTile - 1) / kDevTile + 1;
     const uint32_t grid = std::min<uint32_t>(ntmax, (uint32_t)num_sms * 4);
     uint64_t* src = keys;
     uint64_t* dst = tmp;
     int launches = 0;
     for (int p = 0; p < nshifts; p++) {
-        dev_hist_kernel<<<grid, kRadixThreads, 0, s>>>(src, count, cap, shifts[p], hist, ntmax);
-        dev_scan_kernel<<<1, 1024, 0, s>>>(hist, count, cap, ntmax);
+        dev_hist_kernel<<<grid, kRadixThreads, 0, s>>>(src, count, cap, shifts[p], hist, ntmax,
+                                                       skip);
+        dev_scan_kernel<<<1, 1024, 0, s>>>(hist, count, cap, ntmax, skip);
         dev_scatter_kernel<<<grid, kRadixThreads, 0, s>>>(src, dst, count, cap, shifts[p], hist,
-                                                          ntmax);
+                                                          ntmax, skip);
         launches += 3;
         uint64_t* t = src;
         src = dst;

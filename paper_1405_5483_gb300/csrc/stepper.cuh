@@ -9,6 +9,7 @@
 #include <type_traits>
 
 #include "device_common.cuh"
+#include "multiword.h"
 
 namespace mpm {
 
@@ -20,38 +21,16 @@ enum ScanMode : int {
     kQHash = 4    // raw-byte window, whole q-gram hashed to a bin (q <= 5)
 };
 
-// Two 64-bit words of Shift-Or state, and a mask table entry of 16 bytes
-// (bits 0..63 in lo, 64..127 in hi: the entry's bytes little-endian), for
-// filters of up to 128 positions (Section 3.2: ceil((m/q)/w) words, w = 64).
-struct U128 {
-    uint64_t lo, hi;
-    U128() = default;
-    __host__ __device__ constexpr U128(uint64_t v) : lo(v), hi(0) {}
-    __host__ __device__ constexpr U128(uint64_t l, uint64_t h) : lo(l), hi(h) {}
-    __host__ __device__ explicit operator uint32_t() const { return (uint32_t)lo; }
-};
-__device__ __forceinline__ U128 operator~(const U128& a) { return U128(~a.lo, ~a.hi); }
-__device__ __forceinline__ U128 operator|(const U128& a, const U128& b) {
-    return U128(a.lo | b.lo, a.hi | b.hi);
-}
-__device__ __forceinline__ U128 operator<<(const U128& a, int s) {
-    if (s == 0) return a;
-    if (s >= 64) return U128(0, a.lo << (s - 64));
-    return U128(a.lo << s, (a.hi << s) | (a.lo >> (64 - s)));
-}
-__device__ __forceinline__ U128 operator>>(const U128& a, int s) {
-    if (s == 0) return a;
-    if (s >= 64) return U128(a.hi >> (s - 64), 0);
-    return U128((a.lo >> s) | (a.hi << (64 - s)), a.hi >> s);
-}
-
+// Shift-Or state of more than one 64-bit word: Words<W> (multiword.h), the
+// mask-table entries of the same width (8 W bytes), for filters of up to
+// 64 W positions.
 template <typename ET>
 struct StateOf {  // the Shift-Or state type for table entries of type ET
     using type = typename std::conditional<sizeof(ET) == 8, uint64_t, uint32_t>::type;
 };
-template <>
-struct StateOf<U128> {
-    using type = U128;
+template <int W>
+struct StateOf<Words<W>> {
+    using type = Words<W>;
 };
 
 template <int MODE, typename ET>
@@ -127,7 +106,7 @@ __device__ __forceinline__ uint32_t load_word(const uint8_t* T, uint64_t at) {
 
 template <typename DT>
 __device__ __forceinline__ uint32_t fired_bits(DT D, int rsh, uint32_t kmask) {
-    return (uint32_t)(~D >> rsh) & kmask;
+    return ~bits_at(D, rsh) & kmask;
 }
 
 // Warm-up over the bytes [row_start - Wr, row_start): builds D from the

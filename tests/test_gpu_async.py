@@ -73,15 +73,24 @@ def test_incomplete_cases_and_the_synchronous_rerun(mpm, native):
     assert s[1] == z and s[3] == 0          # z > cap
     pos, pid = m.search(T)
     assert np.array_equal(as_u32(pos), want[0]) and np.array_equal(as_u32(pid), want[1])
-    # more than 4096 occurrences: runs of one symbol
+    # more than 4096 occurrences (runs of one symbol): the radix sort closes
+    # the search when the outputs have room; with 4096 entries they have not
     runs = np.full(20_000, 65, np.uint8)
     P = np.full((2, 8), 65, np.uint8)
     m2 = mpm.Matcher(P, sigma=2)
     big = torch.empty(1 << 16, dtype=torch.int32, device="cuda")
-    m2.search_async(torch.from_numpy(runs).cuda(), big, big.clone(), status)
+    bigi = big.clone()
+    m2.search_async(torch.from_numpy(runs).cuda(), big, bigi, status)
     m2.sync()
     s = status.cpu().numpy()
-    assert s[1] == 2 * (20_000 - 7) and s[3] == 0
+    zr = 2 * (20_000 - 7)
+    assert s[1] == zr and s[3] == 1
+    wr = native.aho_corasick(runs, P)
+    assert np.array_equal(as_u32(big)[:zr], wr[0]) and np.array_equal(as_u32(bigi)[:zr], wr[1])
+    m2.search_async(torch.from_numpy(runs).cuda(), big[:4096], bigi[:4096], status)
+    m2.sync()
+    s = status.cpu().numpy()
+    assert s[1] == zr and s[3] == 0
     # a text shorter than the patterns: z = 0, complete
     m.search_async(T[:5], small, small.clone(), status)
     m.sync()
@@ -167,3 +176,41 @@ def test_join_orders_later_stream_work_and_stream_switches(mpm, native):
     for c in late:
         assert np.array_equal(c.cpu().numpy().view(np.uint32), want[1])
     assert np.all(status.cpu().numpy()[:, 3] == 1)
+
+
+@pytest.mark.parametrize("z_target", [4095, 4097, 9000, 70_000])
+def test_pipelined_large_counts_through_both_buffer_sets(mpm, native, z_target):
+    """Counts on both sides of the rank sort's 4096, several searches in a
+    row (both internal buffer sets, the closing sorts overlapping the next
+    scans), each against the oracle; the occurrence buffer's first size
+    (65 536) is exceeded by the last count, which the synchronous search
+    then grows for the pipelined calls after it."""
+    rng = np.random.default_rng(z_target)
+    n = 1 << 22
+    T = (rng.integers(0, 4, n) + 65).astype(np.uint8)
+    P = (rng.integers(0, 4, (50, 16)) + 65).astype(np.uint8)
+    offs = rng.choice(n // 16, size=z_target, replace=False) * 16
+    for i, o in enumerate(offs):
+        T[o:o + 16] = P[i % 50]
+    want = native.aho_corasick(T, P, threads=8)
+    z = want[0].size
+    Td = torch.from_numpy(T).cuda()
+    m = mpm.Matcher(P, sigma=4)
+    cap = 1 << 17
+    outs = [(torch.full((cap,), -1, dtype=torch.int32, device="cuda"),
+             torch.full((cap,), -1, dtype=torch.int32, device="cuda")) for _ in range(3)]
+    status = torch.zeros((3, 4), dtype=torch.int32, device="cuda")
+    for attempt in range(2):
+        for i in range(3):
+            m.search_async(Td, outs[i][0], outs[i][1], status[i])
+        m.sync()
+        st = status.cpu().numpy()
+        if attempt == 0 and z > 65536:
+            assert np.all(st[:, 3] == 0)   # the first occurrence buffer is too small
+            m.search(Td)                   # grows it
+            continue
+        assert np.all(st[:, 1] == z) and np.all(st[:, 2] == 0) and np.all(st[:, 3] == 1), st
+        for pos, pid in outs:
+            assert np.array_equal(as_u32(pos)[:z], want[0])
+            assert np.array_equal(as_u32(pid)[:z], want[1])
+        break

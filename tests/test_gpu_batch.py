@@ -138,3 +138,39 @@ def test_batch_grows_when_occurrences_outgrow_its_buffers(mpm, native):
     b = mpm.Batch(ms, dev, sot)
     assert np.array_equal(triples(*b.run()), want)
     assert np.array_equal(triples(*b.run()), want)
+
+
+def test_config4_full_shape_learned_parameters_equal_oracle(mpm, native):
+    """The benchmarked batch exactly as the benchmark builds it: 4096 texts of
+    1 KiB - 4 MiB against 64 pattern sets (r up to 10^4), each set's
+    parameters proposed by the committed cost model among mask tables that fit
+    the batched kernel's shared memory; every (text, pos, pid) triple equals
+    Aho-Corasick per text."""
+    from concurrent.futures import ThreadPoolExecutor
+
+    from paper_1405_5483_gb300 import _native
+    from paper_1405_5483_gb300 import cost_model as CM
+    b = W.config4()
+    model = CM.Model.load()
+    params = CM.learned_batch_params(b, model, _native.BATCH_SMEM_TABLE_BYTES)
+    ms = [CM.batch_matcher(P, b.sigma, p) for P, p in zip(b.sets, params)]
+    assert max(P.shape[0] for P in b.sets) > 5000 and max(t.size for t in b.texts) > 1 << 21
+    dev = [torch.from_numpy(t).cuda() for t in b.texts]
+    B = mpm.Batch(ms, dev, b.set_of_text)
+    got = triples(*B.run())
+    B.close()
+
+    acs = [native.AhoCorasick(P) for P in b.sets]
+
+    def one(t):
+        pos, pid = acs[b.set_of_text[t]].search(b.texts[t])
+        return np.stack([np.full(pos.size, t, np.uint32), pos, pid], axis=1)
+
+    with ThreadPoolExecutor(max_workers=16) as ex:
+        parts = list(ex.map(one, range(len(b.texts))))
+    for ac in acs:
+        ac.close()
+    want = np.concatenate(parts)
+    assert want.shape[0] > 10_000
+    assert got.shape == want.shape
+    assert np.array_equal(got, want)

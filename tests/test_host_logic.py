@@ -155,36 +155,39 @@ def test_host_tables_overlapping_qgrams_equal_oracle(mpm, seed):
 
 
 def _wide_positions(table, entry_bytes, positions):
-    # entries as Python integers: up to 16 little-endian bytes each
+    # entries as Python integers: up to 32 little-endian bytes each
     t = table.reshape(-1, entry_bytes)
     mask = (1 << positions) - 1
     return [int.from_bytes(bytes(row), "little") & mask for row in t]
 
 
-@pytest.mark.parametrize("seed", range(12))
-def test_host_tables_two_word_state_equal_oracle(mpm, seed):
+@pytest.mark.parametrize("seed", range(18))
+def test_host_tables_multiword_state_equal_oracle(mpm, seed):
+    """Filters of up to 64 (wide + 1) positions: ceil(positions / 64) words
+    of state, mask-table entries of 8 bytes per word (Section 3.2)."""
     rng = np.random.default_rng(700 + seed)
     sigma = int(rng.choice([4, 20]))
     r = int(rng.integers(1, 40))
-    m = int(rng.choice([80, 130, 200, 260]))
+    m = int(rng.choice([80, 130, 200, 260, 330]))
     q = int(rng.integers(1, 3))
     sr = 4
     k = int(rng.integers(1, 5))
     overlap = int(rng.integers(0, 2))
+    wide = 1 + seed % 3
+    maxpos = 64 * (wide + 1)
     P = (rng.integers(0, sigma, size=(r, m)) + 65).astype(np.uint8)
-    kw = dict(q=q, sigma_r=sr, k=k, map_kind=2, wide=1, overlap=overlap)
+    kw = dict(q=q, sigma_r=sr, k=k, map_kind=2, wide=wide, overlap=overlap)
     mu, table, info = mpm.host_tables(P, sigma, **kw)
     Lc = (m - q + 1) if overlap else (m - q + 1) // q
-    assert info["positions"] == k * (min(Lc, 128) // k)
-    p = dict(q=q, sigma_r=sr, k=k, map_kind=2, map_shift=info["map_shift"], overlap=overlap)
-    fp = F.make_params(P, q, sr, k, "greedy", overlap=bool(overlap), max_positions=128)
+    assert info["positions"] == k * (min(Lc, maxpos) // k)
+    fp = F.make_params(P, q, sr, k, "greedy", overlap=bool(overlap), max_positions=maxpos)
     cls = F.pattern_classes(P, fp)
     otab = F.mask_table(cls, fp)
     assert np.array_equal(mu, fp.mu) and info["positions"] == len(cls)
     got = _wide_positions(table, info["entry_bytes"], len(cls))
     assert got == [int(x) for x in otab]
     if info["positions"] > 64:
-        assert info["entry_bytes"] == 16
+        assert info["entry_bytes"] == 8 * -(-info["positions"] // 64)
     # without wide, the same request keeps 64 positions at most
     _, info64 = mpm.plan(P, sigma, q=q, sigma_r=sr, k=k, map_kind=2, overlap=overlap)
     assert info64["positions"] <= 64
@@ -192,9 +195,9 @@ def test_host_tables_two_word_state_equal_oracle(mpm, seed):
 
 def test_overlap_refusals(mpm):
     P = np.frombuffer(b"ACGTACGTACGTACGT", np.uint8).reshape(1, 16)
-    # two words of state stay in the generic kernels
-    rc, _ = mpm.jit_compile(P, 4, q=1, sigma_r=4, k=1, map_kind=2, wide=1)
-    assert rc == mpm.MPM_ENOTSUP
+    # more than four words of state are refused
+    with pytest.raises(mpm.MpmError):
+        mpm.plan(P, 4, q=1, sigma_r=4, k=1, map_kind=2, wide=4)
     # the planner keeps q-gram hashing to the generic kernel's 5 bytes
     p, _ = mpm.plan(P, 4, map_kind=4, sigma_r=1 << 12, overlap=1)
     assert p["q"] <= 5 and p["overlap"] == 1
@@ -244,6 +247,12 @@ JIT_GRID = [
     ("protein", 32, dict(q=5, sigma_r=1 << 16, k=1, map_kind=4, overlap=1, kernel=2)),
     ("protein", 32, dict(q=3, sigma_r=16, k=6, map_kind=2, overlap=1, kernel=3)),
     ("english", 64, dict(q=4, sigma_r=8, k=16, map_kind=1, overlap=1, kernel=2)),
+    # 2, 3 and 4 words of state (wide), both q-gram families
+    ("dna", 300, dict(q=1, sigma_r=4, k=1, map_kind=2, wide=1, kernel=2)),
+    ("dna", 300, dict(q=1, sigma_r=4, k=2, map_kind=2, wide=2, kernel=3)),
+    ("dna", 300, dict(q=1, sigma_r=4, k=1, map_kind=2, wide=3, kernel=2)),
+    ("dna", 300, dict(q=2, sigma_r=4, k=1, map_kind=3, map_shift=1, wide=3, overlap=1, kernel=3)),
+    ("protein", 260, dict(q=3, sigma_r=1 << 12, k=1, map_kind=4, wide=2, overlap=1, kernel=2)),
 ]
 
 
