@@ -41,6 +41,10 @@ WORKLOADS = {
     "dna-1GiB": ("config1_scaled", 4,
                  "uniform DNA text 1 GiB, r=100, m=16, half planted (config-1 shape at scale)"),
     "dna-1MiB": ("config1", 4, "uniform DNA text 1 MiB, r=100, m=16, half planted"),
+    # the same at 256 MiB: still larger than L2, small enough for a full
+    # profiler capture of the scan
+    "dna-256MiB": ("config1_scaled", 4, "uniform DNA text 256 MiB, r=100, m=16, half planted",
+                   {"n": 1 << 28}),
     "protein-256MiB-varlen": ("config2_varlen", 20,
                               "protein-like text 256 MiB, r=1000 patterns of lengths 16..64, "
                               "half planted (filter on the 16-byte prefixes)"),

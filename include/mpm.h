@@ -223,8 +223,10 @@ int mpm_set_timing(mpm_handle *h, int on);
  * and the sort of the occurrences) on the handle's stream and returns
  * without waiting, so successive searches keep the GPU busy.  The sort is a
  * rank sort for up to 4096 occurrences; when cap is above 4096 a radix sort
- * that reads the count on the device follows it for larger counts (its
- * kernels return at once when the count is at most 4096).  T, out_pos and
+ * that reads the count on the device follows it for larger counts (one
+ * more kernel, in one block, for cap up to 2^20; above that, a multi-block
+ * sort of about 3 kernels per byte of key; it returns at once when the
+ * count is at most 4096).  T, out_pos and
  * out_pid (cap entries each) are device pointers; status points to 4
  * uint32 in device memory or in mapped host memory (cudaHostAlloc with
  * cudaHostAllocMapped).  When the stream reaches the end of the call:

@@ -746,11 +746,13 @@ int mpm_search_async(mpm_handle* h, const uint8_t* T, size_t n, uint32_t* out_po
         }
     }
     // the closing sort on the side stream, after this scan: the rank sort
-    // up to kRankSortMax occurrences; with room for more in the outputs, the
-    // device-count radix sort after it (its kernels return at once when the
-    // rank sort had them all) and the kernel that closes the search
+    // up to kRankSortMax occurrences; with room for more in the outputs, a
+    // radix sort after it that reads the count on the device and returns at
+    // once when the rank sort had them all -- one block for outputs of up to
+    // kBlockSortCap, else the multi-block passes and the closing kernel
     const uint32_t rank_cap = (uint32_t)std::min<size_t>(cap, mpm::kRankSortMax);
     const bool radix = cap > mpm::kRankSortMax;
+    const bool one_block = cap <= mpm::kBlockSortCap;
     const uint32_t cand_lim = fused_search(h) ? 0xFFFFFFFFu : (uint32_t)cand_cap;
     uint64_t* tmp = nullptr;
     const uint32_t sort_cap = (uint32_t)std::min<size_t>(cap, occ_cap);
@@ -761,7 +763,8 @@ int mpm_search_async(mpm_handle* h, const uint8_t* T, size_t n, uint32_t* out_po
             if (grow(&h->d_occ1_tmp, &h->occ1_tmp_cap, occ_cap)) return set_error(MPM_ENOMEM);
             tmp = h->d_occ1_tmp;
         }
-        if (grow(&h->d_ahist[b], &h->ahist_cap[b], mpm::sort_dev_hist_entries(sort_cap)))
+        if (!one_block &&
+            grow(&h->d_ahist[b], &h->ahist_cap[b], mpm::sort_dev_hist_entries(sort_cap)))
             return set_error(MPM_ENOMEM);
     }
     if (cudaEventRecord(h->scan_done[b], s) != cudaSuccess ||
@@ -780,17 +783,28 @@ int mpm_search_async(mpm_handle* h, const uint8_t* T, size_t n, uint32_t* out_po
         const int pos_bits = bits_for(n);
         for (int v = 0; v < pid_bits; v += 8) shifts[ns++] = v;
         for (int v = 0; v < pos_bits; v += 8) shifts[ns++] = 32 + v;
-        uint64_t* sorted = nullptr;
-        const int l = mpm::launch_sort_dev(occ, tmp, h->d_ahist[b], sort_cap,
-                                           counters + mpm::kOccCount, shifts, ns, h->num_sms,
-                                           &sorted, h->side, mpm::kRankSortMax);
-        if (l < 0 || mpm::launch_close_sorted(sorted, counters, (uint32_t)cap, out_pos, out_pid,
-                                              dstatus, cand_lim, (uint32_t)occ_cap,
-                                              mpm::kRankSortMax, h->num_sms, h->side) < 0) {
+        int l;
+        if (one_block) {
+            l = mpm::launch_block_sort_close(occ, tmp, counters, (uint32_t)cap, out_pos, out_pid,
+                                             dstatus, cand_lim, (uint32_t)occ_cap, shifts, ns,
+                                             mpm::kRankSortMax, h->side);
+        } else {
+            uint64_t* sorted = nullptr;
+            l = mpm::launch_sort_dev(occ, tmp, h->d_ahist[b], sort_cap, counters + mpm::kOccCount,
+                                     shifts, ns, h->num_sms, &sorted, h->side,
+                                     mpm::kRankSortMax);
+            if (l >= 0)
+                l = mpm::launch_close_sorted(sorted, counters, (uint32_t)cap, out_pos, out_pid,
+                                             dstatus, cand_lim, (uint32_t)occ_cap,
+                                             mpm::kRankSortMax, h->num_sms, h->side) < 0
+                        ? -1
+                        : l + 1;
+        }
+        if (l < 0) {
             cudaGetLastError();
             return set_error(MPM_ECUDA);
         }
-        launches += l + 1;
+        launches += l;
     }
     if (cudaEventRecord(h->sort_done[b], h->side) != cudaSuccess) {
         cudaGetLastError();

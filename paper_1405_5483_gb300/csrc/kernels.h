@@ -127,6 +127,16 @@ size_t sort_dev_hist_entries(uint32_t cap);
 int launch_sort_dev(uint64_t* keys, uint64_t* tmp, uint32_t* hist, uint32_t cap,
                     const uint32_t* count, const int* shifts, int nshifts, int num_sms,
                     uint64_t** sorted, cudaStream_t s, uint32_t skip = 0);
+// Closes a pipelined search in one block (one launch): when from < count <=
+// min(out_cap, occ_cap) (and no error or candidate overflow), the keys are
+// radix-sorted over the digits at `shifts` (tmp holds as many keys) and split
+// into out_pos/out_pid; always, the counters go to the snapshot with the
+// completeness word and are zeroed.  For outputs of up to kBlockSortCap.
+constexpr uint32_t kBlockSortCap = 1u << 20;
+int launch_block_sort_close(uint64_t* keys, uint64_t* tmp, uint32_t* counters, uint32_t out_cap,
+                            uint32_t* out_pos, uint32_t* out_pid, uint32_t* snapshot,
+                            uint32_t cand_cap, uint32_t occ_cap, const int* shifts, int nshifts,
+                            uint32_t from, cudaStream_t s);
 // Closes a pipelined search after launch_sort_dev: when from < count <=
 // min(out_cap, occ_cap) the sorted keys are split into out_pos/out_pid;
 // always, the counters go to the snapshot (the fourth word 1 when the

@@ -79,6 +79,60 @@ __device__ __forceinline__ void tma_load_2d(unsigned int dst, const void* map, i
         : "memory");
 }
 
+// L2 cache policies (createpolicy): evict_first for data read once (a
+// streamed text), evict_last for data read again and again (a mask table
+// in global memory), so that the stream does not push the table out of L2.
+__device__ __forceinline__ unsigned long long l2_policy_evict_first() {
+    unsigned long long p;
+    asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
+    return p;
+}
+
+__device__ __forceinline__ unsigned long long l2_policy_evict_last() {
+    unsigned long long p;
+    asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p));
+    return p;
+}
+
+// 2-D tiled TMA load with an L2 cache policy.
+__device__ __forceinline__ void tma_load_2d_hint(unsigned int dst, const void* map, int x, int y,
+                                                 unsigned int bar, unsigned long long policy) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes"
+        ".L2::cache_hint [%0], [%1, {%2, %3}], [%4], %5;" ::"r"(dst),
+        "l"(reinterpret_cast<unsigned long long>(map)), "r"(x), "r"(y), "r"(bar), "l"(policy)
+        : "memory");
+}
+
+// Read-only global loads with an L2 cache policy.
+__device__ __forceinline__ unsigned int ldg_hint_u8(const unsigned char* p,
+                                                    unsigned long long policy) {
+    unsigned short v;
+    asm volatile("ld.global.nc.L2::cache_hint.u8 %0, [%1], %2;" : "=h"(v) : "l"(p), "l"(policy));
+    return v;
+}
+
+__device__ __forceinline__ unsigned int ldg_hint_u16(const unsigned short* p,
+                                                     unsigned long long policy) {
+    unsigned short v;
+    asm volatile("ld.global.nc.L2::cache_hint.u16 %0, [%1], %2;" : "=h"(v) : "l"(p), "l"(policy));
+    return v;
+}
+
+__device__ __forceinline__ unsigned int ldg_hint_u32(const unsigned int* p,
+                                                     unsigned long long policy) {
+    unsigned int v;
+    asm volatile("ld.global.nc.L2::cache_hint.u32 %0, [%1], %2;" : "=r"(v) : "l"(p), "l"(policy));
+    return v;
+}
+
+__device__ __forceinline__ unsigned long long ldg_hint_u64(const unsigned long long* p,
+                                                           unsigned long long policy) {
+    unsigned long long v;
+    asm volatile("ld.global.nc.L2::cache_hint.u64 %0, [%1], %2;" : "=l"(v) : "l"(p), "l"(policy));
+    return v;
+}
+
 __device__ __forceinline__ unsigned int lanemask_lt() {
     unsigned int m;
     asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));

@@ -170,11 +170,29 @@ __device__ __forceinline__ u32 code_at(const u32* w, const u32* rw, const u8* sm
     }
 }
 
+// Mask-table entry c: from shared memory, or from global memory with an
+// evict_last L2 policy (pol), so that the streamed text, loaded with
+// evict_first, does not push a table read at random out of L2.
+__device__ __forceinline__ DT entry(const ET* tab, u32 c, u64 pol) {
+#if MPM_SMEM || MPM_EB > 8
+    (void)pol;
+    return (DT)tab[c];
+#elif MPM_EB == 1
+    return (DT)ldg_hint_u8(reinterpret_cast<const u8*>(tab) + c, pol);
+#elif MPM_EB == 2
+    return (DT)ldg_hint_u16(reinterpret_cast<const u16*>(tab) + c, pol);
+#elif MPM_EB == 4
+    return (DT)ldg_hint_u32(reinterpret_cast<const u32*>(tab) + c, pol);
+#else
+    return (DT)ldg_hint_u64(reinterpret_cast<const u64*>(tab) + c, pol);
+#endif
+}
+
 // One stage of C bytes: the NS sampled q-grams fold into D; with REPORT the
 // report bits after each go into fm (k bits per sample).
 template <bool REPORT>
 __device__ __forceinline__ void run_stage(const u32* w, DT& D, FT& fm, const ET* tab,
-                                          const u8* smu) {
+                                          const u8* smu, u64 pol) {
     u32 rw[C / 4];
     if (MPM_MODE == 0) {
 #pragma unroll
@@ -183,7 +201,7 @@ __device__ __forceinline__ void run_stage(const u32* w, DT& D, FT& fm, const ET*
 #pragma unroll
     for (int u = 0; u < NS; u++) {
         const u32 c = code_at(w, rw, smu, u * P + (K - 1) * Q);
-        D = (D << K) | (DT)tab[c];
+        D = (D << K) | entry(tab, c, pol);
         if (REPORT) fm |= ((FT)(~bits_at(D, RSH) & KMASK)) << (u * K);
     }
 }
@@ -194,11 +212,11 @@ __device__ __forceinline__ void run_stage(const u32* w, DT& D, FT& fm, const ET*
 // Every D is ANDed into acc, so a zero report bit of acc means that some
 // sample of the stage fired.
 __device__ __forceinline__ void run_stage_ov(const u32* x, const u32* rx, DT& D, DT& acc,
-                                             const ET* tab, const u8* smu) {
+                                             const ET* tab, const u8* smu, u64 pol) {
 #pragma unroll
     for (int u = 0; u < NS; u++) {
         const u32 c = code_at(x, rx, smu, TW * 4 + E0 - (Q - 1) + u * K);
-        D = (D << K) | (DT)tab[c];
+        D = (D << K) | entry(tab, c, pol);
         acc &= D;
     }
 }
@@ -207,13 +225,13 @@ __device__ __forceinline__ void run_stage_ov(const u32* x, const u32* rx, DT& D,
 // u / SPW of fm, bits (u % SPW) k ..; hs0 = h - (m'-1)k of sample 0 (h its
 // start byte): a window h - (m'-1)k - j before the text start is dropped.
 __device__ __forceinline__ void fired_stage_ov(const u32* x, const u32* rx, DT D, FT* fm,
-                                               i64 hs0, const ET* tab, const u8* smu) {
+                                               i64 hs0, const ET* tab, const u8* smu, u64 pol) {
 #pragma unroll
     for (int w = 0; w < FW; w++) fm[w] = 0;
 #pragma unroll
     for (int u = 0; u < NS; u++) {
         const u32 c = code_at(x, rx, smu, TW * 4 + E0 - (Q - 1) + u * K);
-        D = (D << K) | (DT)tab[c];
+        D = (D << K) | entry(tab, c, pol);
         u32 f = ~bits_at(D, RSH) & KMASK;
         const i64 hs = hs0 + (i64)u * K;
         if (hs < K - 1) f &= hs < 0 ? 0u : ((1u << (u32)(hs + 1)) - 1u);
@@ -355,6 +373,9 @@ extern "C" __global__ void __launch_bounds__(MPM_WARPS * 32, 1)
     __syncthreads();
     const ET* tab = MPM_SMEM ? reinterpret_cast<const ET*>(s_tab)
                              : reinterpret_cast<const ET*>(A.table);
+    // a table in global memory is kept in L2 ahead of the text stream
+    const u64 tpol = MPM_SMEM ? 0ull : l2_policy_evict_last();
+    const u64 spol = MPM_SMEM ? 0ull : l2_policy_evict_first();
     const u32 gw = blockIdx.x * WARPS + warp;
     const u32 GW = gridDim.x * WARPS;
 
@@ -370,8 +391,12 @@ extern "C" __global__ void __launch_bounds__(MPM_WARPS * 32, 1)
                 // the test hook expects 16 bytes more than the copy brings:
                 // the phase never completes and the bounded wait gives up
                 mbar_arrive_expect_tx(bar, SLOT + ((A.inject & 1u) && gw == 0 && i == 0 ? 16u : 0u));
-                tma_load_2d(smem_addr(stage + i * SLOT), &tmap, (int)((i % nst) * C),
-                            (int)((gw + (i / nst) * RW) * 32), bar);
+                if (MPM_SMEM)
+                    tma_load_2d(smem_addr(stage + i * SLOT), &tmap, (int)((i % nst) * C),
+                                (int)((gw + (i / nst) * RW) * 32), bar);
+                else
+                    tma_load_2d_hint(smem_addr(stage + i * SLOT), &tmap, (int)((i % nst) * C),
+                                     (int)((gw + (i / nst) * RW) * 32), bar, spol);
             }
         }
         __syncwarp();
@@ -410,7 +435,7 @@ extern "C" __global__ void __launch_bounds__(MPM_WARPS * 32, 1)
                         for (int i = TW; i < TW + C / 4; i++) rx[i] = pack_word(x[i]);
                     }
                     DT acc = ~(DT)0;
-                    run_stage_ov(x, rx, D, acc, tab, s_mu);
+                    run_stage_ov(x, rx, D, acc, tab, s_mu, tpol);
 #pragma unroll
                     for (int i = 0; i < TW; i++) {
                         x[i] = x[C / 4 + i];
@@ -434,7 +459,7 @@ extern "C" __global__ void __launch_bounds__(MPM_WARPS * 32, 1)
                         w[4 * i + 2] = v.z;
                         w[4 * i + 3] = v.w;
                     }
-                    run_stage<false>(w, D, fm, tab, s_mu);
+                    run_stage<false>(w, D, fm, tab, s_mu, tpol);
                 }
             }
             const u32 h_row = row_start / (u32)Q;
@@ -468,7 +493,7 @@ extern "C" __global__ void __launch_bounds__(MPM_WARPS * 32, 1)
                 }
                 const DT D0 = D;
                 DT acc = ~(DT)0;
-                run_stage_ov(x, rx, D, acc, tab, s_mu);
+                run_stage_ov(x, rx, D, acc, tab, s_mu, tpol);
 #else
                 u32 w[C / 4];
 #pragma unroll
@@ -480,7 +505,7 @@ extern "C" __global__ void __launch_bounds__(MPM_WARPS * 32, 1)
                     w[4 * i + 3] = v.w;
                 }
                 fm = 0;
-                run_stage<true>(w, D, fm, tab, s_mu);
+                run_stage<true>(w, D, fm, tab, s_mu, tpol);
 #endif
                 // the slot's words are consumed: refill it
                 __syncwarp();
@@ -488,8 +513,13 @@ extern "C" __global__ void __launch_bounds__(MPM_WARPS * 32, 1)
                     const u32 j = it + S;
                     const u32 bar = smem_addr(&bars[slot]);
                     mbar_arrive_expect_tx(bar, SLOT);
-                    tma_load_2d(smem_addr(stage + slot * SLOT), &tmap, (int)((j % nst) * C),
-                                (int)((gw + (j / nst) * RW) * 32), bar);
+                    if (MPM_SMEM)
+                        tma_load_2d(smem_addr(stage + slot * SLOT), &tmap, (int)((j % nst) * C),
+                                    (int)((gw + (j / nst) * RW) * 32), bar);
+                    else
+                        tma_load_2d_hint(smem_addr(stage + slot * SLOT), &tmap,
+                                         (int)((j % nst) * C), (int)((gw + (j / nst) * RW) * 32),
+                                         bar, spol);
                 }
 #if MPM_OV
                 const bool any = valid && ((~bits_at(acc, RSH) & KMASK) != 0u);
@@ -497,7 +527,7 @@ extern "C" __global__ void __launch_bounds__(MPM_WARPS * 32, 1)
                     // some lane fired: which samples, from the saved D
                     const i64 h1 = (i64)row_start + (i64)st * C + (E0 - (Q - 1));
                     FT fmw[FW];
-                    fired_stage_ov(x, rx, D0, fmw, h1 - RSH, tab, s_mu);
+                    fired_stage_ov(x, rx, D0, fmw, h1 - RSH, tab, s_mu, tpol);
 #pragma unroll
                     for (int w = 0; w < FW; w++) {
                         const FT f = valid ? fmw[w] : (FT)0;
@@ -536,11 +566,11 @@ extern "C" __global__ void __launch_bounds__(MPM_WARPS * 32, 1)
         for (int t = MP - 1; t >= 1; t--) {
             const i64 hw = h - (i64)t * K;
             if (hw < 0) continue;
-            D = (D << K) | (DT)tab[code_bytes(A.T, (u32)hw, s_mu)];
+            D = (D << K) | entry(tab, code_bytes(A.T, (u32)hw, s_mu), tpol);
         }
         for (; h + Q <= (i64)b; h += K) {
             if (h < 0) continue;
-            D = (D << K) | (DT)tab[code_bytes(A.T, (u32)h, s_mu)];
+            D = (D << K) | entry(tab, code_bytes(A.T, (u32)h, s_mu), tpol);
             const u32 fired = ~bits_at(D, RSH) & KMASK;
             if (fired) {
                 // rare: handled by the lane alone
@@ -559,11 +589,11 @@ extern "C" __global__ void __launch_bounds__(MPM_WARPS * 32, 1)
         for (int j = MP - 2; j >= 0; j--) {
             const i64 e = (i64)a - (i64)j * P;
             if (e - Q < 0) continue;
-            D = (D << K) | (DT)tab[code_bytes(A.T, (u32)(e - Q), s_mu)];
+            D = (D << K) | entry(tab, code_bytes(A.T, (u32)(e - Q), s_mu), tpol);
         }
         for (u32 e = a + P; e <= b; e += P) {
             const u32 st = e - Q;
-            D = (D << K) | (DT)tab[code_bytes(A.T, st, s_mu)];
+            D = (D << K) | entry(tab, code_bytes(A.T, st, s_mu), tpol);
             const u32 fired = ~bits_at(D, RSH) & KMASK;
             if (fired) {
                 // rare: handled by the lane alone

@@ -364,7 +364,124 @@ __global__ void __launch_bounds__(256)
     }
 }
 
+// The whole close of a pipelined search with more than `from` occurrences
+// in one block: an LSD radix sort of the keys over the digits at `sh`
+// (ping-pong between keys and tmp in global memory; warp w owns the w-th
+// contiguous chunk of the keys, so ranks by (warp, lane) are stable), the
+// split into the outputs, and the counters copied to the snapshot and
+// zeroed.  One launch whatever the count, so a search with few occurrences
+// pays one kernel that returns at once.
+constexpr int kBlockSortThreads = 256;
+constexpr int kBlockSortWarps = kBlockSortThreads / 32;
+
+struct DigitShifts {
+    int v[8];
+    int n;
+};
+
+__global__ void __launch_bounds__(kBlockSortThreads)
+    block_sort_close_kernel(uint64_t* keys, uint64_t* tmp, uint32_t* counters, uint32_t out_cap,
+                            uint32_t* out_pos, uint32_t* out_pid, uint32_t* snapshot,
+                            uint32_t cand_cap, uint32_t occ_cap, DigitShifts sh, uint32_t from) {
+    static_assert(kBlockSortThreads == 256, "one thread per digit");
+    __shared__ uint32_t cnt[kBlockSortWarps][256];
+    __shared__ uint32_t s_tot[256];
+    __shared__ uint32_t s_c[3];
+    if (threadIdx.x == 0) {
+        volatile uint32_t* c = counters;
+        s_c[0] = c[kCandCount];
+        s_c[1] = c[kOccCount];
+        s_c[2] = c[kErrorFlag];
+    }
+    __syncthreads();
+    const uint32_t cand = s_c[0], z = s_c[1], err = s_c[2];
+    const bool complete = err == 0 && z <= out_cap && z <= occ_cap && cand <= cand_cap;
+    if (threadIdx.x == 0) {
+        snapshot[kCandCount] = cand;
+        snapshot[kOccCount] = z;
+        snapshot[kErrorFlag] = err;
+        snapshot[kDoneCount] = complete ? 1u : 0u;
+        for (int i = 0; i < kNumCounters; i++) counters[i] = 0;
+    }
+    if (!complete || z <= from) return;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const uint32_t span = ((z + kBlockSortWarps - 1) / kBlockSortWarps + 31) & ~31u;
+    const uint32_t a = min(z, (uint32_t)warp * span), b = min(z, a + span);
+    uint64_t* src = keys;
+    uint64_t* dst = tmp;
+    for (int p = 0; p < sh.n; p++) {
+        const int shift = sh.v[p];
+        for (int i = threadIdx.x; i < kBlockSortWarps * 256; i += blockDim.x) (&cnt[0][0])[i] = 0;
+        __syncthreads();
+        for (uint32_t c = a; c < b; c += 32) {
+            const uint32_t i = c + lane;
+            const bool live = i < b;
+            const uint32_t d = live ? (uint32_t)((src[i] >> shift) & 0xFF) : 256u + lane;
+            const uint32_t peers = __match_any_sync(0xFFFFFFFFu, d);
+            if (live && lane == __ffs(peers) - 1) cnt[warp][d] += __popc(peers);
+            __syncwarp();
+        }
+        __syncthreads();
+        // start of every (digit, warp): the digits before it, then the
+        // earlier warps' keys of the same digit (thread d takes digit d)
+        {
+            const int d = threadIdx.x;
+            uint32_t tot = 0;
+            for (int w = 0; w < kBlockSortWarps; w++) tot += cnt[w][d];
+            s_tot[d] = tot;
+            __syncthreads();
+            for (int o = 1; o < 256; o <<= 1) {  // inclusive scan of the totals
+                const uint32_t v = d >= o ? s_tot[d - o] : 0u;
+                __syncthreads();
+                s_tot[d] += v;
+                __syncthreads();
+            }
+            uint32_t run = s_tot[d] - tot;
+            for (int w = 0; w < kBlockSortWarps; w++) {
+                const uint32_t c = cnt[w][d];
+                cnt[w][d] = run;
+                run += c;
+            }
+        }
+        __syncthreads();
+        for (uint32_t c = a; c < b; c += 32) {
+            const uint32_t i = c + lane;
+            const bool live = i < b;
+            const uint64_t key = live ? src[i] : 0;
+            const uint32_t d = live ? (uint32_t)((key >> shift) & 0xFF) : 256u + lane;
+            const uint32_t peers = __match_any_sync(0xFFFFFFFFu, d);
+            if (live) dst[cnt[warp][d] + __popc(peers & lanemask_lt())] = key;
+            __syncwarp();
+            if (live && lane == __ffs(peers) - 1) cnt[warp][d] += __popc(peers);
+            __syncwarp();
+        }
+        __syncthreads();
+        uint64_t* t = src;
+        src = dst;
+        dst = t;
+    }
+    for (uint32_t i = threadIdx.x; i < z; i += blockDim.x) {
+        const uint64_t k = src[i];
+        out_pos[i] = (uint32_t)(k >> 32);
+        out_pid[i] = (uint32_t)k;
+    }
+}
+
 }  // namespace
+
+int launch_block_sort_close(uint64_t* keys, uint64_t* tmp, uint32_t* counters, uint32_t out_cap,
+                            uint32_t* out_pos, uint32_t* out_pid, uint32_t* snapshot,
+                            uint32_t cand_cap, uint32_t occ_cap, const int* shifts, int nshifts,
+                            uint32_t from, cudaStream_t s) {
+    if (nshifts < 0 || nshifts > 8) return -1;
+    DigitShifts sh{};
+    for (int i = 0; i < nshifts; i++) sh.v[i] = shifts[i];
+    sh.n = nshifts;
+    block_sort_close_kernel<<<1, kBlockSortThreads, 0, s>>>(keys, tmp, counters, out_cap, out_pos,
+                                                            out_pid, snapshot, cand_cap, occ_cap,
+                                                            sh, from);
+    return cudaPeekAtLastError() == cudaSuccess ? 1 : -1;
+}
 
 int launch_close_sorted(const uint64_t* sorted, uint32_t* counters, uint32_t out_cap,
                         uint32_t* out_pos, uint32_t* out_pid, uint32_t* snapshot,

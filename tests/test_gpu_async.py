@@ -178,13 +178,15 @@ def test_join_orders_later_stream_work_and_stream_switches(mpm, native):
     assert np.all(status.cpu().numpy()[:, 3] == 1)
 
 
+@pytest.mark.parametrize("cap", [1 << 17, (1 << 20) + 64], ids=["one-block", "multi-block"])
 @pytest.mark.parametrize("z_target", [4095, 4097, 9000, 70_000])
-def test_pipelined_large_counts_through_both_buffer_sets(mpm, native, z_target):
+def test_pipelined_large_counts_through_both_buffer_sets(mpm, native, z_target, cap):
     """Counts on both sides of the rank sort's 4096, several searches in a
     row (both internal buffer sets, the closing sorts overlapping the next
-    scans), each against the oracle; the occurrence buffer's first size
-    (65 536) is exceeded by the last count, which the synchronous search
-    then grows for the pipelined calls after it."""
+    scans), each against the oracle, with the one-block and the multi-block
+    closing sorts; the occurrence buffer's first size (65 536) is exceeded
+    by the last count, which the synchronous search then grows for the
+    pipelined calls after it."""
     rng = np.random.default_rng(z_target)
     n = 1 << 22
     T = (rng.integers(0, 4, n) + 65).astype(np.uint8)
@@ -196,7 +198,6 @@ def test_pipelined_large_counts_through_both_buffer_sets(mpm, native, z_target):
     z = want[0].size
     Td = torch.from_numpy(T).cuda()
     m = mpm.Matcher(P, sigma=4)
-    cap = 1 << 17
     outs = [(torch.full((cap,), -1, dtype=torch.int32, device="cuda"),
              torch.full((cap,), -1, dtype=torch.int32, device="cuda")) for _ in range(3)]
     status = torch.zeros((3, 4), dtype=torch.int32, device="cuda")

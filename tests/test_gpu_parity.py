@@ -296,12 +296,12 @@ def test_full_size_dna_scaled(mpm, native):
     assert z >= 50
 
 
-def _pipelined_equals(mpm, native, T, P, sigma, params, searches=3):
+def _pipelined_equals(mpm, native, T, P, sigma, params, searches=3, want=None, Td=None):
     """The benchmark's timed form: searches issued back to back with
     mpm_search_async on one handle, each writing its own status row and
     output buffers, then checked against the oracle."""
     m = mpm.Matcher(P, sigma=sigma, **params)
-    Td = dev(T)
+    Td = dev(T) if Td is None else Td
     cap = max(1 << 16, 8 * P.shape[0])
     outs = [(torch.empty(cap, dtype=torch.int32, device="cuda"),
              torch.empty(cap, dtype=torch.int32, device="cuda")) for _ in range(searches)]
@@ -309,7 +309,7 @@ def _pipelined_equals(mpm, native, T, P, sigma, params, searches=3):
     for i in range(searches):
         m.search_async(Td, outs[i][0], outs[i][1], status[i])
     m.sync()
-    wp, wi = native.aho_corasick(T, P, threads=_threads())
+    wp, wi = want if want is not None else native.aho_corasick(T, P, threads=_threads())
     rows = status.cpu().numpy()
     assert np.all(rows[:, 3] == 1) and np.all(rows[:, 2] == 0), rows
     assert np.all(rows[:, 1] == wp.size), (rows, wp.size)
@@ -341,10 +341,18 @@ def test_full_size_dna_in_the_benchmarked_configuration(mpm, native):
 @pytest.mark.parametrize("r,mlen", [(100_000, 32), (10_000, 16), (10_000, 64)])
 def test_full_size_dna_large_sets(mpm, native, r, mlen):
     c = W.config3(r=r, m=mlen)
-    m, z = check_search(mpm, native, c.T, c.P, 4)
+    Td = dev(c.T)
+    m, z = check_search(mpm, native, c.T, c.P, 4, T_dev=Td)
     # every planted pattern occurs at its planting offset
-    pos_set = z
-    assert pos_set >= r // 10
+    assert z >= r // 10
+    want = native.aho_corasick(c.T, c.P, threads=_threads())
+    # the pipelined form the benchmark times (more than 4096 occurrences for
+    # r = 100 000: closed by the radix sort), with the planner's parameters
+    # and with the overlapping-q-gram filter
+    _pipelined_equals(mpm, native, c.T, c.P, 4, {}, want=want, Td=Td)
+    _pipelined_equals(mpm, native, c.T, c.P, 4,
+                      dict(q=8 if mlen == 16 else 12, sigma_r=4, k=2, map_kind=3, overlap=1),
+                      want=want, Td=Td)
 
 
 def test_autotune_picks_a_set_that_is_exact(mpm, native):
