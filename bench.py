@@ -356,8 +356,17 @@ def run_batch(args, rank, steps=None, fast=False):
     # mask tables that the batched kernel keeps in shared memory
     learned = CM.learned_batch_params(b, model, mpm_native.BATCH_SMEM_TABLE_BYTES)
     learn_s = time.perf_counter() - t0
+    # the same parameters through the precompiled kernel (run-time q, k and
+    # mapping), for comparison with the kernel compiled for the batch
+    BG = mpm.Batch([CM.batch_matcher(P, b.sigma, p) for P, p in zip(b.sets, learned)],
+                   texts, b.set_of_text, generic=True)
+    exact_generic = bool(np.array_equal(result(BG), want))
+    generic_ms = timed(BG, "batch_generic")
+    BG.close()
+    t0 = time.perf_counter()
     BL = build(learned)
-    exact_learned = bool(np.array_equal(result(BL), want))
+    compile_s = time.perf_counter() - t0
+    exact_learned = bool(np.array_equal(result(BL), want)) and exact_generic
     with ClockSampler(dev.index) as clk:
         learned_ms = timed(BL, "batch_timed")
     st = BL.stats
@@ -428,18 +437,20 @@ def run_batch(args, rank, steps=None, fast=False):
         cpu = {"value": o.total / dt / 1e9, "unit": "GB/s", "cores": o.threads,
                "kind": "oracle", "sample": o.describe() + " (%.2f s, %d occurrences)" % (dt, oz)}
         o.close()
-    # the dominant kernel (batch_scan_kernel): algorithmic bytes per launch =
-    # every text byte once (candidate records stay in shared memory; the
-    # occurrence records it writes are a few hundred KB)
+    # the dominant kernel (mpm_batch_jit, the kernel compiled for the batch,
+    # or batch_scan_kernel when it could not be): algorithmic bytes per
+    # launch = every text byte once (candidate records stay in shared memory;
+    # the occurrence records it writes are a few hundred KB)
     achieved = total / (scan_ms * 1e-3) / 1e9 if scan_ms > 0 else None
+    kname = "mpm_batch_jit" if st["variants"] else "batch_scan_kernel"
     line = {
         "metric": METRIC, "value": value, "unit": "GB/s", "n_gpus": 1, "steps": steps,
         "warmup": max(3, args.warmup), "ms_per_step": learned_ms, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "u8", "data": "synthetic",
         "config": {"workload": "batch-4096", "texts": len(texts), "sets": len(b.sets),
-                   "bytes": total, "form": "batched (one persistent launch, CUDA graph), "
-                   "parameters per set from the learned cost model (mask tables that fit "
-                   "shared memory)",
+                   "bytes": total, "form": "batched (one persistent launch, CUDA graph) of the "
+                   "kernel compiled for the batch's %d parameter sets, parameters per set from "
+                   "the learned cost model (mask tables that fit shared memory)" % st["variants"],
                    "l2": "inputs larger than L2 (no flush)"},
         "hbm_frac_of_%s_peak" % peak_kind: value / peak,
         "plain_per_request": {"value": total / (plain_ms * 1e-3) / 1e9, "unit": "GB/s",
@@ -451,6 +462,10 @@ def run_batch(args, rank, steps=None, fast=False):
                           "ms_per_step": tuned_ms,
                           "form": "batched, parameters from the exhaustive autotuner "
                                   "(batched kernel timed on 16 MiB of each set's texts)"},
+        "batched_precompiled_kernel": {"value": total / (generic_ms * 1e-3) / 1e9, "unit": "GB/s",
+                                       "ms_per_step": generic_ms,
+                                       "form": "the learned parameters through the precompiled "
+                                               "batched kernel (run-time q, k and mapping)"},
         "batched_over_plain": plain_ms / learned_ms,
         "learned_over_tuned": tuned_ms / learned_ms,
         "bit_exact_vs_plain": exact_learned and exact_tuned, "occurrences": int(st["z"]),
@@ -458,17 +473,16 @@ def run_batch(args, rank, steps=None, fast=False):
         "gpu_launches": launches,
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak if achieved else None,
-                     "traffic": recorded_traffic("batch-4096", {}, "batch_scan_kernel",
-                                                 batch_kernel_rev()),
-                     "kernel": "batch_scan_kernel", "peak_kind": peak_kind,
-                     "scan_ms": scan_ms,
-                     "note": "issue-bound (integer ALU and latency), not HBM-bound"},
+                     "traffic": recorded_traffic("batch-4096", {}, kname,
+                                                 batch_kernel_rev(kname)),
+                     "kernel": kname, "peak_kind": peak_kind, "scan_ms": scan_ms},
         "e2e": {"value": total * e2e_steps / e2e_s / 1e9, "unit": "GB/s",
                 "h2d_bytes_per_step": int(flat.size),
                 "d2h_bytes_per_step": 16 + 12 * e2e_z},
         "clocks": clk.summary(),
         "cpu_baseline": cpu,
         "setup_seconds": {"generate": round(gen_s, 1), "learned_choice": round(learn_s, 1),
+                          "compile_batch_kernel": round(compile_s, 1),
                           "tune": round(tune_s, 1), "tune_plain": round(plain_tune_s, 1)},
     }
     for mm in plain:
@@ -744,6 +758,7 @@ def summary_of(line):
             "hbm_frac_of_fallback_peak", "form", "occurrences", "candidates_per_step",
             "roofline", "sync_per_call", "plain_per_request", "batched_tuned",
             "batched_over_plain", "learned_over_tuned", "bit_exact_vs_plain", "clocks",
+            "batched_precompiled_kernel",
             "gpu_launches", "setup_seconds")
     out = {k: line[k] for k in keep if k in line}
     out["config"] = line.get("config")
@@ -850,13 +865,18 @@ def source_rev(files):
 def kernel_rev():
     """The specialised scan kernel's source and launch geometry."""
     return source_rev(("keyhash.h", "multiword.h", "scan_jit_args.h", "ptx_common.cuh",
-                       "window_check.cuh", "scan_jit.cuh", "jit.cpp"))
+                       "window_check.cuh", "jit_types.h", "scan_stage.cuh", "scan_jit.cuh",
+                       "jit.cpp"))
 
 
-def batch_kernel_rev():
-    """The batched kernel's source and its host side (units, launch)."""
-    return source_rev(("batch.cu", "stepper.cuh", "multiword.h", "device_common.cuh",
-                       "window_check.cuh", "keyhash.h"))
+def batch_kernel_rev(kernel="batch_scan_kernel"):
+    """A batched kernel's source and its host side (units, launch)."""
+    if kernel == "mpm_batch_jit":
+        return source_rev(("batch.cu", "batch_args.h", "batch_lane.cuh", "batch_jit.cuh",
+                           "scan_stage.cuh", "jit_types.h", "jit.cpp", "window_check.cuh",
+                           "keyhash.h", "ptx_common.cuh", "multiword.h"))
+    return source_rev(("batch.cu", "batch_args.h", "stepper.cuh", "multiword.h",
+                       "device_common.cuh", "window_check.cuh", "keyhash.h"))
 
 
 def recorded_traffic(workload, params, profile="mpm_scan_jit", rev=None):

@@ -353,6 +353,10 @@ typedef struct {
     int no_graph;    /* 1: launch the kernels on every run instead of a graph */
     int unit_kib;    /* estimated cost of a work unit, in KiB of scanned text
                         (verification counted as extra bytes); 0 = 2048 */
+    int generic;     /* 0: the kernel compiled (NVRTC, sm_103a) at create time
+                        for the batch's parameter sets, the precompiled one when
+                        that is not possible; 1: the precompiled kernel, whose
+                        q, k and mapping are run-time values */
 } mpm_batch_opts;
 
 typedef struct {
@@ -366,6 +370,9 @@ typedef struct {
     float scan_ms;        /* device time of the last run's scan kernel alone
                              (event records on either side of it, kept as
                              nodes of the graph); 0 when unavailable          */
+    uint32_t variants;    /* parameter sets the batch's compiled kernel
+                             specialises; 0: the precompiled kernel runs      */
+    uint32_t pad;
 } mpm_batch_stats;
 
 mpm_batch *mpm_batch_create(mpm_handle *const *sets, int nsets, const uint8_t *const *texts,
@@ -374,6 +381,16 @@ mpm_batch *mpm_batch_create(mpm_handle *const *sets, int nsets, const uint8_t *c
 int mpm_batch_run(mpm_batch *b, uint32_t *out_tid, uint32_t *out_pos, uint32_t *out_pid,
                   size_t *z);
 int mpm_batch_get_stats(const mpm_batch *b, mpm_batch_stats *out);
+/* Host-only: compiles (NVRTC, sm_103a) the batched kernel that
+ * mpm_batch_create would compile for nsets pattern sets -- set i being the
+ * r[i] x m[i] patterns P[i] over sigma[i] symbols with parameters params[i]
+ * (params may be NULL: automatic) -- without loading it; the compiler's
+ * messages go to log (log_bytes, may be NULL).  MPM_ENOTSUP for a set the
+ * batched form does not take (more than 32 positions, overlapping q-grams,
+ * hashed q-grams of more than 5 bytes) or when NVRTC is missing. */
+int mpm_batch_jit_compile(const uint8_t *const *P, const size_t *r, const size_t *m,
+                          const int *sigma, const mpm_params *params, int nsets, char *log,
+                          size_t log_bytes);
 void mpm_batch_free(mpm_batch *b);
 int mpm_search_batch(mpm_handle *const *sets, int nsets, const uint8_t *const *texts,
                      const size_t *lens, const uint32_t *set_of_text, int ntexts,
@@ -386,10 +403,10 @@ typedef struct {
     int max_k;           /* largest k tried; 0 = 8                                  */
     int reps;            /* timed searches per parameter set (median); 0 = 3       */
     int kernels;         /* bit 0 specialised, bit 1 split, bit 2 generic (timed
-                            through mpm_search), bit 3 the batched kernel (one
-                            mpm_batch over copies of the sample, at least 128 MiB
-                            and at most 256 copies, sets of <= 32 positions);
-                            0 = 1                                                  */
+                            through mpm_search), bit 3 the precompiled batched
+                            kernel (one mpm_batch with generic = 1 over copies of
+                            the sample, at least 128 MiB and at most 256 copies,
+                            sets of <= 32 positions); 0 = 1                        */
     int max_sets;        /* at most this many sets are timed, lowest estimated
                             candidate rate first; 0 = 64                            */
     double max_rate;     /* sets whose estimated candidate records per sampled

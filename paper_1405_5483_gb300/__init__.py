@@ -17,8 +17,8 @@ from ._native import (KERNEL_AUTO, KERNEL_GENERIC, KERNEL_SPECIALISED, KERNEL_SP
                       MPM_ENOTSUP, MPM_OK, TABLE_AUTO, TABLE_GLOBAL, TABLE_SMEM, MpmError,
                       Params, Stats, TableInfo, declared_functions, lib)
 
-__all__ = ["Matcher", "plan", "host_tables", "autotune", "jit_compile", "MpmError", "lib",
-           "declared_functions"]
+__all__ = ["Matcher", "Batch", "plan", "host_tables", "autotune", "jit_compile",
+           "batch_jit_compile", "MpmError", "lib", "declared_functions"]
 
 
 def _torch():
@@ -39,6 +39,22 @@ def jit_compile(P, sigma, **kw):
     buf = ctypes.create_string_buffer(1 << 16)
     rc = lib().mpm_jit_compile(P.ctypes.data, P.shape[0], P.shape[1], sigma,
                                ctypes.byref(make_params(**kw)), buf, len(buf))
+    return rc, buf.value.decode(errors="replace")
+
+
+def batch_jit_compile(sets, sigmas, params=None):
+    """Host-only: compiles the batched kernel that a Batch of these pattern
+    sets (uint8 (r, m) arrays) with these parameters (dicts, or None for
+    automatic) would run; returns (code, compiler log)."""
+    sets = [_patterns(P) for P in sets]
+    n = len(sets)
+    ptrs = (ctypes.c_void_p * n)(*[P.ctypes.data for P in sets])
+    rs = (ctypes.c_size_t * n)(*[P.shape[0] for P in sets])
+    ms = (ctypes.c_size_t * n)(*[P.shape[1] for P in sets])
+    sg = (ctypes.c_int * n)(*sigmas)
+    ps = (Params * n)(*[make_params(**(params[i] if params else {})) for i in range(n)])
+    buf = ctypes.create_string_buffer(1 << 16)
+    rc = lib().mpm_batch_jit_compile(ptrs, rs, ms, sg, ps, n, buf, len(buf))
     return rc, buf.value.decode(errors="replace")
 
 
@@ -289,7 +305,10 @@ class Batch:
     """Many texts (CUDA uint8 tensors), each against one of several Matchers,
     in one persistent launch replayed from a CUDA graph (mpm_batch_*)."""
 
-    def __init__(self, matchers, texts, set_of_text, lane_bytes=0, graph=True, unit_kib=0):
+    def __init__(self, matchers, texts, set_of_text, lane_bytes=0, graph=True, unit_kib=0,
+                 generic=False):
+        """generic=True: the precompiled batched kernel instead of the one
+        compiled for the batch's parameter sets."""
         from ._native import BatchOpts
         self._keep = (list(matchers), list(texts))
         n = len(texts)
@@ -297,7 +316,7 @@ class Batch:
         tp = (ctypes.c_void_p * n)(*[t.data_ptr() for t in texts])
         ln = (ctypes.c_size_t * n)(*[t.numel() for t in texts])
         st = (ctypes.c_uint32 * n)(*[int(s) for s in set_of_text])
-        opts = BatchOpts(lane_bytes, 0 if graph else 1, unit_kib)
+        opts = BatchOpts(lane_bytes, 0 if graph else 1, unit_kib, 1 if generic else 0)
         self._b = lib().mpm_batch_create(hs, len(matchers), tp, ln, st, n, ctypes.byref(opts))
         if not self._b:
             raise MpmError(lib().mpm_last_error(), "mpm_batch_create")

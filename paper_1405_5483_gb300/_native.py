@@ -80,14 +80,15 @@ class TuneEntry(ctypes.Structure):
 
 class BatchOpts(ctypes.Structure):
     _fields_ = [("lane_bytes", ctypes.c_int), ("no_graph", ctypes.c_int),
-                ("unit_kib", ctypes.c_int)]
+                ("unit_kib", ctypes.c_int), ("generic", ctypes.c_int)]
 
 
 class BatchStats(ctypes.Structure):
     _fields_ = [("bytes", ctypes.c_uint64), ("candidates", ctypes.c_uint64),
                 ("z", ctypes.c_uint64), ("tiles", ctypes.c_uint32),
                 ("launches", ctypes.c_uint32), ("ms", ctypes.c_float),
-                ("scan_ms", ctypes.c_float)]
+                ("scan_ms", ctypes.c_float), ("variants", ctypes.c_uint32),
+                ("pad", ctypes.c_uint32)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}
@@ -154,6 +155,9 @@ def lib():
                                             ctypes.POINTER(ctypes.c_uint32), ctypes.c_int,
                                             vp, vp, vp, szp]),
         "mpm_jit_compile": (ctypes.c_int, [u8p, sz, sz, ctypes.c_int, Pp, ctypes.c_char_p, sz]),
+        "mpm_batch_jit_compile": (ctypes.c_int, [ctypes.POINTER(vp), szp, szp,
+                                                 ctypes.POINTER(ctypes.c_int), Pp, ctypes.c_int,
+                                                 ctypes.c_char_p, sz]),
         "mpm_autotune": (ctypes.c_int, [u8p, sz, sz, ctypes.c_int, u8p, sz,
                                         ctypes.POINTER(TuneOpts), Pp, ctypes.POINTER(TuneEntry),
                                         sz, szp]),

@@ -20,10 +20,23 @@ LIB = os.path.join(OUT, "libmpm.so")
 
 SOURCES = ["host_build.cpp", "capi.cu", "scan.cu", "encode.cu", "verify.cu", "sort.cu", "jit.cpp",
            "tune.cpp", "batch.cu", "mlp.cu"]
-# files concatenated, in this order, into the source of the scan kernel that
-# is compiled at run time
-JIT_PARTS = ["keyhash.h", "multiword.h", "scan_jit_args.h", "ptx_common.cuh",
-             "window_check.cuh", "scan_jit.cuh"]
+# sources of the kernels compiled at run time, embedded as C++ raw strings:
+# each generated file is the concatenation of its parts (file names, or
+# literal text)
+_NS_OPEN, _NS_CLOSE = "namespace mpm {\n", "}  // namespace mpm\n"
+JIT_SOURCES = {
+    # the single-text specialised scan
+    "scan_jit_src.inc": ["keyhash.h", "multiword.h", "scan_jit_args.h", "ptx_common.cuh",
+                         "window_check.cuh", "jit_types.h", _NS_OPEN, "scan_stage.cuh",
+                         _NS_CLOSE, "scan_jit.cuh"],
+    # the batched kernel: prelude, the stage primitives and the lane scan
+    # (once per parameter set of a batch), the kernel
+    "batch_prelude_src.inc": ["keyhash.h", "multiword.h", "ptx_common.cuh", "window_check.cuh",
+                              "jit_types.h", "batch_args.h"],
+    "batch_stage_src.inc": ["scan_stage.cuh", "batch_lane.cuh"],
+    "batch_kernel_src.inc": ["batch_jit.cuh"],
+}
+JIT_PARTS = sorted({p for parts in JIT_SOURCES.values() for p in parts if p.endswith((".h", ".cuh"))})
 GEN = os.path.join(OUT, "gen")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
@@ -41,18 +54,22 @@ def _flags():
 
 
 def _write_jit_source():
-    """Embeds the run-time compiled kernel's source as a C++ raw string."""
+    """Embeds the run-time compiled kernels' sources as C++ raw strings."""
     os.makedirs(GEN, exist_ok=True)
-    text = ""
-    for part in JIT_PARTS:
-        with open(os.path.join(CSRC, part)) as f:
-            text += "// ---- %s\n" % part + f.read().replace("#pragma once", "") + "\n"
-    assert ")MPMJIT\"" not in text
-    out = os.path.join(GEN, "scan_jit_src.inc")
-    body = 'R"MPMJIT(' + text + ')MPMJIT"\n'
-    if not os.path.exists(out) or open(out).read() != body:
-        with open(out, "w") as f:
-            f.write(body)
+    for name, parts in JIT_SOURCES.items():
+        text = ""
+        for part in parts:
+            if part.endswith((".h", ".cuh")):
+                with open(os.path.join(CSRC, part)) as f:
+                    text += "// ---- %s\n" % part + f.read().replace("#pragma once", "") + "\n"
+            else:
+                text += part
+        assert ")MPMJIT\"" not in text
+        out = os.path.join(GEN, name)
+        body = 'R"MPMJIT(' + text + ')MPMJIT"\n'
+        if not os.path.exists(out) or open(out).read() != body:
+            with open(out, "w") as f:
+                f.write(body)
 
 
 def _deps_mtime():

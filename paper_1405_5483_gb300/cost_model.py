@@ -258,14 +258,14 @@ def default_params(P, sigma):
 
 
 def time_batched(P, sigma, T, params, reps=3):
-    """The tuner's measurement of the batched kernel: text T (a CUDA tensor)
-    repeated until at least 128 MiB are scanned (at most 256 copies), median
-    device ms of reps runs divided by the number of copies."""
+    """The tuner's measurement of the precompiled batched kernel: text T (a
+    CUDA tensor) repeated until at least 128 MiB are scanned (at most 256
+    copies), median device ms of reps runs divided by the number of copies."""
     from . import Batch, Matcher
     n = int(T.numel())
     copies = min(256, max(1, -(-(128 << 20) // n)))
     m = Matcher(P, sigma=sigma, **{k: v for k, v in params.items() if k != "kernel"})
-    b = Batch([m], [T] * copies, np.zeros(copies, np.uint32))
+    b = Batch([m], [T] * copies, np.zeros(copies, np.uint32), generic=True)
     b.run()
     ms = []
     for _ in range(reps):

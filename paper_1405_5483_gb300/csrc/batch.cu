@@ -19,7 +19,9 @@
 // split into (text, pos, pid) and the count read-back -- is captured once
 // into a CUDA graph and replayed by every run.
 #include <algorithm>
+#include <cstdio>
 #include <cstring>
+#include <string>
 #include <new>
 #include <numeric>
 #include <vector>
@@ -27,31 +29,14 @@
 #include "handle.h"
 #include "stepper.cuh"
 #include "window_check.cuh"
+#include "batch_args.h"
 
 namespace mpm {
 
 namespace {
 
-struct BatchSet {
-    const void* table;      // mask table (entry_bytes per entry), global memory
-    const uint8_t* mu;
-    const Slot* slots;
-    const uint8_t* pat;
-    const uint32_t* pid;
-    const uint32_t* pat_off;  // row starts when the set's patterns differ in length
-    const uint32_t* keys;   // bitmap of key hashes (key_bits bits), or null
-    uint32_t slot_mask, key_bytes, m, table_bytes;  // table_bytes padded to 16
-    int q, k, mprime, ell, shift, mode, map_kind, entry_bytes;
-    uint32_t key_bits, pad;
-};
-
-struct BatchUnit {
-    uint32_t set, tile_begin, tile_end, pad;
-};
-
 constexpr uint32_t kBatchThreads = 1024;
-constexpr uint32_t kBatchSmemTable = MPM_BATCH_SMEM_TABLE_BYTES;  // larger tables stay in L2
-constexpr uint32_t kBatchKeyBits = 1u << 19;      // key bitmap of a set, at most
+static_assert(kBatchSmemTable == MPM_BATCH_SMEM_TABLE_BYTES, "batch table bound");
 constexpr uint32_t kBatchSmem = 256 + kBatchSmemTable + kBatchKeyBits / 8;
 
 static __device__ __noinline__ void batch_probe(const WindowCtx& wc, uint32_t i,
@@ -71,23 +56,6 @@ __device__ __forceinline__ void batch_check(const WindowCtx& wc, const uint32_t*
     if (!((keys[bit >> 5] >> (bit & 31)) & 1u)) return;
     batch_probe(wc, i, lo, hi, h);
 }
-
-struct BatchText {
-    const uint8_t* T;
-    uint32_t n, set;
-};
-
-struct BatchTile {
-    uint32_t text, start, len, sub;
-};
-
-enum BatchCounter : int { kQueue = 0, kBOcc = 1, kBError = 2, kBCand = 3 };
-
-constexpr int kPosBits = 24;   // text positions < 2^24 in a batch
-constexpr int kPidBits = 20;   // pattern ids < 2^20 per set
-constexpr int kTextShift = kPosBits + kPidBits;  // 44
-
-constexpr int kWarpQueue = 64;  // fired steps a warp holds before it verifies them
 
 // The warp verifies its queued fired steps, one record per lane at a time:
 // record (hq << 32) | fired bits stands for the windows
@@ -317,6 +285,30 @@ __global__ void batch_split_kernel(const uint64_t* keys, const uint32_t* count, 
     }
 }
 
+// The batched kernel's specialisation of one pattern set's plan.
+BatchVariant variant_of(const Plan& plan) {
+    BatchVariant v{};
+    v.q = plan.p.q;
+    v.k = plan.p.k;
+    v.mp = plan.info.mprime;
+    v.ell = plan.ell;
+    v.mode = plan.p.map_kind == MPM_MAP_LOWBITS ? 0 : (plan.p.map_kind == MPM_MAP_QHASH ? 2 : 1);
+    v.shift = v.mode == 0 ? plan.p.map_shift : 0;
+    v.eb = plan.info.entry_bytes;
+    v.C = jit_stage_bytes((uint32_t)(v.q * v.k), v.k, false);
+    v.stages = v.C > 0 ? 1 : 0;
+    if (!v.stages) v.C = (uint32_t)(v.q * v.k);  // sample by sample: lanes of whole periods
+    return v;
+}
+
+// Index of v in vs, appended when new.
+int variant_index(std::vector<BatchVariant>& vs, const BatchVariant& v) {
+    size_t idx = 0;
+    while (idx < vs.size() && std::memcmp(&vs[idx], &v, sizeof(v)) != 0) idx++;
+    if (idx == vs.size()) vs.push_back(v);
+    return (int)idx;
+}
+
 int mode_of(const mpm_handle* h) {
     const auto& p = h->plan.p;
     if (p.map_kind == MPM_MAP_QHASH) return kQHash;
@@ -361,6 +353,7 @@ struct mpm_batch {
     cudaGraphExec_t exec = nullptr;
     cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};  // run start/end, scan start/end
     bool scan_events = true;  // ev[2..3] bracket the scan kernel (inside the graph too)
+    const mpm::BatchJit* jit = nullptr;  // the kernel compiled for this batch, or null
     uint64_t bytes = 0;
     mpm_batch_stats stats{};
 };
@@ -431,9 +424,22 @@ int enqueue_batch(mpm_batch* b, bool capturing = false) {
     cudaStream_t s = b->stream;
     if (cudaMemsetAsync(b->d_counters, 0, 16, s) != cudaSuccess) return MPM_ECUDA;
     if (b->scan_events && !record_event(b->ev[2], s, capturing)) return MPM_ECUDA;
-    mpm::batch_scan_kernel<<<b->num_sms, mpm::kBatchThreads, mpm::kBatchSmem, s>>>(
-        b->d_sets, b->d_texts, b->d_tiles, b->d_units, b->nunits, b->d_occ, b->cap,
-        b->d_counters);
+    if (b->jit) {
+        mpm::BatchJitArgs a{};
+        a.sets = b->d_sets;
+        a.texts = b->d_texts;
+        a.tiles = b->d_tiles;
+        a.units = b->d_units;
+        a.occ = reinterpret_cast<unsigned long long*>(b->d_occ);
+        a.counters = b->d_counters;
+        a.nunits = b->nunits;
+        a.occ_cap = b->cap;
+        if (mpm::launch_batch_jit(b->jit, a, b->num_sms, s) < 0) return MPM_ECUDA;
+    } else {
+        mpm::batch_scan_kernel<<<b->num_sms, mpm::kBatchThreads, mpm::kBatchSmem, s>>>(
+            b->d_sets, b->d_texts, b->d_tiles, b->d_units, b->nunits, b->d_occ, b->cap,
+            b->d_counters);
+    }
     if (b->scan_events && !record_event(b->ev[3], s, capturing)) return MPM_ECUDA;
     int l = mpm::launch_sort_dev(b->d_occ, b->d_tmp, b->d_hist, b->cap, b->d_counters + mpm::kBOcc,
                                  b->shifts, b->nshifts, b->num_sms, &b->sorted, s);
@@ -579,6 +585,24 @@ mpm_batch* mpm_batch_create(mpm_handle* const* sets, int nsets, const uint8_t* c
         S.mode = mpm::mode_of(h);
         hs[i] = S;
     }
+    // the kernel compiled for this batch: one specialisation per distinct
+    // parameter set (q, k, m', sigma', shift, mapping, entry width)
+    if (ok && !o.generic) {
+        std::vector<mpm::BatchVariant> vs;
+        for (int i = 0; i < nsets; i++) {
+            const mpm::BatchVariant v = mpm::variant_of(sets[i]->plan);
+            hs[i].variant = mpm::variant_index(vs, v);
+            hs[i].stage = v.C;
+        }
+        int err = MPM_OK;
+        std::string log;
+        b->jit = mpm::jit_batch_kernel(vs, device, &err, &log);
+        if (!b->jit) {
+            if (!log.empty()) std::fprintf(stderr, "mpm: batched kernel compilation failed:\n%s\n", log.c_str());
+            for (auto& S : hs) S.variant = 0, S.stage = 0;
+        }
+        b->stats.variants = b->jit ? (uint32_t)vs.size() : 0u;
+    }
     // the key bitmaps, one after another (each a multiple of 16 bytes)
     if (ok) {
         size_t words = 0;
@@ -631,8 +655,14 @@ mpm_batch* mpm_batch_create(mpm_handle* const* sets, int nsets, const uint8_t* c
         const uint32_t set = set_of_text[t];
         const mpm::BatchSet& S = hs[set];
         const uint32_t P = (uint32_t)(S.k * S.q);
-        uint32_t G = P;  // lcm(P, 32)
-        while (G % 32) G += P;
+        // lane shares: whole stages of the compiled kernel, or whole sectors
+        // and sampling periods, lcm(P, 32), for the precompiled one
+        uint32_t G = P;
+        if (b->jit) {
+            G = S.stage;
+        } else {
+            while (G % 32) G += P;
+        }
         const uint32_t n = (uint32_t)lens[t];
         if (n < S.m) continue;
         const double rate = std::min(1.0, std::max(0.0, sets[set]->plan.info.est_candidate_rate));
@@ -759,6 +789,31 @@ int mpm_batch_run(mpm_batch* b, uint32_t* out_tid, uint32_t* out_pos, uint32_t* 
         }
         return set_error(MPM_OK);
     }
+}
+
+int mpm_batch_jit_compile(const uint8_t* const* P, const size_t* r, const size_t* m,
+                          const int* sigma, const mpm_params* params, int nsets, char* log,
+                          size_t log_bytes) {
+    if (!P || !r || !m || !sigma || nsets <= 0) return set_error(MPM_EINVAL);
+    std::vector<mpm::BatchVariant> vs;
+    for (int i = 0; i < nsets; i++) {
+        mpm::Plan plan;
+        const int rc = mpm::make_plan(P[i], r[i], m[i], sigma[i], params ? &params[i] : nullptr,
+                                      &plan);
+        if (rc) return set_error(rc);
+        if (plan.info.positions > 32 || plan.p.overlap ||
+            (plan.p.map_kind == MPM_MAP_QHASH && plan.p.q > 5))
+            return set_error(MPM_ENOTSUP);
+        mpm::variant_index(vs, mpm::variant_of(plan));
+    }
+    std::string text;
+    const int rc = mpm::jit_batch_compile_only(vs, &text);
+    if (log && log_bytes) {
+        const size_t c = std::min(log_bytes - 1, text.size());
+        std::memcpy(log, text.data(), c);
+        log[c] = 0;
+    }
+    return set_error(rc);
 }
 
 int mpm_batch_get_stats(const mpm_batch* b, mpm_batch_stats* out) {

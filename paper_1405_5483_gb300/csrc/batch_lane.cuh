@@ -1,0 +1,178 @@
+// One lane's range of one text in the batched search, for the parameter set
+// whose stage primitives (scan_stage.cuh) precede this text in the same
+// namespace: the MAG filter of Sections 3.1 and 3.2 with q, k, m', the
+// mapping and the entry width compiled in, and the exact check of the
+// windows it nominates (Section 3.2).  Compiled at run time (NVRTC) once per
+// parameter set of a batch, inside that set's namespace.
+//
+// The lane's range [a, b) starts on a multiple of C from the text start, so
+// every stage of C bytes holds the same C/P sampled q-grams at the same
+// offsets, as in the single-text scan; the warp's lanes step through their
+// stages together, each stage read with C/16 vector loads, and queue the
+// fired samples in shared memory, verifying them 32 at a time.
+
+// The warp verifies its queued fired samples, one record per lane: record
+// (h << 32) | fired stands, for each fired bit j, for the window of q-grams
+// h0 = h - (m'-1)k - j, i.e. the text starts h0 q - s, s = q-1 .. 0, walked
+// in ascending order: the key of the first start is read from the text, each
+// next one drops a byte and takes in the byte after it; a key whose hash
+// misses the set's bitmap has no pattern group to probe.
+__device__ __forceinline__ void flush_queue(const u64* queue, int count, const u32* keys,
+                                            u32 key_mask, const WindowCtx& wc) {
+    const i64 last = (i64)wc.n - (i64)wc.m;  // the last start of a whole window
+    const u32 kb = wc.key_bytes;             // 1 .. 16
+    const u32 top = 8 * ((kb - 1) & 7);      // bit offset of a key's last byte
+    for (int r = (int)(threadIdx.x & 31); r < count; r += 32) {
+        const u64 rec = queue[r];
+        const i64 h = (i64)(rec >> 32);
+        u32 fired = (u32)rec;
+        while (fired) {
+            const int j = __ffs((int)fired) - 1;
+            fired &= fired - 1;
+            const i64 h0 = h - RSH - j;
+            const i64 first = h0 * VQ - (VQ - 1) > 0 ? h0 * VQ - (VQ - 1) : 0;
+            const i64 end = h0 * VQ < last ? h0 * VQ : last;
+            if (first > end) continue;
+            u32 i = (u32)first;
+            unsigned long long lo, hi;
+            window_key(wc, i, &lo, &hi);
+            for (;;) {
+                const unsigned long long hs = key_hash(lo, hi);
+                const u32 bit = (u32)hs & key_mask;
+                if ((keys[bit >> 5] >> (bit & 31)) & 1u) probe_window(wc, i, lo, hi, hs);
+                if ((i64)i >= end) break;
+                // i + kb <= i + m - 1 < n: the byte after the key is in the text
+                const unsigned long long nb = __ldg(wc.T + i + kb);
+                lo = (lo >> 8) | (hi << 56);
+                hi >>= 8;
+                if (kb <= 8)
+                    lo |= nb << top;
+                else
+                    hi |= nb << top;
+                i++;
+            }
+        }
+    }
+}
+
+// Queues the fired samples of one stage (for every lane, every sample u
+// with report bits: (h1 + u k) << 32 | bits), verifying whenever 32 or more
+// are queued.  Warp-collective.
+__device__ __forceinline__ void queue_stage(FT fm, u32 h1, u64* queue, int& qcount, u32& ncand,
+                                            const u32* keys, u32 key_mask, const WindowCtx& wc) {
+    for (;;) {
+        const bool has = fm != 0;
+        const u32 bal = __ballot_sync(0xFFFFFFFFu, has);
+        if (bal == 0) break;
+        if (has) {
+            const int bit = (sizeof(FT) == 8) ? (__ffsll((long long)fm) - 1) : (__ffs((int)fm) - 1);
+            const int u = bit / K;
+            const u32 fired = (u32)(fm >> (u * K)) & KMASK;
+            fm &= ~((FT)KMASK << (u * K));
+            queue[qcount + __popc(bal & lanemask_lt())] = ((u64)(h1 + (u32)(u * K)) << 32) | fired;
+            ncand++;
+        }
+        qcount += __popc(bal);
+        if (qcount >= 32) {
+            __syncwarp();
+            flush_queue(queue, qcount, keys, key_mask, wc);
+            qcount = 0;
+            __syncwarp();
+        }
+    }
+}
+
+// All 32 lanes of a warp call this together for one tile; lane range
+// [a, b), live = a < b.  tab: the set's mask table (shared or global
+// memory), smu: its byte map in shared memory.
+__device__ __forceinline__ void batch_lane(const ET* tab, const u8* smu, const u32* keys,
+                                           u32 key_mask, const u8* T, u32 n, u32 a, u32 b,
+                                           bool live, const WindowCtx& wc, u64* queue,
+                                           u32& ncand) {
+    (void)n;
+    DT D = ~(DT)0;
+    // the m'-1 samples that end at a, a - P, ...; those that would start
+    // before the text do not exist and leave D at all ones
+    if (live) {
+        for (int j = MP - 2; j >= 0; j--) {
+            const i64 e = (i64)a - (i64)j * P;
+            if (e - Q < 0) continue;
+            D = (D << K) | entry(tab, code_bytes(T, (u32)(e - Q), smu), 0ull);
+        }
+    }
+    const bool vec = (reinterpret_cast<unsigned long long>(T) & 15) == 0;
+    const u32 nst = (MPM_STAGES && live && vec) ? (b - a) / (u32)C : 0u;
+    int qcount = 0;
+#if MPM_STAGES
+    u32 nmax = nst;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) nmax = max(nmax, __shfl_xor_sync(0xFFFFFFFFu, nmax, o));
+    const u32 h_a = a / (u32)Q + (u32)(K - 1);  // q-gram index of the first sample
+#pragma unroll 1
+    for (u32 st = 0; st < nmax; st++) {
+        const bool act = st < nst;
+        u32 w[C / 4];
+        if (act) {
+            const uint4* p = reinterpret_cast<const uint4*>(T + a + st * (u32)C);
+#pragma unroll
+            for (int i = 0; i < C / 16; i++) {
+                const uint4 v = __ldg(p + i);
+                w[4 * i] = v.x;
+                w[4 * i + 1] = v.y;
+                w[4 * i + 2] = v.z;
+                w[4 * i + 3] = v.w;
+            }
+        } else {
+#pragma unroll
+            for (int i = 0; i < C / 4; i++) w[i] = 0u;
+        }
+        // a lane past its own stages steps with the warp but keeps its state
+        // for the rest of its range
+        const DT keep = D;
+        FT fm = 0;
+        run_stage<true>(w, D, fm, tab, smu, 0ull);
+        if (!act) {
+            D = keep;
+            fm = 0;
+        }
+        if (__any_sync(0xFFFFFFFFu, fm != 0))
+            queue_stage(fm, h_a + st * (u32)(C / Q), queue, qcount, ncand, keys, key_mask, wc);
+    }
+#endif
+    // the rest of the range, sample by sample with byte loads
+    const u32 e0 = a + nst * (u32)C;
+    const u32 nrest = live ? (b - e0) / (u32)P : 0u;
+    u32 rmax = nrest;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) rmax = max(rmax, __shfl_xor_sync(0xFFFFFFFFu, rmax, o));
+    const u32 below = lanemask_lt();
+#pragma unroll 1
+    for (u32 t = 0; t < rmax; t++) {
+        u32 fired = 0, hq = 0;
+        if (t < nrest) {
+            const u32 st = e0 + (t + 1) * (u32)P - (u32)Q;
+            D = (D << K) | entry(tab, code_bytes(T, st, smu), 0ull);
+            fired = ~bits_at(D, RSH) & KMASK;
+            hq = st / (u32)Q;
+        }
+        const u32 bal = __ballot_sync(0xFFFFFFFFu, fired != 0);
+        if (bal) {
+            if (fired) {
+                queue[qcount + __popc(bal & below)] = ((u64)hq << 32) | fired;
+                ncand++;
+            }
+            qcount += __popc(bal);
+            if (qcount >= 32) {
+                __syncwarp();
+                flush_queue(queue, qcount, keys, key_mask, wc);
+                qcount = 0;
+                __syncwarp();
+            }
+        }
+    }
+    if (qcount) {
+        __syncwarp();
+        flush_queue(queue, qcount, keys, key_mask, wc);
+        __syncwarp();
+    }
+}

@@ -23,6 +23,7 @@
 #include <nvrtc.h>
 
 #include "kernels.h"
+#include "batch_args.h"
 #include "scan_jit_args.h"
 
 namespace mpm {
@@ -31,6 +32,15 @@ namespace {
 
 const char kJitSource[] =
 #include "scan_jit_src.inc"
+    ;
+const char kBatchPrelude[] =
+#include "batch_prelude_src.inc"
+    ;
+const char kBatchStage[] =
+#include "batch_stage_src.inc"
+    ;
+const char kBatchKernel[] =
+#include "batch_kernel_src.inc"
     ;
 
 struct NvrtcApi {
@@ -149,6 +159,22 @@ struct JitKernel {
     int blocks_per_sm = 1;
 };
 
+// Stage bytes of the specialised scans for P text bytes per sampled q-gram:
+// rows of at least 80 bytes (48-byte rows measured up to 3x slower on
+// GB300); odd multiples of lcm(P, 16) keep C/16 odd, which keeps the 16-byte
+// shared loads of a quarter warp on distinct banks; non-overlapping, at
+// most 64 report bits per stage (C / P * k <= 64; the overlapping stage finds
+// its report bits again only when one fired).  0 when lcm(P, 16) > 256.
+uint32_t jit_stage_bytes(uint32_t P, int k, bool overlap) {
+    const uint32_t base = lcm_u(P, 16);
+    if (base > 256) return 0;
+    auto bits_ok = [&](uint32_t c) { return overlap || c / P * (uint32_t)k <= 64; };
+    uint32_t C = base;
+    const uint32_t step = ((base / 16) % 2 == 1) ? 2 * base : base;
+    while (C < 80 && C + step <= 256 && bits_ok(C + step)) C += step;
+    return bits_ok(C) ? C : 0;
+}
+
 // The specialisation for a filter, or false when the filter is outside what
 // the specialised kernel handles (then the generic kernel runs).
 bool jit_spec(const FilterDev& f, bool verify, JitSpec* out) {
@@ -168,16 +194,9 @@ bool jit_spec(const FilterDev& f, bool verify, JitSpec* out) {
     // bytes per sampled q-gram: k q non-overlapping, k overlapping
     const uint32_t P = (uint32_t)(s.ov ? f.k : f.k * f.q);
     const uint32_t base = lcm_u(P, 16);
-    if (base > 256) return false;
-    // stage rows of at least 80 bytes (48-byte rows measured up to 3x slower
-    // on GB300); odd multiples of base keep C/16 odd, which keeps the 16-byte
-    // shared loads of a quarter warp on distinct banks
-    // (and, non-overlapping, at most 64 report bits per stage: C / P * k <= 64;
-    // the overlapping stage finds its report bits again only when one fired)
+    uint32_t C = jit_stage_bytes(P, f.k, s.ov != 0);
+    if (C == 0) return false;
     auto bits_ok = [&](uint32_t c) { return s.ov || c / P * (uint32_t)f.k <= 64; };
-    uint32_t C = base;
-    const uint32_t step = ((base / 16) % 2 == 1) ? 2 * base : base;
-    while (C < 80 && C + step <= 256 && bits_ok(C + step)) C += step;
     s.warps = 16;
     // overrides for tuning the geometry: MPM_JIT_C (stage bytes, a multiple
     // of lcm(k q, 16) up to 256) and MPM_JIT_WARPS (4..32)
@@ -208,19 +227,21 @@ bool jit_spec(const FilterDev& f, bool verify, JitSpec* out) {
     return true;
 }
 
-static int compile_spec(const JitSpec& s, std::string* cubin, std::string* log) {
+// Compiles a source text with NVRTC for sm_103a, with the -D options in
+// `defines` (space separated); the cubin (may be null) and the log.
+static int compile_source(const char* src, const char* name, const std::string& defines,
+                          std::string* cubin, std::string* log) {
     const NvrtcApi& nv = nvrtc();
     if (!nv.ok) {
         if (log) *log = "NVRTC not found";
         return MPM_ENOTSUP;
     }
     nvrtcProgram prog;
-    if (nv.create(&prog, kJitSource, "mpm_scan_jit.cu", 0, nullptr, nullptr) != NVRTC_SUCCESS)
-        return MPM_ECUDA;
+    if (nv.create(&prog, src, name, 0, nullptr, nullptr) != NVRTC_SUCCESS) return MPM_ECUDA;
     std::vector<std::string> opts = {"--gpu-architecture=sm_103a", "--std=c++17", "-lineinfo"};
     if (std::getenv("MPM_JIT_VERBOSE")) opts.push_back("--ptxas-options=-v");
     {
-        std::string d = s.defines();
+        const std::string& d = defines;
         size_t pos = 0;
         while (pos < d.size()) {
             size_t e = d.find(' ', pos);
@@ -249,6 +270,10 @@ static int compile_spec(const JitSpec& s, std::string* cubin, std::string* log) 
     }
     nv.destroy(&prog);
     return ret;
+}
+
+static int compile_spec(const JitSpec& s, std::string* cubin, std::string* log) {
+    return compile_source(kJitSource, "mpm_scan_jit.cu", s.defines(), cubin, log);
 }
 
 int jit_compile_only(const FilterDev& f, bool verify, std::string* log) {
@@ -446,6 +471,124 @@ int launch_scan_jit(const ScanArgs& A, const VerifyArgs* V, const JitKernel* K, 
     void* params[2] = {&J, &tmap};
     if (drv.launch(K->fn, blocks, 1, 1, (unsigned)(s.warps * 32), 1, 1, (unsigned)s.smem_bytes,
                    reinterpret_cast<CUstream>(stream), params, nullptr) != CUDA_SUCCESS)
+        return -1;
+    return 1;
+}
+
+// ------------------------------------------------------- the batched kernel
+
+// Dynamic shared memory of the batched kernel: the byte map, the largest mask
+// table it copies, the largest key bitmap.
+constexpr size_t kBatchJitSmem = 256 + kBatchSmemTable + kBatchKeyBits / 8;
+
+struct BatchJit {
+    CUfunction fn = nullptr;
+};
+
+namespace {
+std::mutex g_batch_mu;
+std::map<std::string, std::string> g_batch_cubins;                // source -> cubin
+std::map<std::string, std::unique_ptr<BatchJit>> g_batch_kernels;  // device + source -> kernel
+}  // namespace
+
+// The batch's source: the prelude, then for every parameter set its stage
+// primitives and lane scan in a namespace bv<i> of their own, compiled with
+// its constants, then the kernel dispatching on the set's variant index.
+static std::string batch_source(const std::vector<BatchVariant>& vs) {
+    std::string src = kBatchPrelude;
+    char buf[512];
+    for (size_t i = 0; i < vs.size(); i++) {
+        const BatchVariant& v = vs[i];
+        std::snprintf(buf, sizeof(buf),
+                      "namespace mpm {\nnamespace bv%zu {\n#define MPM_Q %d\n#define MPM_K %d\n"
+                      "#define MPM_MP %d\n#define MPM_ELL %d\n#define MPM_SHIFT %d\n"
+                      "#define MPM_MODE %d\n#define MPM_EB %d\n#define MPM_SMEM 1\n"
+                      "#define MPM_C %u\n#define MPM_OV 0\n#define MPM_STAGES %d\n",
+                      i, v.q, v.k, v.mp, v.ell, v.shift, v.mode, v.eb, v.C, v.stages);
+        src += buf;
+        src += kBatchStage;
+        src += "\n#undef MPM_Q\n#undef MPM_K\n#undef MPM_MP\n#undef MPM_ELL\n#undef MPM_SHIFT\n"
+               "#undef MPM_MODE\n#undef MPM_EB\n#undef MPM_SMEM\n#undef MPM_C\n#undef MPM_OV\n"
+               "#undef MPM_STAGES\n"
+               "}  // namespace bv\n}  // namespace mpm\n";
+    }
+    src += "#define MPM_BATCH_CASES";
+    for (size_t i = 0; i < vs.size(); i++) {
+        std::snprintf(buf, sizeof(buf), " CASE(%zu)", i);
+        src += buf;
+    }
+    src += "\n";
+    src += kBatchKernel;
+    return src;
+}
+
+static int batch_cubin(const std::string& src, std::string* cubin, std::string* log) {
+    {
+        std::lock_guard<std::mutex> lock(g_batch_mu);
+        auto it = g_batch_cubins.find(src);
+        if (it != g_batch_cubins.end()) {
+            *cubin = it->second;
+            return MPM_OK;
+        }
+    }
+    const int rc = compile_source(src.c_str(), "mpm_batch_jit.cu", "", cubin, log);
+    if (rc == MPM_OK) {
+        std::lock_guard<std::mutex> lock(g_batch_mu);
+        g_batch_cubins[src] = *cubin;
+    }
+    return rc;
+}
+
+int jit_batch_compile_only(const std::vector<BatchVariant>& vs, std::string* log) {
+    std::string cubin;
+    return batch_cubin(batch_source(vs), &cubin, log);
+}
+
+const BatchJit* jit_batch_kernel(const std::vector<BatchVariant>& vs, int device, int* err,
+                                 std::string* log) {
+    *err = MPM_OK;
+    const DriverApi& drv = driver();
+    if (!drv.ok || vs.empty()) {
+        *err = MPM_ENOTSUP;
+        return nullptr;
+    }
+    const std::string src = batch_source(vs);
+    const std::string key = std::to_string(device) + "\n" + src;
+    {
+        std::lock_guard<std::mutex> lock(g_batch_mu);
+        auto it = g_batch_kernels.find(key);
+        if (it != g_batch_kernels.end()) return it->second.get();
+    }
+    std::string cubin;
+    const int rc = batch_cubin(src, &cubin, log);
+    if (rc) {
+        *err = rc;
+        return nullptr;
+    }
+    CUmodule mod;
+    CUfunction fn;
+    if (drv.load(&mod, cubin.data()) != CUDA_SUCCESS ||
+        drv.get(&fn, mod, "mpm_batch_jit") != CUDA_SUCCESS ||
+        drv.set_attr(fn, CU_FUNC_ATTRIBUTE_MAX_DYNAMIC_SHARED_SIZE_BYTES, (int)kBatchJitSmem) !=
+            CUDA_SUCCESS) {
+        *err = MPM_ECUDA;
+        return nullptr;
+    }
+    auto k = std::make_unique<BatchJit>();
+    k->fn = fn;
+    std::lock_guard<std::mutex> lock(g_batch_mu);
+    auto& slot = g_batch_kernels[key];
+    if (!slot) slot = std::move(k);
+    return slot.get();
+}
+
+int launch_batch_jit(const BatchJit* k, const BatchJitArgs& a, int num_sms, cudaStream_t s) {
+    const DriverApi& drv = driver();
+    BatchJitArgs args = a;
+    void* params[1] = {&args};
+    // one block of 16 warps per SM (the kernel's launch bounds)
+    if (drv.launch(k->fn, (unsigned)num_sms, 1, 1, 512, 1, 1, (unsigned)kBatchJitSmem,
+                   reinterpret_cast<CUstream>(s), params, nullptr) != CUDA_SUCCESS)
         return -1;
     return 1;
 }

@@ -105,6 +105,32 @@ bool jit_verifies(const JitKernel* k);
 int launch_scan_jit(const ScanArgs& a, const VerifyArgs* v, const JitKernel* k, int num_sms,
                     int chunk, cudaStream_t s);
 
+// Stage bytes C of the specialised scans for P text bytes per sampled q-gram
+// (0 when lcm(P, 16) > 256).
+uint32_t jit_stage_bytes(uint32_t P, int k, bool overlap);
+
+// One parameter set of a batch, as the batched kernel compiled at run time
+// specialises it: q, k, m', log2 sigma', low-bit shift, mapping (0 low bits,
+// 1 byte map, 2 q-gram hashing), entry bytes, stage bytes C and whether the
+// lanes scan whole stages (else, when no stage of at most 256 bytes fits the
+// sampling period, sample by sample; C is then the period).
+struct BatchVariant {
+    int q, k, mp, ell, shift, mode, eb;
+    uint32_t C;
+    int stages;
+};
+struct BatchJit;
+struct BatchJitArgs;
+// Compiles (NVRTC, cached per process) and loads the batched kernel for these
+// parameter sets on the current device; nullptr with *err set when NVRTC or
+// the driver entry points are missing or the compilation fails.
+const BatchJit* jit_batch_kernel(const std::vector<BatchVariant>& vs, int device, int* err,
+                                 std::string* log);
+// Host-only: compiles it without loading.
+int jit_batch_compile_only(const std::vector<BatchVariant>& vs, std::string* log);
+// One persistent block per SM; returns 1 or -1.
+int launch_batch_jit(const BatchJit* k, const BatchJitArgs& a, int num_sms, cudaStream_t s);
+
 // Sorts the device-counted occurrence keys (counters[kOccCount], in keys)
 // into out_pos/out_pid without the host knowing the count: one grid-wide
 // rank sort, valid while the count is at most kRankSortMax and at most

@@ -291,8 +291,12 @@ extern "C" int mpm_autotune(const uint8_t* P, size_t r, size_t m, int sigma, con
                 const std::vector<const uint8_t*> texts(copies, dT);
                 const std::vector<size_t> lens(copies, n);
                 const std::vector<uint32_t> sot(copies, 0u);
+                // the precompiled batched kernel (run-time q, k and mapping):
+                // one compilation per timed set would cost more than the timing
+                mpm_batch_opts bo{};
+                bo.generic = 1;
                 batch = mpm_batch_create(&h, 1, texts.data(), lens.data(), sot.data(),
-                                         (int)copies, nullptr);
+                                         (int)copies, &bo);
                 if (!batch) e.status = mpm_last_error();
             }
             if (h && e.status == MPM_OK) {

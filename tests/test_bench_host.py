@@ -47,7 +47,7 @@ def _fake_tree(tmp_path, files):
 
 def test_recorded_traffic_follows_the_kernel_revision(tmp_path, monkeypatch):
     files = ("keyhash.h", "multiword.h", "scan_jit_args.h", "ptx_common.cuh",
-             "window_check.cuh", "scan_jit.cuh", "jit.cpp")
+             "window_check.cuh", "jit_types.h", "scan_stage.cuh", "scan_jit.cuh", "jit.cpp")
     csrc = _fake_tree(tmp_path, files)
     monkeypatch.setattr(bench, "ROOT", str(tmp_path))
     rev = bench.kernel_rev()
@@ -65,8 +65,8 @@ def test_recorded_traffic_follows_the_kernel_revision(tmp_path, monkeypatch):
 
 
 def test_batch_traffic_record_uses_its_own_revision(tmp_path, monkeypatch):
-    files = ("batch.cu", "stepper.cuh", "multiword.h", "device_common.cuh", "window_check.cuh",
-             "keyhash.h")
+    files = ("batch.cu", "batch_args.h", "stepper.cuh", "multiword.h", "device_common.cuh",
+             "window_check.cuh", "keyhash.h")
     _fake_tree(tmp_path, files)
     monkeypatch.setattr(bench, "ROOT", str(tmp_path))
     rev = bench.batch_kernel_rev()

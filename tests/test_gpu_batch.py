@@ -82,14 +82,18 @@ def triples(tid, pos, pid):
                      pid.cpu().numpy().view(np.uint32)], axis=1)
 
 
-def test_batch_matches_oracle_graph_and_plain(mpm, native):
+@pytest.mark.parametrize("generic", [False, True], ids=["compiled", "precompiled"])
+def test_batch_matches_oracle_graph_and_plain(mpm, native, generic):
+    """The kernel compiled for the batch's parameter sets and the precompiled
+    one with run-time parameters."""
     texts, sets, sot = small_config4()
     want = expected(native, texts, sets, sot)
     assert want.shape[0] > 1000
     dev = [torch.from_numpy(t).cuda() for t in texts]
     ms = batch_matchers(mpm, sets)
     for graph in (True, False):
-        b = mpm.Batch(ms, dev, sot, graph=graph)
+        b = mpm.Batch(ms, dev, sot, graph=graph, generic=generic)
+        assert (b.stats["variants"] == 0) == generic
         for _ in range(2):  # replays must not see the previous run
             got = triples(*b.run())
             assert np.array_equal(got, want)
@@ -106,7 +110,14 @@ def test_batch_small_lanes_and_one_shot_call(mpm, native):
     want = expected(native, texts, sets, sot)
     dev = [torch.from_numpy(t).cuda() for t in texts]
     ms = batch_matchers(mpm, sets)
-    b = mpm.Batch(ms, dev, sot, lane_bytes=40)
+    for generic in (False, True):
+        b = mpm.Batch(ms, dev, sot, lane_bytes=40, generic=generic)
+        assert np.array_equal(triples(*b.run()), want)
+        b.close()
+    # unaligned texts: the compiled kernel's lanes fall back to byte loads
+    unal = [torch.cat([torch.zeros(1, dtype=torch.uint8, device="cuda"), t])[1:] for t in dev]
+    b = mpm.Batch(ms, unal, sot)
+    assert b.stats["variants"] > 0
     assert np.array_equal(triples(*b.run()), want)
     b.close()
     # the one-shot C call, host outputs
@@ -155,8 +166,17 @@ def test_config4_full_shape_learned_parameters_equal_oracle(mpm, native):
     params = CM.learned_batch_params(b, model, _native.BATCH_SMEM_TABLE_BYTES)
     ms = [CM.batch_matcher(P, b.sigma, p) for P, p in zip(b.sets, params)]
     assert max(P.shape[0] for P in b.sets) > 5000 and max(t.size for t in b.texts) > 1 << 21
-    dev = [torch.from_numpy(t).cuda() for t in b.texts]
+    # the texts in one buffer at 256-byte offsets, as the benchmark lays them out
+    offs = np.zeros(len(b.texts) + 1, np.int64)
+    for i, t in enumerate(b.texts):
+        offs[i + 1] = (offs[i] + t.size + 255) & ~255
+    flat = torch.zeros(int(offs[-1]), dtype=torch.uint8, device="cuda")
+    dev = []
+    for i, t in enumerate(b.texts):
+        flat[int(offs[i]): int(offs[i]) + t.size] = torch.from_numpy(t).cuda()
+        dev.append(flat[int(offs[i]): int(offs[i]) + t.size])
     B = mpm.Batch(ms, dev, b.set_of_text)
+    assert B.stats["variants"] > 0
     got = triples(*B.run())
     B.close()
 

@@ -305,3 +305,31 @@ def test_planner_rate_is_the_oracle_filters_window_rate(mpm, alpha, r, mlen, kw)
         assert rate >= 0.9
     else:
         assert abs(rate - est) <= 0.1 * est + 3 * np.sqrt(windows) / steps, (rate, est)
+
+
+def test_batched_kernel_compiles_for_a_mixed_batch(mpm):
+    """The kernel compiled per batch (NVRTC, sm_103a) for pattern sets of
+    every mapping, entry width and period, on a machine without a GPU."""
+    from paper_1405_5483_gb300 import workloads as W
+    sets, sigmas, params = [], [], []
+    for i, (alpha, m, kw) in enumerate([
+            ("english", 8, dict(q=2, sigma_r=16, k=1, map_kind=2)),
+            ("english", 16, dict(q=3, sigma_r=8, k=2, map_kind=1)),
+            ("english", 32, dict(q=4, sigma_r=1 << 12, k=1, map_kind=4)),
+            ("dna", 16, dict(q=5, sigma_r=4, k=1, map_kind=3, map_shift=1)),
+            ("protein", 64, dict(q=3, sigma_r=16, k=3, map_kind=2)),
+            ("english", 64, dict(q=6, sigma_r=4, k=2, map_kind=2)),
+            ("english", 16, dict(q=3, sigma_r=8, k=2, map_kind=1)),    # a repeated set
+            ("english", 64, dict(q=5, sigma_r=4, k=5, map_kind=2))]):  # period 25: no stage
+        make = {"dna": W.dna_case, "protein": W.protein_case, "english": W.english_case}[alpha]
+        c = make(1 << 12, 40, m, 10, cfg=10 + i)
+        sets.append(c.P)
+        sigmas.append(c.sigma)
+        params.append(kw)
+    rc, log = mpm.batch_jit_compile(sets, sigmas, params)
+    if rc == mpm.MPM_ENOTSUP and "NVRTC not found" in log:
+        pytest.skip("NVRTC is not installed here")
+    assert rc == mpm.MPM_OK, log
+    # more than 32 positions: not a batch set
+    rc, _ = mpm.batch_jit_compile([sets[4]], [20], [dict(q=1, sigma_r=16, k=1, map_kind=2)])
+    assert rc == mpm.MPM_ENOTSUP
