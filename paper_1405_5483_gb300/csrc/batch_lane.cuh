@@ -104,6 +104,10 @@ __device__ __forceinline__ void batch_lane(const ET* tab, const u8* smu, const u
     const u32 nst = (MPM_STAGES && live && vec) ? (b - a) / (u32)C : 0u;
     int qcount = 0;
 #if MPM_STAGES
+    // the lane's stages stream into L2 kPrefetch stages ahead of its loads
+    constexpr u32 kPrefetch = MPM_BATCH_PREFETCH;
+    if (kPrefetch > 0 && nst > 0)
+        prefetch_l2_bulk(T + a, (nst < kPrefetch ? nst : kPrefetch) * (u32)C);
     u32 nmax = nst;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) nmax = max(nmax, __shfl_xor_sync(0xFFFFFFFFu, nmax, o));
@@ -111,6 +115,8 @@ __device__ __forceinline__ void batch_lane(const ET* tab, const u8* smu, const u
 #pragma unroll 1
     for (u32 st = 0; st < nmax; st++) {
         const bool act = st < nst;
+        if (kPrefetch > 0 && st + kPrefetch < nst)
+            prefetch_l2_bulk(T + a + (st + kPrefetch) * (u32)C, (u32)C);
         u32 w[C / 4];
         if (act) {
             const uint4* p = reinterpret_cast<const uint4*>(T + a + st * (u32)C);

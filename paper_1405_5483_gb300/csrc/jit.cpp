@@ -495,8 +495,17 @@ std::map<std::string, std::unique_ptr<BatchJit>> g_batch_kernels;  // device + s
 // primitives and lane scan in a namespace bv<i> of their own, compiled with
 // its constants, then the kernel dispatching on the set's variant index.
 static std::string batch_source(const std::vector<BatchVariant>& vs) {
-    std::string src = kBatchPrelude;
     char buf[512];
+    // stages a lane prefetches into L2 ahead of its loads (4; measurement
+    // override MPM_BATCH_PREFETCH, 0..8)
+    int prefetch = 4;
+    if (const char* e = std::getenv("MPM_BATCH_PREFETCH")) {
+        const int v = std::atoi(e);
+        if (v >= 0 && v <= 8) prefetch = v;
+    }
+    std::snprintf(buf, sizeof(buf), "#define MPM_BATCH_PREFETCH %d\n", prefetch);
+    std::string src = buf;
+    src += kBatchPrelude;
     for (size_t i = 0; i < vs.size(); i++) {
         const BatchVariant& v = vs[i];
         std::snprintf(buf, sizeof(buf),

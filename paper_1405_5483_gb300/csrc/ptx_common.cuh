@@ -104,6 +104,15 @@ __device__ __forceinline__ void tma_load_2d_hint(unsigned int dst, const void* m
         : "memory");
 }
 
+// Bulk prefetch of [p, p + bytes) into L2 (p 16-byte aligned, bytes a
+// multiple of 16): no registers and no completion to wait for.
+__device__ __forceinline__ void prefetch_l2_bulk(const void* p, unsigned int bytes) {
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(
+                     reinterpret_cast<unsigned long long>(p)),
+                 "r"(bytes)
+                 : "memory");
+}
+
 // Read-only global loads with an L2 cache policy.
 __device__ __forceinline__ unsigned int ldg_hint_u8(const unsigned char* p,
                                                     unsigned long long policy) {
