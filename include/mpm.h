@@ -126,6 +126,11 @@ typedef struct {
     double est_candidate_rate; /* expected candidate windows (fired subpatterns)
                                   per sampled q-gram in i.i.d. text with the
                                   pattern set's symbol frequencies, at most 1  */
+    int entry_bits;    /* bits per mask-table entry: 8 * entry_bytes, or 1, 2 or 4
+                          when a table of filters of at most 4 positions, too
+                          large for shared memory, packs several entries into a
+                          byte (entry c at bit c * entry_bits, lowest first; the
+                          specialised kernels only)                             */
 } mpm_table_info;
 
 /* Counters of the last mpm_search / mpm_scan on a handle. */
@@ -403,10 +408,10 @@ typedef struct {
     int max_k;           /* largest k tried; 0 = 8                                  */
     int reps;            /* timed searches per parameter set (median); 0 = 3       */
     int kernels;         /* bit 0 specialised, bit 1 split, bit 2 generic (timed
-                            through mpm_search), bit 3 the precompiled batched
-                            kernel (one mpm_batch with generic = 1 over copies of
-                            the sample, at least 128 MiB and at most 256 copies,
-                            sets of <= 32 positions); 0 = 1                        */
+                            through mpm_search), bit 3 the batched kernel (one
+                            mpm_batch over copies of the sample, at least 128 MiB
+                            and at most 256 copies, sets of <= 32 positions);
+                            0 = 1                                                  */
     int max_sets;        /* at most this many sets are timed, lowest estimated
                             candidate rate first; 0 = 64                            */
     double max_rate;     /* sets whose estimated candidate records per sampled
@@ -422,6 +427,9 @@ typedef struct {
                             the overlapping q-grams of Section 2, each family
                             ranked on its own and given half of max_sets; 2: the
                             overlapping ones only (tuner grid only)                */
+    int batch_generic;   /* bit 3 times: 0 the batched kernel compiled for the set
+                            (compiled for every timed set first, in parallel); 1 the
+                            precompiled one (run-time q, k and mapping)           */
 } mpm_tune_opts;
 
 typedef struct {

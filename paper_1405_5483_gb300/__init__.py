@@ -95,15 +95,16 @@ def host_tables(P, sigma, **kw):
 
 
 def autotune(P, sigma, T, max_q=0, max_k=0, reps=0, kernels=0, max_sets=0, max_rate=0.0,
-             max_positions=0, grid=0, max_table_kib=0, overlap=0):
+             max_positions=0, grid=0, max_table_kib=0, overlap=0, batch_generic=0):
     """Exhaustive parameter search timed on the sample text T (CUDA tensor or
     numpy).  grid=1 times every point of the cost model's grid; overlap=1
-    also times overlapping-q-gram filters (2: only those).  Returns
+    also times overlapping-q-gram filters (2: only those); batch_generic=1
+    times the precompiled batched kernel for kernels bit 3.  Returns
     (best params dict, list of timed sets)."""
     from ._native import TuneEntry, TuneOpts
     P = _patterns(P)
     opts = TuneOpts(max_q, max_k, reps, kernels, max_sets, max_rate, max_positions, grid,
-                    max_table_kib, overlap)
+                    max_table_kib, overlap, batch_generic)
     cap = 4096
     entries = (TuneEntry * cap)()
     best = Params()

@@ -33,7 +33,8 @@ class Params(ctypes.Structure):
 class TableInfo(ctypes.Structure):
     _fields_ = [("L", ctypes.c_int), ("mprime", ctypes.c_int), ("positions", ctypes.c_int),
                 ("entry_bytes", ctypes.c_int), ("entries", ctypes.c_uint64),
-                ("table_bytes", ctypes.c_uint64), ("est_candidate_rate", ctypes.c_double)]
+                ("table_bytes", ctypes.c_uint64), ("est_candidate_rate", ctypes.c_double),
+                ("entry_bits", ctypes.c_int)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}
@@ -55,7 +56,7 @@ class TuneOpts(ctypes.Structure):
                 ("kernels", ctypes.c_int), ("max_sets", ctypes.c_int),
                 ("max_rate", ctypes.c_double), ("max_positions", ctypes.c_int),
                 ("grid", ctypes.c_int), ("max_table_kib", ctypes.c_int),
-                ("overlap", ctypes.c_int)]
+                ("overlap", ctypes.c_int), ("batch_generic", ctypes.c_int)]
 
 
 MODEL_INPUTS, MODEL_HIDDEN, MODEL_PARAMS = 8, 64, 4801

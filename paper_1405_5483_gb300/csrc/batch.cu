@@ -285,30 +285,6 @@ __global__ void batch_split_kernel(const uint64_t* keys, const uint32_t* count, 
     }
 }
 
-// The batched kernel's specialisation of one pattern set's plan.
-BatchVariant variant_of(const Plan& plan) {
-    BatchVariant v{};
-    v.q = plan.p.q;
-    v.k = plan.p.k;
-    v.mp = plan.info.mprime;
-    v.ell = plan.ell;
-    v.mode = plan.p.map_kind == MPM_MAP_LOWBITS ? 0 : (plan.p.map_kind == MPM_MAP_QHASH ? 2 : 1);
-    v.shift = v.mode == 0 ? plan.p.map_shift : 0;
-    v.eb = plan.info.entry_bytes;
-    v.C = jit_stage_bytes((uint32_t)(v.q * v.k), v.k, false);
-    v.stages = v.C > 0 ? 1 : 0;
-    if (!v.stages) v.C = (uint32_t)(v.q * v.k);  // sample by sample: lanes of whole periods
-    return v;
-}
-
-// Index of v in vs, appended when new.
-int variant_index(std::vector<BatchVariant>& vs, const BatchVariant& v) {
-    size_t idx = 0;
-    while (idx < vs.size() && std::memcmp(&vs[idx], &v, sizeof(v)) != 0) idx++;
-    if (idx == vs.size()) vs.push_back(v);
-    return (int)idx;
-}
-
 int mode_of(const mpm_handle* h) {
     const auto& p = h->plan.p;
     if (p.map_kind == MPM_MAP_QHASH) return kQHash;
@@ -326,6 +302,31 @@ bool on_device(const void* p) {
 }
 
 }  // namespace
+
+// The batched kernel's specialisation of one pattern set's plan.
+BatchVariant batch_variant_of(const Plan& plan) {
+    BatchVariant v{};
+    v.q = plan.p.q;
+    v.k = plan.p.k;
+    v.mp = plan.info.mprime;
+    v.ell = plan.ell;
+    v.mode = plan.p.map_kind == MPM_MAP_LOWBITS ? 0 : (plan.p.map_kind == MPM_MAP_QHASH ? 2 : 1);
+    v.shift = v.mode == 0 ? plan.p.map_shift : 0;
+    v.eb = plan.info.entry_bytes;
+    v.C = jit_stage_bytes((uint32_t)(v.q * v.k), v.k, false);
+    v.stages = v.C > 0 ? 1 : 0;
+    v.ebits = plan.info.entry_bits;
+    if (!v.stages) v.C = (uint32_t)(v.q * v.k);  // sample by sample: lanes of whole periods
+    return v;
+}
+
+// Index of v in vs, appended when new.
+int batch_variant_index(std::vector<BatchVariant>& vs, const BatchVariant& v) {
+    size_t idx = 0;
+    while (idx < vs.size() && std::memcmp(&vs[idx], &v, sizeof(v)) != 0) idx++;
+    if (idx == vs.size()) vs.push_back(v);
+    return (int)idx;
+}
 
 }  // namespace mpm
 
@@ -590,8 +591,8 @@ mpm_batch* mpm_batch_create(mpm_handle* const* sets, int nsets, const uint8_t* c
     if (ok && !o.generic) {
         std::vector<mpm::BatchVariant> vs;
         for (int i = 0; i < nsets; i++) {
-            const mpm::BatchVariant v = mpm::variant_of(sets[i]->plan);
-            hs[i].variant = mpm::variant_index(vs, v);
+            const mpm::BatchVariant v = mpm::batch_variant_of(sets[i]->plan);
+            hs[i].variant = mpm::batch_variant_index(vs, v);
             hs[i].stage = v.C;
         }
         int err = MPM_OK;
@@ -603,6 +604,13 @@ mpm_batch* mpm_batch_create(mpm_handle* const* sets, int nsets, const uint8_t* c
         }
         b->stats.variants = b->jit ? (uint32_t)vs.size() : 0u;
     }
+    // packed mask tables are read by the compiled kernel only
+    for (int i = 0; ok && !b->jit && i < nsets; i++)
+        if (sets[i]->plan.info.entry_bits < 8) {
+            release_batch(b);
+            set_error(MPM_ENOTSUP);
+            return nullptr;
+        }
     // the key bitmaps, one after another (each a multiple of 16 bytes)
     if (ok) {
         size_t words = 0;
@@ -804,7 +812,7 @@ int mpm_batch_jit_compile(const uint8_t* const* P, const size_t* r, const size_t
         if (plan.info.positions > 32 || plan.p.overlap ||
             (plan.p.map_kind == MPM_MAP_QHASH && plan.p.q > 5))
             return set_error(MPM_ENOTSUP);
-        mpm::variant_index(vs, mpm::variant_of(plan));
+        mpm::batch_variant_index(vs, mpm::batch_variant_of(plan));
     }
     std::string text;
     const int rc = mpm::jit_batch_compile_only(vs, &text);

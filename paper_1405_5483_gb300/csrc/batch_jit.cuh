@@ -12,7 +12,9 @@
 // it fits) and key bitmap into shared memory, and their warps pop the unit's
 // tiles from a shared counter; each warp scans a tile's 32 lane ranges.
 
+#ifndef MPM_BATCH_WARPS
 #define MPM_BATCH_WARPS 16
+#endif
 
 namespace mpm {
 

@@ -59,6 +59,7 @@ mpm::FilterDev filter_dev(const mpm_handle* h) {
     f.table = h->d_table;
     f.table_bytes = h->table_bytes_padded;
     f.entry_bytes = h->plan.info.entry_bytes;
+    f.entry_bits = h->plan.info.entry_bits;
     f.smem_table = h->plan.p.table_place == MPM_TABLE_SMEM;
     f.mu = h->d_mu;
     f.map_kind = h->plan.p.map_kind;
@@ -382,6 +383,24 @@ static mpm_handle* build_handle(const uint8_t* P, size_t r, size_t m, int sigma,
         delete h;
         set_error(rc);
         return nullptr;
+    }
+    if (h->plan.info.entry_bits < 8) {
+        // a packed table is read by the specialised kernels only: without
+        // them (no NVRTC, or a compilation error) the table is built
+        // unpacked, in global memory
+        const mpm::Plan packed = h->plan;
+        h->table_bytes_padded = (uint32_t)((packed.info.table_bytes + 15) & ~uint64_t(15));
+        int dev = 0, err = MPM_OK;
+        std::string log;
+        const bool jit_ok = cudaGetDevice(&dev) == cudaSuccess &&
+                            mpm::jit_scan_kernel(filter_dev(h), packed.p.kernel != MPM_KERNEL_SPLIT,
+                                                 dev, &err, &log) != nullptr;
+        if (!jit_ok) {
+            cudaGetLastError();
+            h->plan.info.entry_bits = 8 * h->plan.info.entry_bytes;
+            h->plan.info.table_bytes = h->plan.info.entries * (uint64_t)h->plan.info.entry_bytes;
+            h->plan.p.table_place = MPM_TABLE_GLOBAL;
+        }
     }
     if (h->plan.p.smag && (h->plan.p.overlap || h->plan.info.entry_bytes > 8)) {
         // SMAG encodes the text's non-overlapping q-grams and scans them with
@@ -852,6 +871,7 @@ int mpm_jit_compile(const uint8_t* P, size_t r, size_t m, int sigma, const mpm_p
     mpm::FilterDev f{};
     f.table_bytes = (uint32_t)((plan.info.table_bytes + 15) & ~uint64_t(15));
     f.entry_bytes = plan.info.entry_bytes;
+    f.entry_bits = plan.info.entry_bits;
     f.smem_table = plan.p.table_place == MPM_TABLE_SMEM;
     f.map_kind = plan.p.map_kind;
     f.q = plan.p.q;

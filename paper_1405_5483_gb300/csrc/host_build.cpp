@@ -333,7 +333,13 @@ int make_plan(const uint8_t* P, size_t r, size_t m, int sigma, const mpm_params*
             Lengths Lk = lengths(m, q, k, ov, maxpos);
             if (Lk.mprime < 1) continue;
             const int eb = entry_bytes_for(Lk.positions);
-            const uint64_t tb = entries * (uint64_t)eb;
+            // a table too large for shared memory, of filters of at most 4
+            // positions, packs 8, 4 or 2 entries into a byte for the
+            // specialised kernels, so that it stays in L2
+            const bool pack = Lk.positions <= 4 && !req.smag && req.kernel != MPM_KERNEL_GENERIC &&
+                              entries * (uint64_t)eb > kSmemTableBudget;
+            const int ebits = pack ? (Lk.positions <= 1 ? 1 : Lk.positions <= 2 ? 2 : 4) : 8 * eb;
+            const uint64_t tb = pack ? (entries * (uint64_t)ebits + 7) / 8 : entries * (uint64_t)eb;
             if (tb > kMaxTableBytes) continue;
             if (!(req.q && req.sigma_r && req.k) && tb > kAutoTableBytes) continue;
             double rate = candidate_rate(pt, k, Lk.mprime);
@@ -351,6 +357,7 @@ int make_plan(const uint8_t* P, size_t r, size_t m, int sigma, const mpm_params*
             cand.info.mprime = Lk.mprime;
             cand.info.positions = Lk.positions;
             cand.info.entry_bytes = eb;
+            cand.info.entry_bits = ebits;
             cand.info.entries = entries;
             cand.info.table_bytes = tb;
             cand.info.est_candidate_rate = rate;
@@ -419,9 +426,11 @@ int make_plan(const uint8_t* P, size_t r, size_t m, int sigma, const mpm_params*
         if (req.q) {
             qs.push_back(req.q);
         } else {
-            // around the paper's q = log_sigma(r m), widened by one each way
+            // around the paper's q = log_sigma(r m), widened by one below and
+            // three above (large sets: packed tables make longer q-grams
+            // affordable)
             double q0 = std::log((double)r * (double)m) / std::log((double)sr);
-            int lo = std::max(1, (int)std::floor(q0) - 1), hi = (int)std::ceil(q0) + 2;
+            int lo = std::max(1, (int)std::floor(q0) - 1), hi = (int)std::ceil(q0) + 3;
             for (int q = lo; q <= hi && q <= 16; q++) qs.push_back(q);
         }
         for (int q : qs) {
@@ -429,7 +438,12 @@ int make_plan(const uint8_t* P, size_t r, size_t m, int sigma, const mpm_params*
             Lengths L1 = lengths(m, q, 1, ov, maxpos);
             if (L1.L < 1) continue;
             const uint64_t entries = 1ull << (q * ell);
-            if (!req.q && entries * 8 > kAutoTableBytes * 8 && q * ell > 26) continue;
+            // the smallest table this q can have: packed when it has at most
+            // 4 positions
+            const uint64_t least = L1.Lf <= 4 && !req.smag && req.kernel != MPM_KERNEL_GENERIC
+                                       ? (entries * (L1.Lf <= 1 ? 1 : L1.Lf <= 2 ? 2 : 4) + 7) / 8
+                                       : entries;
+            if (!req.q && least > kAutoTableBytes && q * ell > 26) continue;
             std::vector<double> pt =
                 class_probabilities(P, r, m, q, ell, mu, h, L1.Lf, ov);
             consider(kind, sr, ell, shift, q, entries, pt, L1);
@@ -451,6 +465,16 @@ int make_plan(const uint8_t* P, size_t r, size_t m, int sigma, const mpm_params*
 int make_mask_table(const uint8_t* P, const Plan& plan, const uint8_t mu[256],
                     uint8_t* table) {
     const int q = plan.p.q, ell = plan.ell, eb = plan.info.entry_bytes;
+    const int ebits = plan.info.entry_bits;
+    // clears filter position t of entry c (packed: bit c * ebits + t)
+    auto clear = [&](uint64_t c, int t) {
+        if (ebits < 8) {
+            const uint64_t bit = c * (uint64_t)ebits + (uint64_t)t;
+            table[bit >> 3] &= (uint8_t)~(1u << (bit & 7));
+        } else {
+            table[c * (uint64_t)eb + (uint64_t)(t >> 3)] &= (uint8_t)~(1u << (t & 7));
+        }
+    };
     const int npos = plan.info.positions;
     const size_t r = plan.r, m = plan.m;
     // position t's q-grams: s + t * stride, s < shifts (see class_probabilities)
@@ -462,8 +486,7 @@ int make_mask_table(const uint8_t* P, const Plan& plan, const uint8_t mu[256],
                 for (int t = 0; t < npos; t++) {
                     const uint32_t c =
                         qgram_bin(raw_qgram(P + i * m + s + t * stride, q), q, ell);
-                    uint8_t* e = table + (size_t)c * eb;
-                    e[t >> 3] &= (uint8_t)~(1u << (t & 7));
+                    clear(c, t);
                 }
         return MPM_OK;
     }
@@ -473,8 +496,7 @@ int make_mask_table(const uint8_t* P, const Plan& plan, const uint8_t mu[256],
         for (int s = 0; s < shifts; s++) {
             for (int t = 0; t < npos; t++) {
                 uint32_t c = msd_code(&red[s + t * stride], q, ell);
-                uint8_t* e = table + (size_t)c * eb;
-                e[t >> 3] &= (uint8_t)~(1u << (t & 7));
+                clear(c, t);
             }
         }
     }

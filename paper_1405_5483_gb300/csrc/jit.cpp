@@ -137,7 +137,7 @@ constexpr size_t kSmemLimit = 227 * 1024;
 
 // Compile-time constants of one specialisation and its launch geometry.
 struct JitSpec {
-    int q, k, mp, ell, shift, mode, eb, smem, table_bytes, C, S, warps, verify, ecap, ov;
+    int q, k, mp, ell, shift, mode, eb, smem, table_bytes, C, S, warps, verify, ecap, ov, ebits;
     size_t smem_bytes;
 
     std::string defines() const {
@@ -146,9 +146,9 @@ struct JitSpec {
                       "-DMPM_Q=%d -DMPM_K=%d -DMPM_MP=%d -DMPM_ELL=%d -DMPM_SHIFT=%d "
                       "-DMPM_MODE=%d -DMPM_EB=%d -DMPM_SMEM=%d -DMPM_TABLE_BYTES=%du "
                       "-DMPM_C=%d -DMPM_S=%d -DMPM_WARPS=%d -DMPM_VERIFY=%d -DMPM_EMIT_CAP=%d "
-                      "-DMPM_OV=%d",
+                      "-DMPM_OV=%d -DMPM_EBITS=%d",
                       q, k, mp, ell, shift, mode, eb, smem, table_bytes, C, S, warps, verify,
-                      ecap, ov);
+                      ecap, ov, ebits);
         return buf;
     }
 };
@@ -188,6 +188,7 @@ bool jit_spec(const FilterDev& f, bool verify, JitSpec* out) {
     s.shift = f.map_kind == MPM_MAP_LOWBITS ? f.shift : 0;
     s.mode = f.map_kind == MPM_MAP_LOWBITS ? 0 : (f.map_kind == MPM_MAP_QHASH ? 2 : 1);
     s.eb = f.entry_bytes;
+    s.ebits = f.entry_bits > 0 ? f.entry_bits : 8 * f.entry_bytes;
     s.smem = f.smem_table ? 1 : 0;
     s.table_bytes = f.smem_table ? (int)f.table_bytes : 0;
     s.ov = f.overlap ? 1 : 0;
@@ -363,6 +364,9 @@ const JitKernel* jit_scan_kernel(const FilterDev& f, bool verify, int device, in
     }
     CUmodule mod;
     CUfunction fn;
+    // the module goes into the device's primary context, which the runtime
+    // creates on its first call that needs one
+    cudaFree(nullptr);
     if (drv.load(&mod, cubin.data()) != CUDA_SUCCESS ||
         drv.get(&fn, mod, "mpm_scan_jit") != CUDA_SUCCESS ||
         drv.set_attr(fn, CU_FUNC_ATTRIBUTE_MAX_DYNAMIC_SHARED_SIZE_BYTES, (int)s.smem_bytes) !=
@@ -483,7 +487,19 @@ constexpr size_t kBatchJitSmem = 256 + kBatchSmemTable + kBatchKeyBits / 8;
 
 struct BatchJit {
     CUfunction fn = nullptr;
+    int warps = 16;  // per block, as compiled
 };
+
+// Warps per block of the batched kernel: 24 (measured on the batch-4096
+// workload: 16 warps 1.92 ms, 24 warps 1.82 ms, 32 warps 1.89 ms per scan;
+// measurement override MPM_BATCH_WARPS: 8, 16, 24 or 32).
+static int batch_warps() {
+    if (const char* e = std::getenv("MPM_BATCH_WARPS")) {
+        const int w = std::atoi(e);
+        if (w == 8 || w == 16 || w == 24 || w == 32) return w;
+    }
+    return 24;
+}
 
 namespace {
 std::mutex g_batch_mu;
@@ -496,14 +512,15 @@ std::map<std::string, std::unique_ptr<BatchJit>> g_batch_kernels;  // device + s
 // its constants, then the kernel dispatching on the set's variant index.
 static std::string batch_source(const std::vector<BatchVariant>& vs) {
     char buf[512];
-    // stages a lane prefetches into L2 ahead of its loads (4; measurement
+    // stages a lane prefetches into L2 ahead of its loads (6; measurement
     // override MPM_BATCH_PREFETCH, 0..8)
-    int prefetch = 4;
+    int prefetch = 6;
     if (const char* e = std::getenv("MPM_BATCH_PREFETCH")) {
         const int v = std::atoi(e);
         if (v >= 0 && v <= 8) prefetch = v;
     }
-    std::snprintf(buf, sizeof(buf), "#define MPM_BATCH_PREFETCH %d\n", prefetch);
+    std::snprintf(buf, sizeof(buf), "#define MPM_BATCH_PREFETCH %d\n#define MPM_BATCH_WARPS %d\n",
+                  prefetch, batch_warps());
     std::string src = buf;
     src += kBatchPrelude;
     for (size_t i = 0; i < vs.size(); i++) {
@@ -512,13 +529,14 @@ static std::string batch_source(const std::vector<BatchVariant>& vs) {
                       "namespace mpm {\nnamespace bv%zu {\n#define MPM_Q %d\n#define MPM_K %d\n"
                       "#define MPM_MP %d\n#define MPM_ELL %d\n#define MPM_SHIFT %d\n"
                       "#define MPM_MODE %d\n#define MPM_EB %d\n#define MPM_SMEM 1\n"
-                      "#define MPM_C %u\n#define MPM_OV 0\n#define MPM_STAGES %d\n",
-                      i, v.q, v.k, v.mp, v.ell, v.shift, v.mode, v.eb, v.C, v.stages);
+                      "#define MPM_C %u\n#define MPM_OV 0\n#define MPM_STAGES %d\n"
+                      "#define MPM_EBITS %d\n",
+                      i, v.q, v.k, v.mp, v.ell, v.shift, v.mode, v.eb, v.C, v.stages, v.ebits);
         src += buf;
         src += kBatchStage;
         src += "\n#undef MPM_Q\n#undef MPM_K\n#undef MPM_MP\n#undef MPM_ELL\n#undef MPM_SHIFT\n"
                "#undef MPM_MODE\n#undef MPM_EB\n#undef MPM_SMEM\n#undef MPM_C\n#undef MPM_OV\n"
-               "#undef MPM_STAGES\n"
+               "#undef MPM_STAGES\n#undef MPM_EBITS\n"
                "}  // namespace bv\n}  // namespace mpm\n";
     }
     src += "#define MPM_BATCH_CASES";
@@ -546,6 +564,36 @@ static int batch_cubin(const std::string& src, std::string* cubin, std::string* 
         g_batch_cubins[src] = *cubin;
     }
     return rc;
+}
+
+void jit_batch_precompile(const std::vector<BatchVariant>& vs, int threads) {
+    if (!nvrtc().ok) return;
+    std::vector<std::string> todo;
+    {
+        std::lock_guard<std::mutex> lock(g_batch_mu);
+        for (const auto& v : vs) {
+            std::string src = batch_source(std::vector<BatchVariant>{v});
+            if (!g_batch_cubins.count(src) && std::find(todo.begin(), todo.end(), src) == todo.end())
+                todo.push_back(std::move(src));
+        }
+    }
+    size_t next = 0;
+    std::mutex next_mu;
+    auto work = [&] {
+        for (;;) {
+            size_t i;
+            {
+                std::lock_guard<std::mutex> lock(next_mu);
+                if (next >= todo.size()) return;
+                i = next++;
+            }
+            std::string cubin;
+            batch_cubin(todo[i], &cubin, nullptr);
+        }
+    };
+    std::vector<std::thread> pool;
+    for (int t = 0; t < std::max(1, threads); t++) pool.emplace_back(work);
+    for (auto& t : pool) t.join();
 }
 
 int jit_batch_compile_only(const std::vector<BatchVariant>& vs, std::string* log) {
@@ -576,6 +624,7 @@ const BatchJit* jit_batch_kernel(const std::vector<BatchVariant>& vs, int device
     }
     CUmodule mod;
     CUfunction fn;
+    cudaFree(nullptr);  // the primary context, as for the single-text scan
     if (drv.load(&mod, cubin.data()) != CUDA_SUCCESS ||
         drv.get(&fn, mod, "mpm_batch_jit") != CUDA_SUCCESS ||
         drv.set_attr(fn, CU_FUNC_ATTRIBUTE_MAX_DYNAMIC_SHARED_SIZE_BYTES, (int)kBatchJitSmem) !=
@@ -585,6 +634,7 @@ const BatchJit* jit_batch_kernel(const std::vector<BatchVariant>& vs, int device
     }
     auto k = std::make_unique<BatchJit>();
     k->fn = fn;
+    k->warps = batch_warps();
     std::lock_guard<std::mutex> lock(g_batch_mu);
     auto& slot = g_batch_kernels[key];
     if (!slot) slot = std::move(k);
@@ -595,8 +645,9 @@ int launch_batch_jit(const BatchJit* k, const BatchJitArgs& a, int num_sms, cuda
     const DriverApi& drv = driver();
     BatchJitArgs args = a;
     void* params[1] = {&args};
-    // one block of 16 warps per SM (the kernel's launch bounds)
-    if (drv.launch(k->fn, (unsigned)num_sms, 1, 1, 512, 1, 1, (unsigned)kBatchJitSmem,
+    // one block per SM (the kernel's launch bounds)
+    if (drv.launch(k->fn, (unsigned)num_sms, 1, 1, (unsigned)(32 * k->warps), 1, 1,
+                   (unsigned)kBatchJitSmem,
                    reinterpret_cast<CUstream>(s), params, nullptr) != CUDA_SUCCESS)
         return -1;
     return 1;

@@ -25,6 +25,7 @@ struct FilterDev {
     const void* table;        // mask table, global memory
     uint32_t table_bytes;     // padded to a multiple of 16
     int entry_bytes;          // 1, 2, 4, 8; 16, 24, 32 (2 - 4 words of state)
+    int entry_bits;           // 8 * entry_bytes, or 1, 2, 4: packed (specialised kernels only)
     int smem_table;           // copy the table into shared memory
     const uint8_t* mu;        // 256-entry byte -> reduced symbol map
     int map_kind, q, k, ell, shift, mprime, positions;
@@ -118,9 +119,18 @@ struct BatchVariant {
     int q, k, mp, ell, shift, mode, eb;
     uint32_t C;
     int stages;
+    int ebits;  // bits per mask-table entry (below 8: packed)
 };
 struct BatchJit;
 struct BatchJitArgs;
+struct Plan;
+// The specialisation of one pattern set's plan, and its index among vs
+// (appended when new).
+BatchVariant batch_variant_of(const Plan& plan);
+int batch_variant_index(std::vector<BatchVariant>& vs, const BatchVariant& v);
+// Compiles (NVRTC) the batched kernel of each single parameter set in vs that
+// is not compiled yet, on `threads` host threads, into the process cache.
+void jit_batch_precompile(const std::vector<BatchVariant>& vs, int threads);
 // Compiles (NVRTC, cached per process) and loads the batched kernel for these
 // parameter sets on the current device; nullptr with *err set when NVRTC or
 // the driver entry points are missing or the compilation fails.

@@ -445,6 +445,8 @@ int launch_mode(const ScanArgs& A, int num_sms, int chunk, cudaStream_t s) {
 
 int launch_scan(const ScanArgs& A, int num_sms, int chunk, cudaStream_t s) {
     if (A.n == 0) return 0;
+    // packed tables are read by the specialised kernels only
+    if (A.f.entry_bits > 0 && A.f.entry_bits < 8) return -2;
     // the generic kernel's raw window holds q-grams of at most 5 bytes
     if (A.f.map_kind == MPM_MAP_QHASH && A.f.q > 5) return -2;
     switch (scan_mode(A.f)) {
@@ -459,6 +461,7 @@ int launch_scan(const ScanArgs& A, int num_sms, int chunk, cudaStream_t s) {
 int launch_scan_codes(const uint32_t* codes, uint32_t nq, const FilterDev& f, uint64_t* cand,
                       uint32_t cap, uint32_t* counters, cudaStream_t s) {
     if (f.entry_bytes > 8) return -2;  // several words of state: the MAG scans only
+    if (f.entry_bits > 0 && f.entry_bits < 8) return -2;  // packed: specialised kernels only
     const uint32_t nsamp = nq / (uint32_t)f.k;
     if (nsamp == 0) return 0;
     const uint32_t per = std::max<uint32_t>(64, nsamp / (1u << 18));

@@ -13,6 +13,8 @@
 //                     alphabet mapping on the q-grams)
 //   MPM_EB            bytes per mask-table entry (1, 2, 4, 8; 16, 24, 32 for
 //                     2 - 4 words of Shift-Or state, multiword.h)
+//   MPM_EBITS         bits per entry: 8 MPM_EB (default), or 1, 2, 4 for a
+//                     packed table (entry c at bit c * MPM_EBITS, MPM_EB = 1)
 //   MPM_SMEM          1: the table pointer may be read as is (shared memory,
 //                     or a generic pointer); 0: global memory, read with an
 //                     L2 policy
@@ -129,8 +131,22 @@ __device__ __forceinline__ u32 code_at(const u32* w, const u32* rw, const u8* sm
 // Mask-table entry c: from shared memory, or from global memory with an
 // evict_last L2 policy (pol), so that the streamed text, loaded with
 // evict_first, does not push a table read at random out of L2.
+#ifndef MPM_EBITS
+#define MPM_EBITS (8 * MPM_EB)
+#endif
 __device__ __forceinline__ DT entry(const ET* tab, u32 c, u64 pol) {
-#if MPM_SMEM || MPM_EB > 8
+#if MPM_EBITS < 8
+    // packed: the entry's bits within its byte (q l <= 30, so c * bits < 2^32)
+    const u32 bit = c * (u32)MPM_EBITS;
+    const u8* t8 = reinterpret_cast<const u8*>(tab) + (bit >> 3);
+#if MPM_SMEM
+    (void)pol;
+    const u32 byte = *t8;
+#else
+    const u32 byte = ldg_hint_u8(t8, pol);
+#endif
+    return (DT)((byte >> (bit & 7u)) & ((1u << MPM_EBITS) - 1u));
+#elif MPM_SMEM || MPM_EB > 8
     (void)pol;
     return (DT)tab[c];
 #elif MPM_EB == 1

@@ -14,6 +14,7 @@
 #include <cuda_runtime.h>
 
 #include "kernels.h"
+#include "mpm_internal.h"
 
 namespace {
 
@@ -23,6 +24,7 @@ mpm::FilterDev filter_of(const mpm::Plan& plan) {
     mpm::FilterDev f{};
     f.table_bytes = (uint32_t)((plan.info.table_bytes + 15) & ~uint64_t(15));
     f.entry_bytes = plan.info.entry_bytes;
+    f.entry_bits = plan.info.entry_bits;
     f.smem_table = plan.p.table_place == MPM_TABLE_SMEM;
     f.map_kind = plan.p.map_kind;
     f.q = plan.p.q;
@@ -50,7 +52,10 @@ struct Candidate {
     double key;  // estimated candidate records per text byte
 };
 
-constexpr uint64_t kTuneMaxTable = 16ull << 20;
+// largest mask table of the cost model's grid, and of the tuner's own sets
+// (a packed table of 32 MiB for r = 100 000 DNA patterns is among the best)
+constexpr uint64_t kModelMaxTable = 16ull << 20;
+constexpr uint64_t kTuneMaxTable = 64ull << 20;
 
 }  // namespace
 
@@ -72,7 +77,7 @@ void model_grid(const uint8_t* P, size_t r, size_t m, int sigma, int max_positio
         std::vector<mpm::Plan> all;
         if (mpm::make_plan(P, r, m, sigma, &p, &best_k, &all) != MPM_OK) return;
         for (const auto& pl : all) {
-            if (pl.p.k > 8 || pl.info.positions > maxpos || pl.info.table_bytes > kTuneMaxTable)
+            if (pl.p.k > 8 || pl.info.positions > maxpos || pl.info.table_bytes > kModelMaxTable)
                 continue;
             plans->push_back(pl);
         }
@@ -119,6 +124,7 @@ extern "C" int mpm_autotune(const uint8_t* P, size_t r, size_t m, int sigma, con
     std::vector<Candidate> above_rate;  // timed only when no set passes max_rate
     if (o.grid < 0 || o.grid > 1) return set_error(MPM_EINVAL);
     if (o.overlap < 0 || o.overlap > 2) return set_error(MPM_EINVAL);
+    if (o.batch_generic < 0 || o.batch_generic > 1) return set_error(MPM_EINVAL);
     if (o.grid == 1) {
         // exactly the cost model's grid (max_q, max_k, max_sets and max_rate unused)
         std::vector<mpm::Plan> plans;
@@ -240,6 +246,16 @@ extern "C" int mpm_autotune(const uint8_t* P, size_t r, size_t m, int sigma, con
     for (const auto& c : cands) fs.push_back(filter_of(c.plan));
     if (kernels & 1) mpm::jit_precompile(fs, true, threads);
     if (kernels & 2) mpm::jit_precompile(fs, false, threads);
+    if ((kernels & 8) && !o.batch_generic) {
+        // the batched kernel of every set the batch takes, as mpm_batch_create
+        // compiles it for a batch of that one set
+        std::vector<mpm::BatchVariant> vs;
+        for (const auto& c : cands)
+            if (c.plan.info.positions <= 32 && !c.plan.p.overlap &&
+                !(c.plan.p.map_kind == MPM_MAP_QHASH && c.plan.p.q > 5))
+                vs.push_back(mpm::batch_variant_of(c.plan));
+        mpm::jit_batch_precompile(vs, threads);
+    }
 
     // the sample on the device, and output buffers
     const uint8_t* dT = T;
@@ -291,10 +307,8 @@ extern "C" int mpm_autotune(const uint8_t* P, size_t r, size_t m, int sigma, con
                 const std::vector<const uint8_t*> texts(copies, dT);
                 const std::vector<size_t> lens(copies, n);
                 const std::vector<uint32_t> sot(copies, 0u);
-                // the precompiled batched kernel (run-time q, k and mapping):
-                // one compilation per timed set would cost more than the timing
                 mpm_batch_opts bo{};
-                bo.generic = 1;
+                bo.generic = o.batch_generic;
                 batch = mpm_batch_create(&h, 1, texts.data(), lens.data(), sot.data(),
                                          (int)copies, &bo);
                 if (!batch) e.status = mpm_last_error();

@@ -71,7 +71,15 @@ def _oracle_mu(P, p):
     return fp.mu if fp.mu is not None else np.arange(256, dtype=np.uint8)
 
 
-def _table_positions(table, entry_bytes, positions):
+def _table_positions(table, entry_bytes, positions, entry_bits=None, entries=None):
+    if entry_bits is not None and entry_bits < 8:
+        # packed: entry c at bit c * entry_bits
+        bits = np.unpackbits(table, bitorder="little")[: entries * entry_bits]
+        t = bits.reshape(entries, entry_bits).astype(np.uint64)
+        v = np.zeros(entries, np.uint64)
+        for b in range(entry_bits):
+            v |= t[:, b] << np.uint64(b)
+        return v & np.uint64((1 << positions) - 1)
     t = table.reshape(-1, entry_bytes).astype(np.uint64)
     v = np.zeros(t.shape[0], np.uint64)
     for b in range(entry_bytes):
@@ -102,7 +110,8 @@ def test_host_tables_equal_oracle(mpm, seed):
     omu, otab, npos = _oracle_tables(P, p)
     assert np.array_equal(mu, omu), "mu differs from the oracle"
     assert info["positions"] == npos
-    got = _table_positions(table, info["entry_bytes"], npos)
+    got = _table_positions(table, info["entry_bytes"], npos, info["entry_bits"],
+                           int(info["entries"]))
     assert np.array_equal(got, otab.astype(np.uint64)), "mask table differs from the oracle"
 
 
@@ -123,7 +132,8 @@ def test_host_tables_qgram_hashing_equal_oracle(mpm, seed):
     p = dict(q=q, sigma_r=bins, k=k, map_kind=4, map_shift=0)
     omu, otab, npos = _oracle_tables(P, p)
     assert np.array_equal(mu, omu)
-    got = _table_positions(table, info["entry_bytes"], npos)
+    got = _table_positions(table, info["entry_bytes"], npos, info["entry_bits"],
+                           int(info["entries"]))
     assert np.array_equal(got, otab.astype(np.uint64))
 
 
@@ -150,7 +160,8 @@ def test_host_tables_overlapping_qgrams_equal_oracle(mpm, seed):
     omu, otab, npos = _oracle_tables(P, p)
     assert np.array_equal(mu, omu)
     assert info["positions"] == npos
-    got = _table_positions(table, info["entry_bytes"], npos)
+    got = _table_positions(table, info["entry_bytes"], npos, info["entry_bits"],
+                           int(info["entries"]))
     assert np.array_equal(got, otab.astype(np.uint64))
 
 
@@ -212,7 +223,8 @@ def test_host_tables_auto_params_equal_oracle(mpm):
         mu, table, info = mpm.host_tables(case.P, case.sigma)
         omu, otab, npos = _oracle_tables(case.P, info)
         assert np.array_equal(mu, omu)
-        got = _table_positions(table, info["entry_bytes"], npos)
+        got = _table_positions(table, info["entry_bytes"], npos, info["entry_bits"],
+                           int(info["entries"]))
         assert np.array_equal(got, otab.astype(np.uint64))
 
 
@@ -320,7 +332,8 @@ def test_batched_kernel_compiles_for_a_mixed_batch(mpm):
             ("protein", 64, dict(q=3, sigma_r=16, k=3, map_kind=2)),
             ("english", 64, dict(q=6, sigma_r=4, k=2, map_kind=2)),
             ("english", 16, dict(q=3, sigma_r=8, k=2, map_kind=1)),    # a repeated set
-            ("english", 64, dict(q=5, sigma_r=4, k=5, map_kind=2))]):  # period 25: no stage
+            ("english", 64, dict(q=5, sigma_r=4, k=5, map_kind=2)),    # period 25: no stage
+            ("dna", 24, dict(q=11, sigma_r=4, k=1, map_kind=3, map_shift=1))]):  # packed table
         make = {"dna": W.dna_case, "protein": W.protein_case, "english": W.english_case}[alpha]
         c = make(1 << 12, 40, m, 10, cfg=10 + i)
         sets.append(c.P)
@@ -333,3 +346,29 @@ def test_batched_kernel_compiles_for_a_mixed_batch(mpm):
     # more than 32 positions: not a batch set
     rc, _ = mpm.batch_jit_compile([sets[4]], [20], [dict(q=1, sigma_r=16, k=1, map_kind=2)])
     assert rc == mpm.MPM_ENOTSUP
+
+
+@pytest.mark.parametrize("m,kw,bits", [
+    (20, dict(q=9, sigma_r=4, k=1, map_kind=3, map_shift=1), 1),             # 32 KiB: shared
+    (24, dict(q=11, sigma_r=4, k=1, map_kind=3, map_shift=1), 1),            # 512 KiB: global
+    (27, dict(q=9, sigma_r=4, k=1, map_kind=3, map_shift=1), 2),             # 2 positions
+    (12, dict(q=9, sigma_r=4, k=1, map_kind=3, map_shift=1, overlap=1), 4),  # 4 positions
+])
+def test_packed_tables_equal_oracle(mpm, m, kw, bits):
+    """Tables of filters of at most 4 positions too large for shared memory
+    pack 8, 4 or 2 entries into a byte; every entry equals the oracle's."""
+    from paper_1405_5483_gb300 import workloads as W
+    c = W.dna_case(1 << 12, 60, m, 20, cfg=30 + m)
+    mu, table, info = mpm.host_tables(c.P, 4, **kw)
+    assert info["entry_bits"] == bits and info["positions"] <= bits
+    assert info["table_bytes"] == (info["entries"] * bits + 7) // 8
+    omu, otab, npos = _oracle_tables(c.P, info)
+    assert np.array_equal(mu, omu)
+    got = _table_positions(table, info["entry_bytes"], npos, bits, int(info["entries"]))
+    assert np.array_equal(got, otab.astype(np.uint64))
+    # the generic kernel, SMAG and the precompiled batched kernel keep whole bytes
+    _, g = mpm.plan(c.P, 4, kernel=1, **kw)
+    assert g["entry_bits"] == 8
+    if not kw.get("overlap"):
+        _, sm = mpm.plan(c.P, 4, smag=1, **kw)
+        assert sm["entry_bits"] == 8
