@@ -301,17 +301,19 @@ def run_batch(args, rank, steps=None, fast=False):
     total = b.total_bytes
     steps = max(1, steps or args.steps)
     # plain per-request form: each set's parameters tuned (mpm_search timed)
-    # on up to 16 MiB of its texts
+    # on up to 16 MiB of its texts (--no-tune: the automatic parameters)
     t0 = time.perf_counter()
     plain = []
     for sidx, P in enumerate(b.sets):
         mine = [texts[t] for t in np.flatnonzero(b.set_of_text == sidx)]
         sample = torch.cat(mine)[: 16 << 20] if mine else texts[0]
-        try:
-            best, _ = mpm.autotune(P, b.sigma, sample, kernels=3, overlap=1,
-                                   max_sets=8 if fast else 24, reps=2)
-        except mpm.MpmError:
-            best = {}
+        best = {}
+        if not args.no_tune:
+            try:
+                best, _ = mpm.autotune(P, b.sigma, sample, kernels=3, overlap=1,
+                                       max_sets=8 if fast else 24, reps=2)
+            except mpm.MpmError:
+                best = {}
         plain.append(mpm.Matcher(P, sigma=b.sigma, **best))
     plain_tune_s = time.perf_counter() - t0
     cap = 1 << 20
@@ -381,7 +383,7 @@ def run_batch(args, rank, steps=None, fast=False):
     # batched + tuned: the exhaustive tuner on a sample of each set's texts
     t0 = time.perf_counter()
     tuned = []
-    for sidx, P in enumerate(b.sets):
+    for sidx, P in enumerate(b.sets if not args.no_tune else []):
         mine = [texts[t] for t in np.flatnonzero(b.set_of_text == sidx)]
         sample = torch.cat(mine)[: 16 << 20] if mine else texts[0]
         try:
@@ -392,10 +394,12 @@ def run_batch(args, rank, steps=None, fast=False):
             best = {}
         tuned.append(best)
     tune_s = time.perf_counter() - t0
-    BT = build(tuned)
-    exact_tuned = bool(np.array_equal(result(BT), want))
-    tuned_ms = timed(BT, "batch_tuned")
-    BT.close()
+    exact_tuned, tuned_ms = True, None
+    if tuned:
+        BT = build(tuned)
+        exact_tuned = bool(np.array_equal(result(BT), want))
+        tuned_ms = timed(BT, "batch_tuned")
+        BT.close()
 
     plain_steps = max(1, min(3, steps))
     plain_pass()
@@ -456,18 +460,19 @@ def run_batch(args, rank, steps=None, fast=False):
         "plain_per_request": {"value": total / (plain_ms * 1e-3) / 1e9, "unit": "GB/s",
                               "ms_per_step": plain_ms,
                               "form": "one mpm_search per text, each set's parameters "
-                                      "from the autotuner (mpm_search timed on up to 16 MiB "
-                                      "of its texts)"},
-        "batched_tuned": {"value": total / (tuned_ms * 1e-3) / 1e9, "unit": "GB/s",
-                          "ms_per_step": tuned_ms,
-                          "form": "batched, parameters from the exhaustive autotuner "
-                                  "(batched kernel timed on 16 MiB of each set's texts)"},
+                                      + ("automatic" if args.no_tune else
+                                         "from the autotuner (mpm_search timed on up to 16 "
+                                         "MiB of its texts)")},
+        "batched_tuned": None if tuned_ms is None else {
+            "value": total / (tuned_ms * 1e-3) / 1e9, "unit": "GB/s", "ms_per_step": tuned_ms,
+            "form": "batched, parameters from the exhaustive autotuner (the compiled batched "
+                    "kernel timed on 16 MiB of each set's texts)"},
         "batched_precompiled_kernel": {"value": total / (generic_ms * 1e-3) / 1e9, "unit": "GB/s",
                                        "ms_per_step": generic_ms,
                                        "form": "the learned parameters through the precompiled "
                                                "batched kernel (run-time q, k and mapping)"},
         "batched_over_plain": plain_ms / learned_ms,
-        "learned_over_tuned": tuned_ms / learned_ms,
+        "learned_over_tuned": None if tuned_ms is None else tuned_ms / learned_ms,
         "bit_exact_vs_plain": exact_learned and exact_tuned, "occurrences": int(st["z"]),
         "candidates_per_step": int(st["candidates"]),
         "gpu_launches": launches,
