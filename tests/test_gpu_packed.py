@@ -105,11 +105,14 @@ def test_packed_search_equals_aho_corasick(mpm, native, case, kernel):
 
 def test_packed_large_set(mpm, native):
     """r = 100 000, m = 32 (the large-set configuration's patterns) on 64 MiB
-    of its text: the planner's q = 13 filter, an 8 MiB packed table read from
-    L2, both variants and the pipelined call."""
+    of its text: the planner's filter (one position, q = 14 on 2-bit codes), a
+    packed table of one bit per entry (32 MiB) read from L2, both variants and
+    the pipelined call."""
     c = W.config3(n=1 << 26)
     M = mpm.Matcher(c.P, sigma=4)
-    assert M.info["entry_bits"] == 1 and M.info["table_bytes"] == 1 << 23
+    q = M.params["q"]
+    assert M.info["positions"] == 1 and M.info["entry_bits"] == 1
+    assert M.info["table_bytes"] == (1 << (2 * q)) // 8 and M.info["table_bytes"] > 227 << 10
     want = native.aho_corasick(c.T, c.P, threads=16)
     T = dev(c.T)
     for kernel in (2, 3):
