@@ -51,10 +51,9 @@ __device__ __forceinline__ void batch_check(const WindowCtx& wc, const uint32_t*
                                             uint32_t key_mask, uint32_t i) {
     unsigned long long lo, hi;
     window_key(wc, i, &lo, &hi);
-    const unsigned long long h = key_hash(lo, hi);
-    const uint32_t bit = (uint32_t)h & key_mask;
+    const uint32_t bit = key_bit(lo, hi, 64u - (uint32_t)__popc(key_mask));
     if (!((keys[bit >> 5] >> (bit & 31)) & 1u)) return;
-    batch_probe(wc, i, lo, hi, h);
+    batch_probe(wc, i, lo, hi, key_hash(lo, hi));
 }
 
 // The warp verifies its queued fired steps, one record per lane at a time:
@@ -316,6 +315,10 @@ BatchVariant batch_variant_of(const Plan& plan) {
     v.C = jit_stage_bytes((uint32_t)(v.q * v.k), v.k, false);
     v.stages = v.C > 0 ? 1 : 0;
     v.ebits = plan.info.entry_bits;
+    // the kernel copies a table of at most kBatchSmemTable bytes (padded to
+    // 16) into shared memory; the variant then reads it there with
+    // shared-memory loads, else from global memory kept in L2
+    v.smem = ((plan.info.table_bytes + 15) & ~uint64_t(15)) <= kBatchSmemTable ? 1 : 0;
     if (!v.stages) v.C = (uint32_t)(v.q * v.k);  // sample by sample: lanes of whole periods
     return v;
 }
@@ -621,7 +624,7 @@ mpm_batch* mpm_batch_create(mpm_handle* const* sets, int nsets, const uint8_t* c
             const uint32_t mask = hs[i].key_bits - 1;
             for (const auto& sl : sets[i]->host.slots) {
                 if (!sl.count) continue;
-                const uint32_t bit = (uint32_t)mpm::key_hash(sl.lo, sl.hi) & mask;
+                const uint32_t bit = mpm::key_bit(sl.lo, sl.hi, 64u - (uint32_t)__builtin_ctz(mask + 1));
                 bm[at + bit / 32] |= 1u << (bit % 32);
             }
             at += hs[i].key_bits / 32;

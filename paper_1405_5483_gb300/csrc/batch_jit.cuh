@@ -48,7 +48,6 @@ extern "C" __global__ void __launch_bounds__(MPM_BATCH_WARPS * 32, 1)
             reinterpret_cast<uint4*>(s_keys)[i] = reinterpret_cast<const uint4*>(S.keys)[i];
         const u32 kmask = S.key_bits - 1;
         __syncthreads();
-        const void* tab = in_smem ? (const void*)s_tab : S.table;
         for (;;) {
             u32 t = 0;
             if (lane == 0) t = atomicAdd(&s_next, 1u);
@@ -78,8 +77,9 @@ extern "C" __global__ void __launch_bounds__(MPM_BATCH_WARPS * 32, 1)
             switch (S.variant) {
 #define CASE(i)                                                                               \
     case i:                                                                                   \
-        bv##i::batch_lane(reinterpret_cast<const bv##i::ET*>(tab), s_mu, s_keys, kmask, tx.T, \
-                          tx.n, a, b, live, wc, queue, ncand);                                \
+        bv##i::batch_lane(bv##i::kTableInSmem ? reinterpret_cast<const bv##i::ET*>(s_tab)       \
+                                              : reinterpret_cast<const bv##i::ET*>(S.table),   \
+                          s_mu, s_keys, kmask, tx.T, tx.n, a, b, live, wc, queue, ncand);      \
         break;
                 MPM_BATCH_CASES
 #undef CASE

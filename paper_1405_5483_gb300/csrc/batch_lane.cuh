@@ -14,45 +14,36 @@
 // The warp verifies its queued fired samples, one record per lane: record
 // (h << 32) | fired stands, for each fired bit j, for the window of q-grams
 // h0 = h - (m'-1)k - j, i.e. the text starts h0 q - s, s = q-1 .. 0, walked
-// in ascending order: the key of the first start is read from the text, each
-// next one drops a byte and takes in the byte after it; a key whose hash
-// misses the set's bitmap has no pattern group to probe.
-__device__ __forceinline__ void flush_queue(const u64* queue, int count, const u32* keys,
-                                            u32 key_mask, const WindowCtx& wc) {
-    const i64 last = (i64)wc.n - (i64)wc.m;  // the last start of a whole window
-    const u32 kb = wc.key_bytes;             // 1 .. 16
-    const u32 top = 8 * ((kb - 1) & 7);      // bit offset of a key's last byte
+// in ascending order (check_starts: the keys of all of them read at once); a
+// key whose hash misses the set's bitmap has no pattern group to probe.
+// Texts of a batch are shorter than 2^24 bytes, so 32-bit arithmetic holds
+// every start.  KW: the key width class (1: at most 8 bytes, 2: more).
+template <int KW>
+__device__ __forceinline__ void flush_records(const u64* queue, int count, const u32* keys,
+                                              u32 key_mask, const WindowCtx& wc) {
+    const int last = (int)wc.n - (int)wc.m;  // the last start of a whole window
     for (int r = (int)(threadIdx.x & 31); r < count; r += 32) {
         const u64 rec = queue[r];
-        const i64 h = (i64)(rec >> 32);
+        const int h = (int)(rec >> 32);
         u32 fired = (u32)rec;
         while (fired) {
             const int j = __ffs((int)fired) - 1;
             fired &= fired - 1;
-            const i64 h0 = h - RSH - j;
-            const i64 first = h0 * VQ - (VQ - 1) > 0 ? h0 * VQ - (VQ - 1) : 0;
-            const i64 end = h0 * VQ < last ? h0 * VQ : last;
+            const int h0 = h - RSH - j;
+            const int first = max(h0 * VQ - (VQ - 1), 0);
+            const int end = min(h0 * VQ, last);
             if (first > end) continue;
-            u32 i = (u32)first;
-            unsigned long long lo, hi;
-            window_key(wc, i, &lo, &hi);
-            for (;;) {
-                const unsigned long long hs = key_hash(lo, hi);
-                const u32 bit = (u32)hs & key_mask;
-                if ((keys[bit >> 5] >> (bit & 31)) & 1u) probe_window(wc, i, lo, hi, hs);
-                if ((i64)i >= end) break;
-                // i + kb <= i + m - 1 < n: the byte after the key is in the text
-                const unsigned long long nb = __ldg(wc.T + i + kb);
-                lo = (lo >> 8) | (hi << 56);
-                hi >>= 8;
-                if (kb <= 8)
-                    lo |= nb << top;
-                else
-                    hi |= nb << top;
-                i++;
-            }
+            check_starts<KW>(wc, (u32)first, (u32)end, keys, key_mask);
         }
     }
+}
+
+__device__ __forceinline__ void flush_queue(const u64* queue, int count, const u32* keys,
+                                            u32 key_mask, const WindowCtx& wc) {
+    if (wc.key_bytes <= 8)
+        flush_records<1>(queue, count, keys, key_mask, wc);
+    else
+        flush_records<2>(queue, count, keys, key_mask, wc);
 }
 
 // Queues the fired samples of one stage (for every lane, every sample u
@@ -82,14 +73,22 @@ __device__ __forceinline__ void queue_stage(FT fm, u32 h1, u64* queue, int& qcou
     }
 }
 
+// Where this parameter set's mask table is read: shared memory (the
+// kernel's copy of a table of at most kBatchSmemTable bytes; the caller
+// passes the shared-memory copy itself, so that the lookups compile to
+// shared-memory loads, not generic ones), else global memory through L2.
+constexpr bool kTableInSmem = MPM_SMEM != 0;
+
 // All 32 lanes of a warp call this together for one tile; lane range
-// [a, b), live = a < b.  tab: the set's mask table (shared or global
-// memory), smu: its byte map in shared memory.
+// [a, b), live = a < b.  tab: the set's mask table (in shared memory when
+// kTableInSmem, else in global memory), smu: its byte map in shared memory.
 __device__ __forceinline__ void batch_lane(const ET* tab, const u8* smu, const u32* keys,
                                            u32 key_mask, const u8* T, u32 n, u32 a, u32 b,
                                            bool live, const WindowCtx& wc, u64* queue,
                                            u32& ncand) {
     (void)n;
+    // a table in global memory is kept in L2 ahead of the text stream
+    const u64 tpol = kTableInSmem ? 0ull : l2_policy_evict_last();
     DT D = ~(DT)0;
     // the m'-1 samples that end at a, a - P, ...; those that would start
     // before the text do not exist and leave D at all ones
@@ -97,7 +96,7 @@ __device__ __forceinline__ void batch_lane(const ET* tab, const u8* smu, const u
         for (int j = MP - 2; j >= 0; j--) {
             const i64 e = (i64)a - (i64)j * P;
             if (e - Q < 0) continue;
-            D = (D << K) | entry(tab, code_bytes(T, (u32)(e - Q), smu), 0ull);
+            D = (D << K) | entry(tab, code_bytes(T, (u32)(e - Q), smu), tpol);
         }
     }
     const bool vec = (reinterpret_cast<unsigned long long>(T) & 15) == 0;
@@ -136,7 +135,7 @@ __device__ __forceinline__ void batch_lane(const ET* tab, const u8* smu, const u
         // for the rest of its range
         const DT keep = D;
         FT fm = 0;
-        run_stage<true>(w, D, fm, tab, smu, 0ull);
+        run_stage<true>(w, D, fm, tab, smu, tpol);
         if (!act) {
             D = keep;
             fm = 0;
@@ -157,7 +156,7 @@ __device__ __forceinline__ void batch_lane(const ET* tab, const u8* smu, const u
         u32 fired = 0, hq = 0;
         if (t < nrest) {
             const u32 st = e0 + (t + 1) * (u32)P - (u32)Q;
-            D = (D << K) | entry(tab, code_bytes(T, st, smu), 0ull);
+            D = (D << K) | entry(tab, code_bytes(T, st, smu), tpol);
             fired = ~bits_at(D, RSH) & KMASK;
             hq = st / (u32)Q;
         }

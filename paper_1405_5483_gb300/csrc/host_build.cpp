@@ -589,7 +589,7 @@ std::vector<uint32_t> key_bitmap(const HostTables& t, uint32_t max_bits) {
     std::vector<uint32_t> bm(bits / 32, 0u);
     for (const auto& sl : t.slots) {
         if (!sl.count) continue;
-        const uint32_t bit = (uint32_t)key_hash(sl.lo, sl.hi) & (bits - 1);
+        const uint32_t bit = key_bit(sl.lo, sl.hi, 64u - (uint32_t)__builtin_ctz(bits));
         bm[bit / 32] |= 1u << (bit % 32);
     }
     return bm;

@@ -528,10 +528,11 @@ static std::string batch_source(const std::vector<BatchVariant>& vs) {
         std::snprintf(buf, sizeof(buf),
                       "namespace mpm {\nnamespace bv%zu {\n#define MPM_Q %d\n#define MPM_K %d\n"
                       "#define MPM_MP %d\n#define MPM_ELL %d\n#define MPM_SHIFT %d\n"
-                      "#define MPM_MODE %d\n#define MPM_EB %d\n#define MPM_SMEM 1\n"
+                      "#define MPM_MODE %d\n#define MPM_EB %d\n#define MPM_SMEM %d\n"
                       "#define MPM_C %u\n#define MPM_OV 0\n#define MPM_STAGES %d\n"
                       "#define MPM_EBITS %d\n",
-                      i, v.q, v.k, v.mp, v.ell, v.shift, v.mode, v.eb, v.C, v.stages, v.ebits);
+                      i, v.q, v.k, v.mp, v.ell, v.shift, v.mode, v.eb, v.smem, v.C, v.stages,
+                      v.ebits);
         src += buf;
         src += kBatchStage;
         src += "\n#undef MPM_Q\n#undef MPM_K\n#undef MPM_MP\n#undef MPM_ELL\n#undef MPM_SHIFT\n"

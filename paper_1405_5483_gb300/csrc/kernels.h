@@ -120,6 +120,7 @@ struct BatchVariant {
     uint32_t C;
     int stages;
     int ebits;  // bits per mask-table entry (below 8: packed)
+    int smem;   // 1: the table fits the kernel's shared-memory copy
 };
 struct BatchJit;
 struct BatchJitArgs;

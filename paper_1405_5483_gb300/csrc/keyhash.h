@@ -19,6 +19,17 @@ inline unsigned long long key_hash(unsigned long long lo, unsigned long long hi)
     return h;
 }
 
+// Bit of a key in a key bitmap of 2^(64 - shift) bits: the top bits of one
+// multiplicative (Fibonacci) hash of the key.  The bitmap only filters keys
+// before the slot probe, which hashes with key_hash, so this hash is the
+// cheaper one: for a key of at most 8 bytes (hi = 0) one 64-bit multiply.
+#if defined(__CUDACC__) || defined(__CUDACC_RTC__)
+__host__ __device__
+#endif
+inline unsigned int key_bit(unsigned long long lo, unsigned long long hi, unsigned int shift) {
+    return (unsigned int)(((lo ^ (hi * 0xC2B2AE3D27D4EB4Full)) * 0x9E3779B97F4A7C15ull) >> shift);
+}
+
 // Bin of a whole q-gram for the q-gram hashing map (MPM_MAP_QHASH): raw is
 // its q (<= 8) bytes read little-endian; the bin is the top `bits` bits of a
 // multiplicative hash, 32-bit for q <= 4 and 64-bit above.

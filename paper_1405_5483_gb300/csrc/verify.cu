@@ -5,9 +5,9 @@
 // A candidate record (fired << 32) | h stands, for every set bit j of fired,
 // for the window of q-grams starting at h0 = h - (m'-1)k - j, i.e. for the
 // text starts i = h0*q - s, s = 0..q-1 (each start has exactly one (h0, s)).
-// One thread takes one record and walks its q starts in ascending order: the
-// key (first min(m, 16) bytes) of the first start is read from the text,
-// each next key drops a byte and takes in the byte after it.  A key whose
+// One thread takes one record and walks its q starts in ascending order
+// (check_starts: the keys, the first min(m, 16) bytes of each window, read
+// together from the aligned 32 bytes around them when they fit).  A key whose
 // hash hits a clear bit of the key bitmap (copied into shared memory by
 // every block: random bit tests there cost a few bank conflicts, where in L1
 // each lane's test is a cache line of its own) has no pattern group; the others
@@ -36,7 +36,6 @@ __global__ void __launch_bounds__(kVerifyThreads, 2) verify_kernel(const VerifyA
     const int64_t q = A.q;
     const int64_t last = (int64_t)(A.n - A.m);  // the last start of a whole window
     const uint32_t kb = (uint32_t)A.key_bytes;   // 1 .. 16
-    const uint32_t top = 8 * ((kb - 1) & 7);     // bit offset of a key's last byte
     WindowCtx wc;
     wc.T = A.T;
     wc.n = A.n;
@@ -64,25 +63,10 @@ __global__ void __launch_bounds__(kVerifyThreads, 2) verify_kernel(const VerifyA
             const int64_t first = max(h0 * q - (q - 1), (int64_t)0);
             const int64_t end = min(h0 * q, last);
             if (first > end) continue;
-            uint32_t i = (uint32_t)first;
-            unsigned long long lo, hi;
-            window_key(wc, i, &lo, &hi);
-            for (;;) {
-                const unsigned long long hs = key_hash(lo, hi);
-                const uint32_t bit = (uint32_t)hs & A.key_mask;
-                if ((s_keys[bit >> 5] >> (bit & 31)) & 1u)
-                    probe_window(wc, i, lo, hi, hs);
-                if ((int64_t)i >= end) break;
-                // i + kb <= i + m - 1 < n: the byte after the key is in the text
-                const unsigned long long nb = __ldg(A.T + i + kb);
-                lo = (lo >> 8) | (hi << 56);
-                hi >>= 8;
-                if (kb <= 8)
-                    lo |= nb << top;
-                else
-                    hi |= nb << top;
-                i++;
-            }
+            if (kb <= 8)
+                check_starts<1>(wc, (uint32_t)first, (uint32_t)end, s_keys, A.key_mask);
+            else
+                check_starts<2>(wc, (uint32_t)first, (uint32_t)end, s_keys, A.key_mask);
         }
     }
 }

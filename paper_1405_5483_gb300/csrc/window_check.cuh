@@ -100,6 +100,76 @@ static __device__ __forceinline__ void probe_window(const WindowCtx& c, unsigned
     }
 }
 
+// The text starts first .. end (first <= end) of one candidate, in ascending
+// order: the key of each start (the first key_bytes bytes of its window) is
+// tested against the key bitmap `keys` (key_mask + 1 bits, the bit key_bit
+// of every pattern group's key set), and only a set bit probes the groups.  The keys of all the starts lie in end - first + key_bytes
+// bytes; when these fit the aligned 24 (keys of at most 8 bytes) or 32 bytes
+// around them they are read with three or four independent 8-byte loads, so
+// the walk waits for memory once, and each next key is that window shifted
+// by a byte.  Otherwise the first key is read whole and each next one takes
+// in the byte after it.  KW: 1 for keys of at most 8 bytes, 2 for longer
+// keys, 0 to decide from key_bytes at run time.
+template <int KW = 0>
+static __device__ __forceinline__ void check_starts(const WindowCtx& c, unsigned int first,
+                                                    unsigned int end, const unsigned int* keys,
+                                                    unsigned int key_mask) {
+    const unsigned int kb = c.key_bytes;  // 1 .. 16
+    const bool narrow = KW == 1 || (KW == 0 && kb <= 8);
+    const unsigned long long tb = reinterpret_cast<unsigned long long>(c.T);
+    const unsigned long long ad = tb + first;
+    const unsigned long long ab = ad & ~7ull;
+    const unsigned int span = narrow ? 24u : 32u;
+    const unsigned int kshift = 64u - (unsigned int)__popc(key_mask);
+    if (end - first + kb + 7 <= span && ab >= tb && ab + span <= tb + c.n) {
+        const unsigned long long* p = reinterpret_cast<const unsigned long long*>(ab);
+        const unsigned long long x0 = __ldg(p), x1 = __ldg(p + 1), x2 = __ldg(p + 2);
+        const unsigned long long x3 = narrow ? 0ull : __ldg(p + 3);
+        // bytes first .. in a (lowest), b, d; (x << (63 - s)) << 1 is
+        // x << (64 - s), and 0 for s = 0
+        const unsigned int s8 = (unsigned int)(ad - ab) * 8;
+        unsigned long long a = (x0 >> s8) | ((x1 << (63 - s8)) << 1);
+        unsigned long long b = (x1 >> s8) | ((x2 << (63 - s8)) << 1);
+        unsigned long long d = narrow ? 0ull : (x2 >> s8) | ((x3 << (63 - s8)) << 1);
+        const unsigned long long lom = kb >= 8 ? ~0ull : (1ull << (8 * kb)) - 1;
+        const unsigned long long him =
+            kb <= 8 ? 0ull : (kb >= 16 ? ~0ull : (1ull << (8 * (kb - 8))) - 1);
+        for (unsigned int i = first;; i++) {
+            const unsigned long long lo = a & lom;
+            const unsigned long long hi = narrow ? 0ull : b & him;
+            const unsigned int bit = narrow ? key_bit(lo, 0ull, kshift) : key_bit(lo, hi, kshift);
+            if ((keys[bit >> 5] >> (bit & 31)) & 1u) probe_window(c, i, lo, hi, key_hash(lo, hi));
+            if (i >= end) break;
+            a = (a >> 8) | (b << 56);
+            if (narrow) {
+                b >>= 8;
+            } else {
+                b = (b >> 8) | (d << 56);
+                d >>= 8;
+            }
+        }
+        return;
+    }
+    const unsigned int top = 8 * ((kb - 1) & 7);  // bit offset of a key's last byte
+    unsigned int i = first;
+    unsigned long long lo, hi;
+    window_key(c, i, &lo, &hi);
+    for (;;) {
+        const unsigned int bit = key_bit(lo, hi, kshift);
+        if ((keys[bit >> 5] >> (bit & 31)) & 1u) probe_window(c, i, lo, hi, key_hash(lo, hi));
+        if (i >= end) break;
+        // i + kb <= i + m - 1 < n: the byte after the key is in the text
+        const unsigned long long nb = __ldg(c.T + i + kb);
+        lo = (lo >> 8) | (hi << 56);
+        hi >>= 8;
+        if (kb <= 8)
+            lo |= nb << top;
+        else
+            hi |= nb << top;
+        i++;
+    }
+}
+
 // The window T[i..i+m) checked against the pattern set.
 static __device__ __noinline__ void check_window(const WindowCtx& c, unsigned int i) {
     unsigned long long lo, hi;
